@@ -1,0 +1,637 @@
+"""Plain FP64 oracle of one Enzo-P/Cello hydro step over the leaves of an
+array-of-octrees mesh.  TEST INFRASTRUCTURE ONLY: used by tests/, by the
+smoke check and by the CPU-baseline leg of the benchmark, never by the
+product library.
+
+What the paper fixes (Sec. II.B, II.C): leaf Blocks carry the fields; a ghost
+layer of configurable width around each Block is refreshed from neighbouring
+Blocks before a Method runs (Sec. II.B, Fig. 4); Refine / Restrict / Prolong
+plug-ins move data between levels (Sec. II.B); the hydro Method is a modified
+piecewise parabolic method (PPM, Colella & Woodward 1984; Bryan et al. 1995)
+(Sec. II.C).  The paper prints none of the formulas, so every formula below is
+a reading of the named published method, stated in the docstrings and listed
+in the design doc.  The code is vectorised torch float64 on the CPU: every
+elementwise operation is written out in the stated order (no fused
+multiply-add, no reassociation), so a reader can check it term by term.
+
+Layout: U[B, 5, N, N, N] float64, leaves in mesh order, conserved fields
+(rho, rho*u, rho*v, rho*w, E), cells indexed [z, y, x] with N = n + 2g.
+
+Parity pins (tests/test_oracle_*.py): uniform-state invariance, mirror
+symmetry, conservation on periodic AMR meshes, all-one-level AMR equal to a
+single uniform block, Sod against the exact Riemann solution, interface
+formula exact on cubics, two-shock solver exact on symmetric collisions,
+prolongation/restriction identities, CFL closed form, brute-force flags.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .mesh import FINE, OUTFLOW, PERIODIC, Mesh, neighbour_table  # noqa: F401
+
+RHO_FLOOR = 1e-10
+P_FLOOR = 1e-20
+EPS_SHOCK = 0.33     # CW84 shock-detector threshold on the relative pressure jump
+OMEGA1 = 0.75        # CW84 flattening: ratio offset
+OMEGA2 = 10.0        # CW84 flattening: ratio slope
+N_RIEMANN = 5        # fixed Newton iterations of the two-shock solver, no early exit
+SIXTH = 1.0 / 6.0
+TWO_THIRDS = 2.0 / 3.0
+GHOSTS = 4           # the PPM stencil below reaches 4 cells on each side
+
+# conserved component order seen by a sweep along each axis:
+# (density, normal momentum, transverse momentum 1, transverse momentum 2, E)
+AXIS_COMPONENTS = {0: (0, 1, 2, 3, 4), 1: (0, 2, 1, 3, 4), 2: (0, 3, 1, 2, 4)}
+AXIS_DIM = {0: 4, 1: 3, 2: 2}   # tensor dim of an axis in U[B, 5, z, y, x]
+
+
+# ----------------------------------------------------------------- 1-D PPM
+def primitives(rho_c, mn, mt1, mt2, E, gamma):
+    """Conserved -> primitive (rho, u_n, u_t1, u_t2, p) with density and
+    pressure floors.  Kinetic energy 0.5*rho*(u_n^2 + (u_t1^2 + u_t2^2))."""
+    rho = torch.clamp_min(rho_c, RHO_FLOOR)
+    un = mn / rho
+    ut1 = mt1 / rho
+    ut2 = mt2 / rho
+    ke = (0.5 * rho) * (un * un + (ut1 * ut1 + ut2 * ut2))
+    p = torch.clamp_min((gamma - 1.0) * (E - ke), P_FLOOR)
+    return rho, un, ut1, ut2, p
+
+
+def limited_slope(am, a0, ap):
+    """CW84 monotonised centred slope: 0.5*(a+ - a-), limited to twice the
+    one-sided differences, zero at a local extremum."""
+    dl = a0 - am
+    dr = ap - a0
+    da = 0.5 * (ap - am)
+    m = torch.minimum(torch.abs(da), torch.minimum(2.0 * torch.abs(dl), 2.0 * torch.abs(dr)))
+    return torch.where(dl * dr > 0.0, torch.copysign(m, da), torch.zeros_like(da))
+
+
+def interface_value(a0, a1, dm0, dm1):
+    """CW84 interface value between cells j and j+1 in limited form:
+    0.5*(a_j + a_j+1) - (dm_j+1 - dm_j)/6.  With unlimited slopes this is the
+    fourth-order (7/12, -1/12) interpolant, exact for cell averages of cubics."""
+    return 0.5 * (a0 + a1) - (dm1 - dm0) * SIXTH
+
+
+def flatten_tilde(pm2, pm1, pp1, pp2, um1, up1):
+    """CW84 shock detector: nonzero only across a compressive pressure jump
+    larger than EPS_SHOCK relative; 10*(dp1/dp2 - 0.75) clipped to [0, 1]."""
+    dp1 = pp1 - pm1
+    dp2 = pp2 - pm2
+    shock = (torch.abs(dp1) > EPS_SHOCK * torch.minimum(pp1, pm1)) & (um1 - up1 > 0.0) & (dp2 != 0.0)
+    ratio = dp1 / torch.where(dp2 != 0.0, dp2, torch.ones_like(dp2))
+    ft = torch.clamp_min(torch.clamp_max(OMEGA2 * (ratio - OMEGA1), 1.0), 0.0)
+    return torch.where(shock, ft, torch.zeros_like(ft))
+
+
+def monotonize(a, aL, aR):
+    """CW84 monotonicity constraints on the parabola of one cell."""
+    ext = (aR - a) * (a - aL) <= 0.0
+    da = aR - aL
+    dm = a - 0.5 * (aL + aR)
+    t1 = da * dm
+    t2 = (da * da) * SIXTH
+    nL = torch.where(ext, a, torch.where(t1 > t2, 3.0 * a - 2.0 * aR, aL))
+    nR = torch.where(ext, a, torch.where(-t2 > t1, 3.0 * a - 2.0 * aL, aR))
+    return nL, nR
+
+
+def edge_avg_right(aL, aR, a6, sigma):
+    """Average of the cell parabola over the last sigma of the cell (CW84)."""
+    da = aR - aL
+    return aR - (0.5 * sigma) * (da - (1.0 - TWO_THIRDS * sigma) * a6)
+
+
+def edge_avg_left(aL, aR, a6, sigma):
+    """Average of the cell parabola over the first sigma of the cell (CW84)."""
+    da = aR - aL
+    return aL + (0.5 * sigma) * (da + (1.0 - TWO_THIRDS * sigma) * a6)
+
+
+def trace(W, aL, aR, dtdx, gamma):
+    """Characteristic tracing of one cell to its two edges at the half step.
+
+    Waves u-c, u, u+c with the left/right eigenvectors of the primitive
+    (rho, u, p) system at the cell centre.  Right edge: reference state = the
+    average seen by the fastest wave moving right (or aR if none does); every
+    other wave moving right subtracts its projection l.(ref - avg) along its
+    right eigenvector.  Left edge mirrors it.  Transverse velocities ride the
+    entropy wave.  Returns (state at the left edge, state at the right edge),
+    each (rho, u_n, u_t1, u_t2, p), floored."""
+    rho, un, p = W[0], W[1], W[4]
+    csq = (gamma * p) / rho
+    c = torch.sqrt(csq)
+    a6 = [6.0 * (W[q] - 0.5 * (aL[q] + aR[q])) for q in range(5)]
+    lm, l0, lp = un - c, un, un + c
+    half_rho_c = (0.5 * rho) / c
+    half_inv_csq = 0.5 / csq
+    c_rho = c / rho
+    zero = torch.zeros_like(un)
+
+    # right edge: waves with lambda > 0
+    sp, s0, sm = lp * dtdx, l0 * dtdx, lm * dtdx
+    ref = [torch.where(lp > 0.0, edge_avg_right(aL[q], aR[q], a6[q], sp), aR[q]) for q in range(5)]
+    bm = torch.where(lm > 0.0,
+                     (ref[4] - edge_avg_right(aL[4], aR[4], a6[4], sm)) * half_inv_csq
+                     - (ref[1] - edge_avg_right(aL[1], aR[1], a6[1], sm)) * half_rho_c, zero)
+    b0 = torch.where(l0 > 0.0,
+                     (ref[0] - edge_avg_right(aL[0], aR[0], a6[0], s0))
+                     - (ref[4] - edge_avg_right(aL[4], aR[4], a6[4], s0)) / csq, zero)
+    r_rho = torch.clamp_min(ref[0] - (b0 + bm), RHO_FLOOR)
+    r_un = ref[1] + c_rho * bm
+    r_p = torch.clamp_min(ref[4] - csq * bm, P_FLOOR)
+    r_t1 = torch.where(l0 > 0.0, edge_avg_right(aL[2], aR[2], a6[2], s0), ref[2])
+    r_t2 = torch.where(l0 > 0.0, edge_avg_right(aL[3], aR[3], a6[3], s0), ref[3])
+
+    # left edge: waves with lambda < 0
+    tm, t0, tp = -lm * dtdx, -l0 * dtdx, -lp * dtdx
+    ref = [torch.where(lm < 0.0, edge_avg_left(aL[q], aR[q], a6[q], tm), aL[q]) for q in range(5)]
+    bp = torch.where(lp < 0.0,
+                     (ref[4] - edge_avg_left(aL[4], aR[4], a6[4], tp)) * half_inv_csq
+                     + (ref[1] - edge_avg_left(aL[1], aR[1], a6[1], tp)) * half_rho_c, zero)
+    b0 = torch.where(l0 < 0.0,
+                     (ref[0] - edge_avg_left(aL[0], aR[0], a6[0], t0))
+                     - (ref[4] - edge_avg_left(aL[4], aR[4], a6[4], t0)) / csq, zero)
+    l_rho = torch.clamp_min(ref[0] - (b0 + bp), RHO_FLOOR)
+    l_un = ref[1] - c_rho * bp
+    l_p = torch.clamp_min(ref[4] - csq * bp, P_FLOOR)
+    l_t1 = torch.where(l0 < 0.0, edge_avg_left(aL[2], aR[2], a6[2], t0), ref[2])
+    l_t2 = torch.where(l0 < 0.0, edge_avg_left(aL[3], aR[3], a6[3], t0), ref[3])
+    return (l_rho, l_un, l_t1, l_t2, l_p), (r_rho, r_un, r_t1, r_t2, r_p)
+
+
+def riemann_flux(WL, WR, gamma):
+    """CW84 two-shock approximate Riemann solver with N_RIEMANN fixed Newton
+    steps on p* (shock curves on both sides, derivative Z = 2W^3/(W^2+C^2)),
+    u* = Z-weighted mean, sampled at x/t = 0 (u* >= 0 takes the left side);
+    inside a rarefaction the state is interpolated linearly between the head
+    and tail speeds.  Returns the five fluxes (rho, m_n, m_t1, m_t2, E)."""
+    rL, uL, t1L, t2L, pL = WL
+    rR, uR, t1R, t2R, pR = WR
+    g1 = (gamma + 1.0) / (2.0 * gamma)
+    CL = torch.sqrt((gamma * pL) * rL)
+    CR = torch.sqrt((gamma * pR) * rR)
+    ps = ((CR * pL + CL * pR) + (CL * CR) * (uL - uR)) / (CL + CR)
+    ps = torch.clamp_min(ps, P_FLOOR)
+
+    def curves(ps):
+        WLs = CL * torch.sqrt(1.0 + g1 * (ps / pL - 1.0))
+        WRs = CR * torch.sqrt(1.0 + g1 * (ps / pR - 1.0))
+        uLs = uL - (ps - pL) / WLs
+        uRs = uR + (ps - pR) / WRs
+        ZL = ((2.0 * WLs) * WLs) * WLs / (WLs * WLs + CL * CL)
+        ZR = ((2.0 * WRs) * WRs) * WRs / (WRs * WRs + CR * CR)
+        return WLs, WRs, uLs, uRs, ZL, ZR
+
+    for _ in range(N_RIEMANN):
+        _, _, uLs, uRs, ZL, ZR = curves(ps)
+        ps = torch.clamp_min(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), P_FLOOR)
+    WLs, WRs, uLs, uRs, ZL, ZR = curves(ps)
+    us = (ZL * uLs + ZR * uRs) / (ZL + ZR)
+
+    left = us >= 0.0
+    rs = torch.where(left, rL, rR)
+    u_s = torch.where(left, uL, uR)
+    p_s = torch.where(left, pL, pR)
+    W_s = torch.where(left, WLs, WRs)
+    t1 = torch.where(left, t1L, t1R)
+    t2 = torch.where(left, t2L, t2R)
+    v_s = torch.where(left, -uL, uR)        # outward normal velocity of the sampled side
+    v_star = torch.where(left, -us, us)
+    tau = 1.0 / rs - (ps - p_s) / (W_s * W_s)
+    rstar = torch.where(tau > 0.0, 1.0 / torch.where(tau > 0.0, tau, torch.ones_like(tau)),
+                        torch.full_like(tau, RHO_FLOOR))
+    rstar = torch.clamp_min(rstar, RHO_FLOOR)
+    c_s = torch.sqrt((gamma * p_s) / rs)
+    c_star = torch.sqrt((gamma * ps) / rstar)
+    shock = ps > p_s
+    head = torch.where(shock, v_s + W_s / rs, v_s + c_s)
+    tail = torch.where(shock, head, v_star + c_star)
+    orig = head <= 0.0
+    star = (~orig) & (tail > 0.0)
+    den = head - tail
+    w = head / torch.where(orig | star, torch.ones_like(den), den)
+    fan_r = rs + w * (rstar - rs)
+    fan_u = u_s + w * (us - u_s)
+    fan_p = p_s + w * (ps - p_s)
+    r = torch.where(orig, rs, torch.where(star, rstar, fan_r))
+    u = torch.where(orig, u_s, torch.where(star, us, fan_u))
+    p = torch.where(orig, p_s, torch.where(star, ps, fan_p))
+
+    inv_gm1 = 1.0 / (gamma - 1.0)
+    f0 = r * u
+    f1 = f0 * u + p
+    f2 = f0 * t1
+    f3 = f0 * t2
+    E = p * inv_gm1 + (0.5 * r) * (u * u + (t1 * t1 + t2 * t2))
+    f4 = u * (E + p)
+    return f0, f1, f2, f3, f4
+
+
+def pencil_fluxes(Uc, dtdx, gamma):
+    """Fluxes at the n+1 interfaces between cells c and c+1, c = 3 .. N-5, of
+    pencils of length N = n + 8 (last tensor dim).  Uc = (rho, m_n, m_t1,
+    m_t2, E) tensors."""
+    N = Uc[0].shape[-1]
+    W = primitives(*Uc, gamma)
+    p, un = W[4], W[1]
+    dm = [limited_slope(a[..., :-2], a[..., 1:-1], a[..., 2:]) for a in W]           # cells 1..N-2
+    ai = [0.5 * (a[..., 1:N - 2] + a[..., 2:N - 1]) - (d[..., 1:] - d[..., :-1]) * SIXTH
+          for a, d in zip(W, dm)]                                                        # j+1/2, j=1..N-3
+    ft = flatten_tilde(p[..., 0:N - 4], p[..., 1:N - 3], p[..., 3:N - 1], p[..., 4:N],
+                       un[..., 1:N - 3], un[..., 3:N - 1])                                # cells 2..N-3
+    s = p[..., 4:N - 2] - p[..., 2:N - 4]                                                  # cells 3..N-4
+    fj, fm, fp = ft[..., 1:N - 5], ft[..., 0:N - 6], ft[..., 2:N - 4]
+    f = torch.where(s > 0.0, torch.maximum(fj, fm), torch.where(s < 0.0, torch.maximum(fj, fp), fj))
+    Wc = [a[..., 3:N - 3] for a in W]
+    aL, aR = [], []
+    for q in range(5):
+        l = ai[q][..., 1:N - 5]
+        r = ai[q][..., 2:N - 4]
+        l = f * Wc[q] + (1.0 - f) * l
+        r = f * Wc[q] + (1.0 - f) * r
+        l, r = monotonize(Wc[q], l, r)
+        aL.append(l)
+        aR.append(r)
+    Wm, Wp = trace(Wc, aL, aR, dtdx, gamma)        # cells 3..N-4
+    left = [x[..., 0:N - 7] for x in Wp]
+    right = [x[..., 1:N - 6] for x in Wm]
+    return riemann_flux(left, right, gamma)
+
+
+# ------------------------------------------------------------------ sweeps
+def dx_of_leaves(mesh: Mesh):
+    d = mesh.desc
+    return torch.tensor([d.dx(int(L)) for L in mesh.leaves[:, 0]], dtype=torch.float64)
+
+
+def sweep(U, mesh: Mesh, axis: int, dt: float, rows):
+    """One directional PPM sweep of every leaf.  rows = ((lo, hi), (lo, hi))
+    ranges of the two transverse tensor dims (in their U order) whose pencils
+    are updated; cells g..g+n-1 along the axis are updated in place.
+    Returns (U, faces) with faces = (F at interface g-1/2, F at g+n-1/2) on
+    interior rows, each [B, 5, n, n] indexed [t2, t1] (t1 < t2 axes)."""
+    n, g = mesh.desc.n, mesh.desc.ghosts
+    assert g == GHOSTS
+    B = U.shape[0]
+    dim = AXIS_DIM[axis]
+    comp = AXIS_COMPONENTS[axis]
+    V = U.movedim(dim, -1)
+    dtdx = (dt / dx_of_leaves(mesh)).view(B, 1, 1, 1)
+    F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma)
+    (a0, a1), (b0, b1) = rows
+    V2 = V.clone()
+    for q in range(5):
+        Fq = F[q][:, a0:a1, b0:b1]
+        V2[:, comp[q], a0:a1, b0:b1, g:g + n] = (V[:, comp[q], a0:a1, b0:b1, g:g + n]
+                                                - dtdx * (Fq[..., 1:] - Fq[..., :-1]))
+    inv = [0] * 5
+    for q in range(5):
+        inv[comp[q]] = q
+    lo = torch.stack([F[inv[f]][:, g:g + n, g:g + n, 0] for f in range(5)], 1)
+    hi = torch.stack([F[inv[f]][:, g:g + n, g:g + n, n] for f in range(5)], 1)
+    return V2.movedim(-1, dim), (lo, hi)
+
+
+def sweep_order(cycle: int):
+    """x, y, z on even cycles and z, y, x on odd ones (Strang-type alternation)."""
+    return (0, 1, 2) if cycle % 2 == 0 else (2, 1, 0)
+
+
+def transverse_rows(mesh: Mesh, axis: int, swept):
+    """Rows updated by a sweep: a transverse axis already swept this step
+    needs interior rows only, one not yet swept needs all N rows (the later
+    sweeps read its ghost rows)."""
+    n, g = mesh.desc.n, mesh.desc.ghosts
+    N = n + 2 * g
+    dims = [a for a in (2, 1, 0) if a != axis]      # transverse axes in U dim order (z, y, x)
+    return tuple((g, g + n) if a in swept else (0, N) for a in dims)
+
+
+# ----------------------------------------------------------- ghost refresh
+def _bc(mesh: Mesh, M: int, axis: int, v):
+    """Apply the physical boundary to level-M global cell indices: periodic
+    wraps, outflow clamps to the nearest interior cell."""
+    ncell = (mesh.desc.root[axis] << M) * mesh.desc.n
+    if mesh.desc.bc[axis] == PERIODIC:
+        return np.mod(v, ncell)
+    return np.clip(v, 0, ncell - 1)
+
+
+class RefreshPlan:
+    """Gather plan of the ghost refresh for one mesh.
+
+    For a ghost cell of a leaf at level L, with global level-L cell index X
+    after the boundary rule, the value is that of the level-L cell X:
+      * covered by a level-L leaf: copy;
+      * covered by level-L+1 leaves: restriction, the mean of its 8 children
+        summed in (dz, dy, dx) lexicographic order, times 0.125;
+      * covered by a level-L-1 leaf: conservative linear prolongation of the
+        parent cell C: U_f = U_C + 0.25*((sx*Dx + sy*Dy) + sz*Dz) with
+        s = +1 for the upper child, D_d = minmod(U_C - U_C-e_d, U_C+e_d - U_C);
+        the level-L-1 neighbours C+-e_d (boundary rule at level L-1) are copied
+        from a level-L-1 leaf, restricted from level-L leaves or injected from
+        the level-L-2 leaf that covers them.
+    The sources are always leaf interiors, so the refresh has no ordering."""
+
+    def __init__(self, mesh: Mesh):
+        d = mesh.desc
+        n, g = d.n, d.ghosts
+        N = n + 2 * g
+        self.N3 = N ** 3
+        maps = mesh.maps()
+        zz, yy, xx = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+        inner = ((xx >= g) & (xx < g + n) & (yy >= g) & (yy < g + n) & (zz >= g) & (zz < g + n))
+        gz, gy, gx = zz[~inner], yy[~inner], xx[~inner]
+        gcell = (gz * N + gy) * N + gx
+        N3 = self.N3
+
+        def flat(b, z, y, x):
+            return b * 5 * N3 + (z * N + y) * N + x
+
+        def leaf_at(M, X, Y, Z):
+            return maps[M][Z // n, Y // n, X // n]
+
+        copy_d, copy_s = [], []
+        rst_d, rst_s = [], []
+        pro_d, pro_c, pro_sg, pro_nb, pro_mode = [], [], [], [], []
+
+        def restrict_src(M, X, Y, Z):
+            """8 children (level M+1) of level-M cells, order (dz, dy, dx)."""
+            srcs = []
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        x2, y2, z2 = 2 * X + dx, 2 * Y + dy, 2 * Z + dz
+                        f = leaf_at(M + 1, x2, y2, z2)
+                        assert (f >= 0).all()
+                        srcs.append(flat(f, z2 % n + g, y2 % n + g, x2 % n + g))
+            return np.stack(srcs, -1)
+
+        def value0(M, X, Y, Z):
+            """Sources of level-M cells for prolongation slopes:
+            returns (idx[k, 8], mode[k]) mode 0 single source, 1 mean of 8."""
+            m = leaf_at(M, X, Y, Z)
+            idx = np.zeros(X.shape + (8,), dtype=np.int64)
+            mode = np.zeros(X.shape, dtype=np.int64)
+            s = m >= 0
+            idx[s, 0] = flat(m[s], Z[s] % n + g, Y[s] % n + g, X[s] % n + g)
+            f = m == -1
+            if f.any():
+                idx[f] = restrict_src(M, X[f], Y[f], Z[f])
+                mode[f] = 1
+            c = m == -2
+            if c.any():
+                Xc, Yc, Zc = X[c] // 2, Y[c] // 2, Z[c] // 2
+                cc = leaf_at(M - 1, Xc, Yc, Zc)
+                assert (cc >= 0).all()
+                idx[c, 0] = flat(cc, Zc % n + g, Yc % n + g, Xc % n + g)
+            return idx, mode
+
+        for b, (L, bi, bj, bk) in enumerate(mesh.leaves):
+            L, bi, bj, bk = int(L), int(bi), int(bj), int(bk)
+            X = _bc(mesh, L, 0, bi * n + gx - g)
+            Y = _bc(mesh, L, 1, bj * n + gy - g)
+            Z = _bc(mesh, L, 2, bk * n + gz - g)
+            dst = b * 5 * N3 + gcell
+            m = leaf_at(L, X, Y, Z)
+            s = m >= 0
+            copy_d.append(dst[s])
+            copy_s.append(flat(m[s], Z[s] % n + g, Y[s] % n + g, X[s] % n + g))
+            f = m == -1
+            if f.any():
+                rst_d.append(dst[f])
+                rst_s.append(restrict_src(L, X[f], Y[f], Z[f]))
+            c = m == -2
+            if c.any():
+                Xf, Yf, Zf = X[c], Y[c], Z[c]
+                Xc, Yc, Zc = Xf // 2, Yf // 2, Zf // 2
+                cc = leaf_at(L - 1, Xc, Yc, Zc)
+                assert (cc >= 0).all()
+                pro_d.append(dst[c])
+                pro_c.append(flat(cc, Zc % n + g, Yc % n + g, Xc % n + g))
+                pro_sg.append(np.stack([np.where(Xf % 2 == 1, 1.0, -1.0),
+                                        np.where(Yf % 2 == 1, 1.0, -1.0),
+                                        np.where(Zf % 2 == 1, 1.0, -1.0)], -1))
+                nbi, nbm = [], []
+                for ax in range(3):
+                    for sgn in (-1, 1):
+                        P = [Xc, Yc, Zc]
+                        P[ax] = _bc(mesh, L - 1, ax, P[ax] + sgn)
+                        i8, md = value0(L - 1, *P)
+                        nbi.append(i8)
+                        nbm.append(md)
+                pro_nb.append(np.stack(nbi, 1))
+                pro_mode.append(np.stack(nbm, 1))
+
+        cat = lambda xs, shape: (torch.from_numpy(np.concatenate(xs)) if xs
+                                 else torch.zeros(shape, dtype=torch.int64))
+        self.copy_d, self.copy_s = cat(copy_d, (0,)), cat(copy_s, (0,))
+        self.rst_d, self.rst_s = cat(rst_d, (0,)), cat(rst_s, (0, 8))
+        self.pro_d, self.pro_c = cat(pro_d, (0,)), cat(pro_c, (0,))
+        self.pro_sg = (torch.from_numpy(np.concatenate(pro_sg)) if pro_sg
+                       else torch.zeros((0, 3), dtype=torch.float64))
+        self.pro_nb, self.pro_mode = cat(pro_nb, (0, 6, 8)), cat(pro_mode, (0, 6))
+
+    def apply(self, U):
+        shape = U.shape
+        Uf = U.reshape(-1)
+        out = Uf.clone()
+        fo = (torch.arange(5, dtype=torch.int64) * self.N3).view(5, 1)
+
+        def gather(idx):            # idx [k] -> [5, k]
+            return Uf[idx.view(1, -1) + fo]
+
+        def restrict(idx8):         # idx8 [k, 8] -> [5, k]
+            v = gather(idx8[:, 0])
+            for t in range(1, 8):
+                v = v + gather(idx8[:, t])
+            return v * 0.125
+
+        if self.copy_d.numel():
+            out[self.copy_d.view(1, -1) + fo] = gather(self.copy_s)
+        if self.rst_d.numel():
+            out[self.rst_d.view(1, -1) + fo] = restrict(self.rst_s)
+        if self.pro_d.numel():
+            Uc = gather(self.pro_c)
+            nb = []
+            for e in range(6):
+                single = gather(self.pro_nb[:, e, 0])
+                mean = restrict(self.pro_nb[:, e, :])
+                nb.append(torch.where(self.pro_mode[:, e].view(1, -1) == 1, mean, single))
+            D = [minmod(Uc - nb[2 * ax], nb[2 * ax + 1] - Uc) for ax in range(3)]
+            sg = self.pro_sg.t().unsqueeze(1)       # [3, 1, k]
+            Uf_new = Uc + 0.25 * ((sg[0] * D[0] + sg[1] * D[1]) + sg[2] * D[2])
+            out[self.pro_d.view(1, -1) + fo] = Uf_new
+        return out.view(shape)
+
+
+def minmod(a, b):
+    return torch.where(a * b > 0.0, torch.where(torch.abs(a) <= torch.abs(b), a, b), torch.zeros_like(a))
+
+
+def ghost_refresh(U, mesh: Mesh, plan: RefreshPlan | None = None):
+    return (plan or RefreshPlan(mesh)).apply(U)
+
+
+# ---------------------------------------------------------- flux correction
+FACE_ORDER = [(0, -1), (0, 1), (1, -1), (1, 1), (2, -1), (2, 1)]
+
+
+def coarse_fine_faces(mesh: Mesh):
+    """(coarse leaf, axis, side, [(fine leaf, o1, o2) x4]) for every face of a
+    leaf whose same-level neighbour node is refined; o1, o2 are the child
+    octant bits along the two transverse axes (t1 < t2)."""
+    maps = mesh.maps()
+    out = []
+    for b, (L, i, j, k) in enumerate(mesh.leaves):
+        L, i, j, k = int(L), int(i), int(j), int(k)
+        for axis, side in FACE_ORDER:
+            off = [0, 0, 0]
+            off[axis] = side
+            ni, nj, nk = (mesh.wrap(L, 0, i + off[0]), mesh.wrap(L, 1, j + off[1]),
+                          mesh.wrap(L, 2, k + off[2]))
+            if ni is None or nj is None or nk is None or maps[L][nk, nj, ni] != -1:
+                continue
+            t = [a for a in range(3) if a != axis]
+            kids = []
+            for o1 in (0, 1):
+                for o2 in (0, 1):
+                    o = [0, 0, 0]
+                    o[axis] = 1 if side < 0 else 0
+                    o[t[0]], o[t[1]] = o1, o2
+                    f = int(maps[L + 1][2 * nk + o[2], 2 * nj + o[1], 2 * ni + o[0]])
+                    assert f >= 0
+                    kids.append((f, o1, o2))
+            out.append((b, axis, side, kids))
+    return out
+
+
+def flux_correct(U, mesh: Mesh, faces, dt: float, cf=None):
+    """Replace the coarse flux at every coarse-fine face by the mean of the
+    four fine fluxes over it (one global dt, no subcycling):
+    U_c += s*(dt/dx_c)*(F_c - 0.25*((F00 + F10) + (F01 + F11))), s = +1 on
+    the coarse cell's high face, -1 on its low face, faces in the order
+    -x, +x, -y, +y, -z, +z."""
+    d = mesh.desc
+    n, g = d.n, d.ghosts
+    h = n // 2
+    cf = coarse_fine_faces(mesh) if cf is None else cf
+    if not cf:
+        return U
+    U = U.clone()
+    dxs = dx_of_leaves(mesh)
+    for b, axis, side, kids in cf:
+        dtdx = dt / float(dxs[b])
+        Fc = faces[axis][1 if side > 0 else 0][b]            # [5, n(t2), n(t1)]
+        for f, o1, o2 in kids:
+            Ff = faces[axis][0 if side > 0 else 1][f]       # fine leaf, opposite face
+            F00 = Ff[:, 0::2, 0::2]
+            F10 = Ff[:, 0::2, 1::2]
+            F01 = Ff[:, 1::2, 0::2]
+            F11 = Ff[:, 1::2, 1::2]
+            mean = ((F00 + F10) + (F01 + F11)) * 0.25       # [5, h(t2), h(t1)]
+            sl2 = slice(o2 * h, (o2 + 1) * h)
+            sl1 = slice(o1 * h, (o1 + 1) * h)
+            corr = (dtdx * (Fc[:, sl2, sl1] - mean)) * float(side)
+            cell = g + n - 1 if side > 0 else g
+            t1, t2 = [a for a in range(3) if a != axis]
+            idx = [slice(None)] * 5
+            idx[0] = b
+            idx[AXIS_DIM[axis]] = cell
+            idx[AXIS_DIM[t1]] = slice(g + o1 * h, g + (o1 + 1) * h)
+            idx[AXIS_DIM[t2]] = slice(g + o2 * h, g + (o2 + 1) * h)
+            U[tuple(idx)] = U[tuple(idx)] + corr
+    return U
+
+
+# ------------------------------------------------------ reductions and step
+def lab_primitives(U, gamma):
+    rho = torch.clamp_min(U[:, 0], RHO_FLOOR)
+    u, v, w = U[:, 1] / rho, U[:, 2] / rho, U[:, 3] / rho
+    ke = (0.5 * rho) * (u * u + (v * v + w * w))
+    p = torch.clamp_min((gamma - 1.0) * (U[:, 4] - ke), P_FLOOR)
+    return rho, u, v, w, p
+
+
+def reduce_dt_totals(U, mesh: Mesh, cfl: float):
+    """dt = cfl * min over leaf interior cells of dx_L / (max(|u|,|v|,|w|) + c),
+    c = sqrt(gamma*p/rho); totals = sum over leaves of dx_L^3 * sum of U."""
+    d = mesh.desc
+    n, g = d.n, d.ghosts
+    I = U[:, :, g:g + n, g:g + n, g:g + n]
+    rho, u, v, w, p = lab_primitives(I, d.gamma)
+    c = torch.sqrt((d.gamma * p) / rho)
+    s = torch.maximum(torch.abs(u), torch.maximum(torch.abs(v), torch.abs(w))) + c
+    dx = dx_of_leaves(mesh).view(-1, 1, 1, 1)
+    dt = cfl * float(torch.min(dx / s))
+    vol = dx.view(-1) ** 3
+    totals = (I.sum(dim=(2, 3, 4)) * vol.view(-1, 1)).sum(0)
+    return dt, totals
+
+
+def step(U, mesh: Mesh, dt: float, cycle: int, plan: RefreshPlan | None = None,
+         flux_correction: bool = True, cf=None):
+    """One hydro step: ghost refresh, three split PPM sweeps, coarse-fine flux
+    correction.  dt is given (the caller takes it from reduce_dt_totals or
+    from a fixed sequence)."""
+    U = ghost_refresh(U, mesh, plan)
+    faces = {}
+    swept = set()
+    for axis in sweep_order(cycle):
+        U, faces[axis] = sweep(U, mesh, axis, dt, transverse_rows(mesh, axis, swept))
+        swept.add(axis)
+    if flux_correction:
+        U = flux_correct(U, mesh, faces, dt, cf)
+    return U
+
+
+def run(U, mesh: Mesh, steps: int, cfl: float, dts=None, cycle0: int = 0):
+    """Advance `steps` steps; dt from the CFL reduction of the state at the
+    start of each step unless a fixed sequence dts is given.  Returns
+    (U, list of dt used)."""
+    plan = RefreshPlan(mesh)
+    cf = coarse_fine_faces(mesh)
+    used = []
+    for s in range(steps):
+        dt = float(dts[s]) if dts is not None else reduce_dt_totals(U, mesh, cfl)[0]
+        U = step(U, mesh, dt, cycle0 + s, plan, cf=cf)
+        used.append(dt)
+    return U, used
+
+
+# ------------------------------------------------------------ refine flags
+def refine_flags(U, mesh: Mesh, field: int, tau: float, tau_c: float):
+    """Per-leaf flag from the relative-slope criterion on density (field 0) or
+    pressure (field 4), compared in float64 on cells of the (ghost-refreshed)
+    leaf interior: a cell passes on axis d if |q(i+e_d) - q(i-e_d)| >
+    (2*tau)*|q(i)|.  +1 if any cell passes and L < max_level; -1 if none
+    passes with tau_c and L > 0; 0 otherwise."""
+    d = mesh.desc
+    n, g = d.n, d.ghosts
+    Ud = U.to(torch.float64)
+    if field == 0:
+        q = torch.clamp_min(Ud[:, 0], RHO_FLOOR)
+    else:
+        q = lab_primitives(Ud, d.gamma)[4]
+    thr, thr_c = 2.0 * tau, 2.0 * tau_c
+    c = q[:, g:g + n, g:g + n, g:g + n]
+    hit = torch.zeros(U.shape[0], dtype=torch.bool)
+    hit_c = torch.zeros(U.shape[0], dtype=torch.bool)
+    for axis in range(3):
+        lo = [slice(None), slice(g, g + n), slice(g, g + n), slice(g, g + n)]
+        hi = list(lo)
+        dim = 3 - axis
+        lo[dim] = slice(g - 1, g + n - 1)
+        hi[dim] = slice(g + 1, g + n + 1)
+        diff = torch.abs(q[tuple(hi)] - q[tuple(lo)])
+        hit |= (diff > thr * torch.abs(c)).flatten(1).any(1)
+        hit_c |= (diff > thr_c * torch.abs(c)).flatten(1).any(1)
+    L = torch.from_numpy(mesh.leaves[:, 0])
+    flags = torch.zeros(U.shape[0], dtype=torch.int8)
+    flags[(~hit_c) & (L > 0)] = -1
+    flags[hit & (L < d.max_level)] = 1
+    return flags
