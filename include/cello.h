@@ -1,0 +1,153 @@
+/* cello.h - C ABI of the GB300 hydro hot path of the Enzo-P/Cello method
+ * (Bordner & Norman, arXiv:1810.01319).
+ *
+ * One leaf Block of the array-of-octrees mesh (Sec. II.B) holds n^3 cells
+ * plus a ghost layer of depth g on every side; the hydro Method is a
+ * directionally split piecewise parabolic method (Sec. II.C).  This library
+ * builds the leaf table, computes refinement flags, refreshes ghost zones
+ * (same-level copy, restriction, prolongation, physical boundaries) and
+ * advances the PPM step with coarse-fine flux correction and the CFL
+ * reduction, all on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - Field pool: caller-owned device memory, U[leaf][field][z][y][x], five
+ *    conserved fields (rho, rho*u, rho*v, rho*w, E) per leaf, each a padded
+ *    cube of N = n + 2g cells per edge (x fastest), element type float
+ *    (precision 4) or double (precision 8), base 256-byte aligned.  Leaves
+ *    are in the mesh's Morton order (see cello_mesh_leaves).  The library
+ *    never frees it.
+ *  - Streams: every device call is enqueued on the given cudaStream_t
+ *    (passed as void*, NULL = legacy default stream) and returns without
+ *    synchronising.  dt, totals and flags stay on the device.
+ *  - Errors: every call returns a cello_status and never aborts; the text of
+ *    the last error of the calling thread is in cello_last_error().
+ *  - A cello_mesh is not thread-safe; use one per host thread.
+ */
+#ifndef CELLO_H
+#define CELLO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cello_mesh cello_mesh;
+
+typedef enum {
+    CELLO_OK = 0,
+    CELLO_EINVAL = 1,     /* bad argument or unsupported size */
+    CELLO_ENOMEM = 2,     /* device or host allocation failed */
+    CELLO_ECUDA = 3,      /* a CUDA runtime call failed */
+    CELLO_ENONFINITE = 4, /* reserved: non-finite state detected */
+    CELLO_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    CELLO_EINTERNAL = 6   /* broken invariant (e.g. 2:1 balance) */
+} cello_status;
+
+enum { CELLO_PERIODIC = 0, CELLO_OUTFLOW = 1 };
+
+/* Mesh description.  Sec. II.B: an array of root octrees (root[3] per axis)
+ * over the box [lo, hi]; cells must be cubes.  n in {8, 16, 32} cells per
+ * block edge, ghosts = 4 (the PPM stencil reaches four cells), max_level
+ * <= 10, bc per axis (both faces of an axis share it), precision 4 or 8,
+ * gamma the ideal-gas ratio of specific heats. */
+typedef struct {
+    int root[3];
+    int n;
+    int ghosts;
+    int max_level;
+    double lo[3];
+    double hi[3];
+    int bc[3];
+    int precision;
+    double gamma;
+} cello_mesh_desc;
+
+/* Build a mesh (Sec. II.B, array of octrees; Refine drives adaptation).
+ * prev == NULL: the root array, every leaf at level 0.  Otherwise the new
+ * leaf set is derived from prev and flags_host (host int8, one per leaf of
+ * prev: +1 refine, 0 keep, -1 coarsen candidate): refine +1 leaves below
+ * max_level; replace a complete octet of -1 sibling leaves by their parent
+ * where that parent would touch no leaf two levels finer; then refine every
+ * leaf touching a leaf two or more levels finer (faces, edges, corners,
+ * periodic images) until none does.  Leaves are sorted by the Morton key of
+ * their lower corner at max_level.  The 27-entry neighbour table is then
+ * computed on the device.  *out receives a new mesh owned by the caller
+ * (free with cello_mesh_free). */
+cello_status cello_octree_build(const cello_mesh_desc* desc, const cello_mesh* prev,
+                                const int8_t* flags_host, cello_mesh** out);
+
+void cello_mesh_free(cello_mesh* mesh);
+
+/* Sizes: leaves, elements per leaf (5 * N^3), coarse-fine faces. */
+cello_status cello_mesh_info(const cello_mesh* mesh, int64_t* n_leaves, int64_t* leaf_elems,
+                             int64_t* n_coarse_fine_faces);
+
+/* Host copy of the leaf list: leaves_host[b*4 + {0,1,2,3}] = (level, i, j, k),
+ * i in [0, root[0] << level). */
+cello_status cello_mesh_leaves(const cello_mesh* mesh, int32_t* leaves_host);
+
+/* Host copy of the device neighbour table (Sec. II.B: ghost data comes from
+ * neighbouring Blocks).  27 entries per leaf, entry (dz+1)*9+(dy+1)*3+(dx+1):
+ * kind 0 same-level leaf (idx), 1 coarser leaf containing the neighbour node
+ * (idx), 2 refined neighbour node (fine8[8], children in octant order
+ * oz*4+oy*2+ox, -1 for a child that is not a leaf), 3 outside an outflow
+ * boundary.  Periodic axes wrap.  Any pointer may be NULL. */
+cello_status cello_neighbour_table(const cello_mesh* mesh, int8_t* kind_host, int32_t* idx_host,
+                                   int32_t* fine8_host);
+
+/* Refinement flags (Sec. II.B, Refine), one int8 per leaf into flags_dev:
+ * on density (field 0) or pressure (field 4), computed in float64 from the
+ * stored values with ghost zones already refreshed; a cell passes on axis d
+ * if |q(i+e_d) - q(i-e_d)| > (2*tau)*|q(i)|.  +1 if any interior cell
+ * passes and level < max_level; -1 if none passes with tau_coarsen and
+ * level > 0; else 0. */
+cello_status cello_refine_flags(cello_mesh* mesh, const void* U, int field, double tau,
+                                double tau_coarsen, int8_t* flags_dev, void* stream);
+
+/* Ghost refresh (Sec. II.B, Fig. 4; Restrict and Prolong): every ghost cell
+ * of every leaf takes the value of the cell at its own level and position
+ * after the physical boundary rule (periodic wrap, outflow clamp to the
+ * nearest interior cell): copied from a same-level leaf, restricted (mean of
+ * 8, fixed order) from finer leaves, or prolonged (conservative
+ * minmod-limited linear) from the coarser leaf.  Reads leaf interiors only,
+ * writes ghost cells only. */
+cello_status cello_ghost_refresh(cello_mesh* mesh, void* U, void* stream);
+
+/* One hydro step (Sec. II.C, PPM) on every leaf: ghost refresh, three split
+ * PPM sweeps (x,y,z for even cycle, z,y,x for odd) with the two-shock Riemann
+ * flux, then coarse-fine flux correction in float64.  dt_dev: device double,
+ * the step's dt.  Afterwards dt_next_dev (device double, may be NULL) =
+ * cfl * min over leaf cells of dx/(max|u_d| + c), and totals_dev (device
+ * double[5], may be NULL) = float64 sums of each conserved field times cell
+ * volume over leaf interiors. */
+cello_status cello_hydro_step(cello_mesh* mesh, void* U, const double* dt_dev, int cycle, double cfl,
+                              double* dt_next_dev, double* totals_dev, void* stream);
+
+/* The CFL dt and conserved totals of the current state (as after a step). */
+cello_status cello_reduce(cello_mesh* mesh, const void* U, double cfl, double* dt_next_dev,
+                          double* totals_dev, void* stream);
+
+/* Execution mode of cello_hydro_step: CELLO_EXEC_PLAIN launches each phase
+ * once per leaf (the per-Block Method calls of Sec. II.B); CELLO_EXEC_BATCHED
+ * launches each phase once over all leaves; CELLO_EXEC_GRAPH replays the
+ * batched step from a CUDA graph captured on first use. */
+enum { CELLO_EXEC_PLAIN = 0, CELLO_EXEC_BATCHED = 1, CELLO_EXEC_GRAPH = 2 };
+cello_status cello_set_exec(cello_mesh* mesh, int mode);
+
+/* One batched step (as cello_hydro_step, without dt_next/totals) with CUDA
+ * events recorded between its phases; blocks until it completes and writes
+ * the device time of each phase in milliseconds to phase_ms_host[6]:
+ * ghost refresh, sweep 1, sweep 2, sweep 3, flux correction, reduction
+ * (the reduction of dt and totals is run and timed as well). */
+cello_status cello_profile_step(cello_mesh* mesh, void* U, const double* dt_dev, int cycle, double cfl,
+                                float* phase_ms_host, void* stream);
+
+/* Text of the calling thread's last error ("" if none). */
+const char* cello_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELLO_H */

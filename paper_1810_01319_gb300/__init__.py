@@ -1,0 +1,131 @@
+"""GB300-native hydro hot path of the Enzo-P/Cello method (arXiv:1810.01319).
+
+Sec. II.B: an array-of-octrees mesh whose leaf Blocks carry the fields and a
+ghost layer refreshed from neighbouring Blocks; Sec. II.C: a PPM hydro
+Method.  The work runs in libcello_gpu.so (hand-written sm_103a CUDA); this
+package only marshals arguments.  PyTorch supplies device memory and
+streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import EXEC_BATCHED, EXEC_GRAPH, EXEC_PLAIN, OUTFLOW, PERIODIC, CelloError  # noqa: F401
+
+__all__ = ["Mesh", "make_desc", "PERIODIC", "OUTFLOW", "EXEC_PLAIN", "EXEC_BATCHED", "EXEC_GRAPH", "CelloError"]
+
+
+def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3,
+              precision=8, gamma=1.4, ghosts=4) -> _lib.MeshDesc:
+    d = _lib.MeshDesc()
+    d.root[:] = list(root)
+    d.n, d.ghosts, d.max_level = n, ghosts, max_level
+    d.lo[:] = [float(v) for v in lo]
+    d.hi[:] = [float(v) for v in hi]
+    d.bc[:] = list(bc)
+    d.precision = precision
+    d.gamma = float(gamma)
+    return d
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Mesh:
+    """A leaf table built by cello_octree_build; owns the C handle."""
+
+    def __init__(self, desc: _lib.MeshDesc, prev: "Mesh | None" = None, flags=None):
+        L = _lib.lib()
+        self.desc = desc
+        out = ctypes.c_void_p()
+        fl = None
+        if flags is not None:
+            fl = np.ascontiguousarray(np.asarray(flags, dtype=np.int8))
+            assert prev is not None and len(fl) == prev.n_leaves
+        _lib.check(L.cello_octree_build(ctypes.byref(desc), prev.handle if prev else None,
+                                        fl.ctypes.data_as(ctypes.c_void_p) if fl is not None else None,
+                                        ctypes.byref(out)), "cello_octree_build")
+        self.handle = out
+        nl, le, ncf = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _lib.check(L.cello_mesh_info(out, ctypes.byref(nl), ctypes.byref(le), ctypes.byref(ncf)), "cello_mesh_info")
+        self.n_leaves, self.leaf_elems, self.n_coarse_fine = nl.value, le.value, ncf.value
+        self.N = desc.n + 2 * desc.ghosts
+        self.dtype = torch.float32 if desc.precision == 4 else torch.float64
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.lib().cello_mesh_free(h)
+            self.handle = None
+
+    # ------------------------------------------------------------- queries
+    @property
+    def leaves(self) -> np.ndarray:
+        out = np.zeros((self.n_leaves, 4), dtype=np.int32)
+        _lib.check(_lib.lib().cello_mesh_leaves(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "cello_mesh_leaves")
+        return out
+
+    def neighbour_table(self):
+        B = self.n_leaves
+        kind = np.zeros((B, 27), np.int8)
+        idx = np.zeros((B, 27), np.int32)
+        fine8 = np.zeros((B, 27, 8), np.int32)
+        _lib.check(_lib.lib().cello_neighbour_table(self.handle, kind.ctypes.data_as(ctypes.c_void_p),
+                                                    idx.ctypes.data_as(ctypes.c_void_p),
+                                                    fine8.ctypes.data_as(ctypes.c_void_p)), "cello_neighbour_table")
+        return kind, idx, fine8
+
+    def empty_state(self, device="cuda"):
+        return torch.empty((self.n_leaves, 5, self.N, self.N, self.N), dtype=self.dtype, device=device)
+
+    def _check_state(self, U):
+        if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous()
+                and U.numel() >= self.n_leaves * self.leaf_elems):
+            raise CelloError("state must be a contiguous CUDA tensor of the mesh's dtype and size")
+
+    # ------------------------------------------------------------- compute
+    def refine_flags(self, U, field=0, tau=0.3, tau_c=0.075, flags=None, stream=None):
+        self._check_state(U)
+        if flags is None:
+            flags = torch.empty(self.n_leaves, dtype=torch.int8, device=U.device)
+        _lib.check(_lib.lib().cello_refine_flags(self.handle, _ptr(U), field, tau, tau_c, _ptr(flags),
+                                                 _stream(stream)), "cello_refine_flags")
+        return flags
+
+    def ghost_refresh(self, U, stream=None):
+        self._check_state(U)
+        _lib.check(_lib.lib().cello_ghost_refresh(self.handle, _ptr(U), _stream(stream)), "cello_ghost_refresh")
+
+    def hydro_step(self, U, dt, cycle, cfl=0.4, dt_next=None, totals=None, stream=None):
+        """dt, dt_next: float64 CUDA tensors of one element; totals: five."""
+        self._check_state(U)
+        _lib.check(_lib.lib().cello_hydro_step(self.handle, _ptr(U), _ptr(dt), int(cycle), float(cfl),
+                                               _ptr(dt_next), _ptr(totals), _stream(stream)), "cello_hydro_step")
+
+    def reduce(self, U, cfl=0.4, dt_next=None, totals=None, stream=None):
+        self._check_state(U)
+        _lib.check(_lib.lib().cello_reduce(self.handle, _ptr(U), float(cfl), _ptr(dt_next), _ptr(totals),
+                                           _stream(stream)), "cello_reduce")
+
+    def profile_step(self, U, dt, cycle, cfl=0.4, stream=None):
+        """Device milliseconds of each phase of one batched step: refresh,
+        sweep 1, 2, 3, flux correction, reduction.  Advances U by one step."""
+        self._check_state(U)
+        out = (ctypes.c_float * 6)()
+        _lib.check(_lib.lib().cello_profile_step(self.handle, _ptr(U), _ptr(dt), int(cycle), float(cfl),
+                                                 ctypes.cast(out, ctypes.c_void_p), _stream(stream)),
+                   "cello_profile_step")
+        return list(out)
+
+    def set_exec(self, mode: int):
+        _lib.check(_lib.lib().cello_set_exec(self.handle, int(mode)), "cello_set_exec")

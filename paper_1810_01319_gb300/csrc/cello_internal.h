@@ -1,0 +1,81 @@
+// Internal types shared by the host orchestration and the kernel translation
+// units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cello {
+
+constexpr int kGhosts = 4;
+constexpr int kFields = 5;
+constexpr int kPencilsPerTile = 8;   // pencils per sweep CTA
+
+// Neighbour kinds of the 27-entry table.
+enum NbKind : int8_t { kSame = 0, kCoarse = 1, kFine = 2, kBoundary = 3 };
+
+// Read-only view of the device-resident block table.
+struct DevMesh {
+  int n, g, N;            // cells per block edge, ghosts, padded edge
+  int max_level;
+  int root[3];
+  int bc[3];              // 0 periodic, 1 outflow
+  double dx0;             // cell width at level 0
+  double gamma;
+  int B;                  // leaves
+  const int4* leaf;       // (level, i, j, k)
+  const int8_t* kind;     // [B][27]
+  const int* idx;         // [B][27]
+  const int* fine8;       // [B][27][8]
+  const int* face_slot;   // [B][6] flux-register slot of each face or -1
+};
+
+// Face order used by registers and corrections: -x, +x, -y, +y, -z, +z.
+__host__ __device__ inline int face_dir(int axis, int side) {
+  int d[3] = {0, 0, 0};
+  d[axis] = side;
+  return (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
+}
+
+// One coarse face that touches four finer leaves.
+struct CoarseFace {
+  int leaf;       // coarse leaf
+  int axis, side; // face
+  int cslot;      // register slot of the coarse flux
+  int fslot[4];   // register slots of the fine fluxes, index o2*2 + o1
+};
+
+struct SweepParams {
+  void* U;
+  int leaf0, nleaf;        // leaves [leaf0, leaf0 + nleaf)
+  int axis;
+  int a0, a1, b0, b1;      // transverse ranges (padded coordinates)
+  int tiles_per_leaf;
+  const double* dt;        // device scalar
+  double* reg;             // flux registers (may be null)
+  unsigned* work;          // persistent work counter (null: static schedule)
+  int n_items;
+};
+
+// One-time kernel attribute set-up (dynamic shared memory limits), done
+// outside any stream capture.
+void prepare_kernels();
+void prepare_kernels_f32();
+void prepare_kernels_f64();
+
+// Launchers (defined in the kernel translation units).
+void launch_neighbour_table(const DevMesh& m, const unsigned long long* keys, int8_t* kind, int* idx,
+                            int* fine8, cudaStream_t s);
+void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, cudaStream_t s);
+void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, cudaStream_t s);
+void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
+void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
+void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces,
+                     const int* group_start, int ngroups, const double* reg, const double* dt,
+                     cudaStream_t s);
+void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
+                   double* dt_next, double* totals, cudaStream_t s);
+void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
+                  int8_t* flags, cudaStream_t s);
+
+}  // namespace cello

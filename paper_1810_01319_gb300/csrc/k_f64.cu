@@ -1,0 +1,116 @@
+// Float64 sweep and the precision-generic kernels (refresh, reductions,
+// flags, flux correction).  Built without FMA contraction so that float64
+// results round exactly like the same formulas evaluated term by term.
+#define CELLO_DEFINE_FINISH_KERNEL
+#include "kernels.cuh"
+
+namespace cello {
+
+template <int NB, int P>
+static void sweep_f64_n(const DevMesh& m, const SweepParams& p, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  const size_t smem = sizeof(double) * 21 * N * (P + 1);
+  auto k = sweep_kernel<double, NB, P>;
+  k<<<p.n_items, N * P, smem, s>>>(m, p);
+}
+
+template <int NB, int P>
+static void prepare_n() {
+  constexpr int N = NB + 2 * kGhosts;
+  cudaFuncSetAttribute(sweep_kernel<double, NB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(double) * 21 * N * (P + 1)));
+}
+
+void prepare_kernels_f64() {
+  prepare_n<8, kPencilsPerTile>();
+  prepare_n<16, kPencilsPerTile>();
+  prepare_n<32, kPencilsPerTile>();
+}
+
+void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
+  (void)pencils;
+  if (p.n_items <= 0) return;
+  switch (m.n) {
+    case 8: sweep_f64_n<8, kPencilsPerTile>(m, p, s); break;
+    case 16: sweep_f64_n<16, kPencilsPerTile>(m, p, s); break;
+    case 32: sweep_f64_n<32, kPencilsPerTile>(m, p, s); break;
+  }
+}
+
+template <typename T, int NB>
+static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  constexpr long NG = (long)N * N * N - (long)NB * NB * NB;
+  const long threads = NG * nleaf;
+  if (threads <= 0) return;
+  refresh_kernel<T, NB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, U, leaf0, nleaf);
+}
+
+template <typename T>
+static void refresh_t(const DevMesh& m, T* U, int leaf0, int nleaf, cudaStream_t s) {
+  switch (m.n) {
+    case 8: refresh_n<T, 8>(m, U, leaf0, nleaf, s); break;
+    case 16: refresh_n<T, 16>(m, U, leaf0, nleaf, s); break;
+    case 32: refresh_n<T, 32>(m, U, leaf0, nleaf, s); break;
+  }
+}
+
+void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, cudaStream_t s) {
+  refresh_t<float>(m, U, leaf0, nleaf, s);
+}
+void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, cudaStream_t s) {
+  refresh_t<double>(m, U, leaf0, nleaf, s);
+}
+
+template <typename T, int NB>
+static void reduce_n(const DevMesh& m, const void* U, double* partials, cudaStream_t s) {
+  reduce_partials_kernel<T, NB><<<m.B, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials);
+}
+
+void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
+                   double* dt_next, double* totals, cudaStream_t s) {
+  if (m.B <= 0) return;
+#define CELLO_RED(T)                                            \
+  switch (m.n) {                                                \
+    case 8: reduce_n<T, 8>(m, U, partials, s); break;           \
+    case 16: reduce_n<T, 16>(m, U, partials, s); break;         \
+    case 32: reduce_n<T, 32>(m, U, partials, s); break;         \
+  }
+  if (precision == 4) { CELLO_RED(float) } else { CELLO_RED(double) }
+#undef CELLO_RED
+  reduce_finish_kernel<<<1, 1024, 0, s>>>(partials, m.B, cfl, dt_next, totals);
+}
+
+void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
+                  int8_t* flags, cudaStream_t s) {
+  if (m.B <= 0) return;
+  const double thr = 2.0 * tau, thr_c = 2.0 * tau_c;
+#define CELLO_FLG(T, NB) flags_kernel<T, NB><<<m.B, 256, 0, s>>>(m, static_cast<const T*>(U), field, thr, thr_c, flags)
+#define CELLO_FLG_T(T)                        \
+  switch (m.n) {                              \
+    case 8: CELLO_FLG(T, 8); break;           \
+    case 16: CELLO_FLG(T, 16); break;         \
+    case 32: CELLO_FLG(T, 32); break;         \
+  }
+  if (precision == 4) { CELLO_FLG_T(float) } else { CELLO_FLG_T(double) }
+#undef CELLO_FLG_T
+#undef CELLO_FLG
+}
+
+void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces, const int* group_start,
+                     int ngroups, const double* reg, const double* dt, cudaStream_t s) {
+  if (ngroups <= 0) return;
+#define CELLO_FC(T, NB) \
+  fluxcorr_kernel<T, NB><<<ngroups, 256, 0, s>>>(m, static_cast<T*>(U), faces, group_start, reg, dt)
+#define CELLO_FC_T(T)                       \
+  switch (m.n) {                            \
+    case 8: CELLO_FC(T, 8); break;          \
+    case 16: CELLO_FC(T, 16); break;        \
+    case 32: CELLO_FC(T, 32); break;        \
+  }
+  if (precision == 4) { CELLO_FC_T(float) } else { CELLO_FC_T(double) }
+#undef CELLO_FC_T
+#undef CELLO_FC
+}
+
+}  // namespace cello

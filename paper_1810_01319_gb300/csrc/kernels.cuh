@@ -1,0 +1,498 @@
+// Templated kernels of the hydro step.  Included by the per-precision
+// translation units, which fix the FMA policy (float64: no contraction).
+#pragma once
+
+#include "cello_internal.h"
+#include "ppm.cuh"
+
+namespace cello {
+
+__device__ __forceinline__ int wrap_mod(int v, int m) {
+  int r = v % m;
+  return r < 0 ? r + m : r;
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  return (a * b > T(0)) ? ((vabs(a) <= vabs(b)) ? a : b) : T(0);
+}
+
+// =====================================================================
+// Directional PPM sweep.  One CTA item = P pencils of one leaf; a thread
+// owns one cell of one pencil.  Shared arrays are [5][N][P+1] (pencil
+// fastest, padded against bank conflicts).  Phases:
+//   1 load + primitives  2 limited slopes, shock detector  3 interface
+//   values  4 flatten + monotone + trace  5 Riemann flux (+ face registers)
+//   6 conservative update of cells g..g+n-1.
+// =====================================================================
+template <typename T, int NB, int P>
+__global__ void __launch_bounds__((NB + 8) * P)
+sweep_kernel(DevMesh m, SweepParams prm) {
+  constexpr int G = kGhosts, N = NB + 2 * G, S = P + 1, A = N * S;
+  constexpr long SLAB = (long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sW = reinterpret_cast<T*>(smem_raw);
+  T* sA = sW + 5 * A;   // slopes, then left-edge states
+  T* sB = sA + 5 * A;   // interface values, then fluxes
+  T* sC = sB + 5 * A;   // right-edge states
+  T* sFT = sC + 5 * A;  // shock detector
+
+  const Gas<T> gs = Gas<T>::make(m.gamma);
+  T* U = static_cast<T*>(prm.U);
+  const int axis = prm.axis;
+  const int cA = prm.a1 - prm.a0, cB = prm.b1 - prm.b0;
+  const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
+  const long sTA = axis == 2 ? N : (long)N * N;   // transverse A: z (x, y sweeps) or y (z sweep)
+  const long sTB = axis == 0 ? N : 1;             // transverse B: y (x sweep) or x (y, z sweeps)
+  int comp[5];
+  comp[0] = 0; comp[1] = 1 + axis; comp[4] = 4;
+  comp[2] = axis == 0 ? 2 : 1;
+  comp[3] = axis == 2 ? 2 : 3;
+
+  const int t = threadIdx.x;
+  const int lc = axis == 0 ? t % N : t / P;   // load mapping: cell
+  const int lp = axis == 0 ? t / N : t % P;   //               pencil
+  const int cp = t % P, cj = t / P;           // compute mapping
+
+  for (int item = blockIdx.x; item < prm.n_items; item += gridDim.x) {
+    const int leaf = prm.leaf0 + item / prm.tiles_per_leaf;
+    const int tile = item % prm.tiles_per_leaf;
+    const int4 lf = m.leaf[leaf];
+    const double dtdx_d = *prm.dt / ldexp(m.dx0, -lf.x);
+    const T dtdx = T(dtdx_d);
+
+    // ---- phase 1
+    const int q = tile * P + lp;
+    const bool valid = q < cA * cB;
+    const int pa = prm.a0 + (valid ? q / cB : 0), pb = prm.b0 + (valid ? q % cB : 0);
+    T* base = U + (long)leaf * 5 * SLAB + pa * sTA + pb * sTB + lc * sAx;
+    T Uc[5];
+    if (valid) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) Uc[f] = base[f * SLAB];
+      T Us[5], W[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Us[k] = Uc[comp[k]];
+      to_primitive(Us, gs, W);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sW[k * A + lc * S + lp] = W[k];
+    }
+    __syncthreads();
+
+    const int j = cj, p = cp;
+    // ---- phase 2
+    if (j >= 1 && j <= N - 2) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const T* a = sW + k * A + p;
+        sA[k * A + j * S + p] = limited_slope(a[(j - 1) * S], a[j * S], a[(j + 1) * S]);
+      }
+    }
+    if (j >= 2 && j <= N - 3) {
+      const T* pr = sW + 4 * A + p;
+      const T* un = sW + 1 * A + p;
+      sFT[j * S + p] = flatten_tilde(pr[(j - 2) * S], pr[(j - 1) * S], pr[(j + 1) * S], pr[(j + 2) * S],
+                                     un[(j - 1) * S], un[(j + 1) * S]);
+    }
+    __syncthreads();
+    // ---- phase 3
+    if (j >= 1 && j <= N - 3) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        sB[k * A + j * S + p] = interface_value(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
+                                                sA[k * A + j * S + p], sA[k * A + (j + 1) * S + p]);
+    }
+    __syncthreads();
+    // ---- phase 4
+    if (j >= 3 && j <= N - 4) {
+      const T* pr = sW + 4 * A + p;
+      const T s = pr[(j + 1) * S] - pr[(j - 1) * S];
+      const T fj = sFT[j * S + p], fm = sFT[(j - 1) * S + p], fpp = sFT[(j + 1) * S + p];
+      const T f = (s > T(0)) ? vmax(fj, fm) : ((s < T(0)) ? vmax(fj, fpp) : fj);
+      T W[5], aL[5], aR[5], Wm[5], Wp[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        W[k] = sW[k * A + j * S + p];
+        aL[k] = sB[k * A + (j - 1) * S + p];
+        aR[k] = sB[k * A + j * S + p];
+        flatten_monotone(W[k], f, aL[k], aR[k]);
+      }
+      trace(W, aL, aR, dtdx, gs, Wm, Wp);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        sA[k * A + j * S + p] = Wm[k];
+        sC[k * A + j * S + p] = Wp[k];
+      }
+    }
+    __syncthreads();
+    // ---- phase 5
+    if (j >= 3 && j <= N - 5) {
+      T L[5], R[5], F[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        L[k] = sC[k * A + j * S + p];
+        R[k] = sA[k * A + (j + 1) * S + p];
+      }
+      riemann_flux(L, R, gs, F);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sB[k * A + j * S + p] = F[k];
+      if (prm.reg && (j == G - 1 || j == G + NB - 1)) {
+        const int qq = tile * P + p;
+        if (qq < cA * cB) {
+          const int ca = prm.a0 + qq / cB, cb = prm.b0 + qq % cB;
+          if (ca >= G && ca < G + NB && cb >= G && cb < G + NB) {
+            const int face = 2 * axis + (j == G - 1 ? 0 : 1);
+            const int slot = m.face_slot[leaf * 6 + face];
+            if (slot >= 0) {
+              double* r = prm.reg + (long)slot * 5 * NB * NB + (ca - G) * NB + (cb - G);
+#pragma unroll
+              for (int k = 0; k < 5; ++k) r[(long)comp[k] * NB * NB] = double(F[k]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // ---- phase 6
+    if (valid && lc >= G && lc < G + NB) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const T Fp = sB[k * A + lc * S + lp], Fm = sB[k * A + (lc - 1) * S + lp];
+        base[comp[k] * SLAB] = Uc[comp[k]] - dtdx * (Fp - Fm);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// =====================================================================
+// Ghost refresh: one thread per ghost cell of a leaf, all five fields.
+// =====================================================================
+template <int NB>
+__device__ __forceinline__ void ghost_coord(int q, int& x, int& y, int& z) {
+  constexpr int G = kGhosts, N = NB + 2 * G, plane = N * N, ring = N * N - NB * NB;
+  if (q < G * plane) {
+    z = q / plane; const int r = q % plane; y = r / N; x = r % N;
+  } else if (q < 2 * G * plane) {
+    q -= G * plane; z = G + NB + q / plane; const int r = q % plane; y = r / N; x = r % N;
+  } else {
+    q -= 2 * G * plane; z = G + q / ring; int r = q % ring;
+    if (r < G * N) {
+      y = r / N; x = r % N;
+    } else if (r < 2 * G * N) {
+      r -= G * N; y = G + NB + r / N; x = r % N;
+    } else {
+      r -= 2 * G * N; y = G + r / (2 * G); const int tt = r % (2 * G); x = tt < G ? tt : NB + tt;
+    }
+  }
+}
+
+// Mean of the 8 cells (fine padded coords f0 + {0,1}^3) of leaf `leaf`,
+// summed in (dz, dy, dx) order, times 0.125.
+template <typename T, int NB>
+__device__ __forceinline__ void restrict8(const T* U, int leaf, int fx, int fy, int fz, T out[5]) {
+  constexpr int N = NB + 2 * kGhosts;
+  constexpr long SLAB = (long)N * N * N;
+  const T* b = U + (long)leaf * 5 * SLAB + ((long)fz * N + fy) * N + fx;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    const T* c = b + f * SLAB;
+    T v = c[0];
+    v = v + c[1];
+    v = v + c[N];
+    v = v + c[N + 1];
+    v = v + c[N * N];
+    v = v + c[N * N + 1];
+    v = v + c[N * N + N];
+    v = v + c[N * N + N + 1];
+    out[f] = v * T(0.125);
+  }
+}
+
+template <typename T, int NB>
+__device__ __forceinline__ void load5(const T* U, int leaf, int x, int y, int z, T out[5]) {
+  constexpr int N = NB + 2 * kGhosts;
+  constexpr long SLAB = (long)N * N * N;
+  const T* b = U + (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) out[f] = b[f * SLAB];
+}
+
+// Value of the level-(L-1) cell r (local to the coarse leaf C, r[a] may be
+// -1 or NB on exactly one axis a) used as a prolongation slope neighbour:
+// C's own cell, a same-level copy, a restriction from level-L leaves, an
+// injection from the level-(L-2) leaf, or C's cell itself behind an outflow
+// boundary.
+template <typename T, int NB>
+__device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int rc[3], int a, int side,
+                                const T Uc[5], T out[5]) {
+  constexpr int G = kGhosts, H = NB / 2;
+  const int fe = face_dir(a, side);
+  const int e = C * 27 + fe;
+  const int8_t k = m.kind[e];
+  if (k == kBoundary) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) out[f] = Uc[f];
+    return;
+  }
+  int r2[3] = {rc[0], rc[1], rc[2]};
+  r2[a] = side < 0 ? NB - 1 : 0;   // position inside the neighbour node
+  if (k == kSame) {
+    load5<T, NB>(U, m.idx[e], r2[0] + G, r2[1] + G, r2[2] + G, out);
+  } else if (k == kFine) {
+    const int o0 = r2[0] / H, o1 = r2[1] / H, o2 = r2[2] / H;
+    const int child = m.fine8[e * 8 + o2 * 4 + o1 * 2 + o0];
+    restrict8<T, NB>(U, child, 2 * r2[0] - o0 * NB + G, 2 * r2[1] - o1 * NB + G, 2 * r2[2] - o2 * NB + G, out);
+  } else {  // coarser: inject the level-(L-2) cell
+    const int4 cl = m.leaf[C];
+    const int K = m.idx[e];
+    const int4 kl = m.leaf[K];
+    const int Lc = cl.x;
+    int g[3] = {cl.y * NB + rc[0], cl.z * NB + rc[1], cl.w * NB + rc[2]};
+    g[a] += side;
+    const int ncell = (m.root[a] << Lc) * NB;
+    g[a] = wrap_mod(g[a], ncell);
+    const int lx = (g[0] >> 1) - kl.y * NB, ly = (g[1] >> 1) - kl.z * NB, lz = (g[2] >> 1) - kl.w * NB;
+    load5<T, NB>(U, K, lx + G, ly + G, lz + G, out);
+  }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
+  constexpr int G = kGhosts, N = NB + 2 * G, NG = N * N * N - NB * NB * NB, H = NB / 2;
+  constexpr long SLAB = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)nleaf * NG) return;
+  const int leaf = leaf0 + (int)(gid / NG);
+  int c[3];
+  ghost_coord<NB>((int)(gid % NG), c[0], c[1], c[2]);
+  const long dst = (long)leaf * 5 * SLAB + ((long)c[2] * N + c[1]) * N + c[0];
+  int d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    d[a] = c[a] < G ? -1 : (c[a] >= G + NB ? 1 : 0);
+    if (d[a] != 0 && m.kind[leaf * 27 + face_dir(a, d[a])] == kBoundary) {
+      c[a] = d[a] < 0 ? G : G + NB - 1;   // outflow: nearest interior cell
+      d[a] = 0;
+    }
+  }
+  const int e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
+  const int8_t k = m.kind[e];
+  T v[5];
+  if (k == kSame) {
+    load5<T, NB>(U, m.idx[e], c[0] - d[0] * NB, c[1] - d[1] * NB, c[2] - d[2] * NB, v);
+  } else if (k == kFine) {
+    int r[3], o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r[a] = c[a] - G - d[a] * NB;
+      o[a] = r[a] / H;
+    }
+    const int child = m.fine8[e * 8 + o[2] * 4 + o[1] * 2 + o[0]];
+    restrict8<T, NB>(U, child, 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G, 2 * r[2] - o[2] * NB + G, v);
+  } else {  // coarse: conservative minmod-limited linear prolongation
+    const int4 lf = m.leaf[leaf];
+    const int C = m.idx[e];
+    const int4 cl = m.leaf[C];
+    const int L = lf.x;
+    const int lij[3] = {lf.y, lf.z, lf.w}, cij[3] = {cl.y, cl.z, cl.w};
+    int rc[3];
+    T sgn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ncell = (m.root[a] << L) * NB;
+      const int gl = wrap_mod(lij[a] * NB + (c[a] - G), ncell);
+      rc[a] = (gl >> 1) - cij[a] * NB;
+      sgn[a] = (gl & 1) ? T(1) : T(-1);
+    }
+    T Uc[5];
+    load5<T, NB>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+    T D[3][5];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T Um[5], Up[5];
+      int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
+      rm[a] -= 1;
+      rp[a] += 1;
+      if (rm[a] >= 0) load5<T, NB>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, 1, Uc, Up);
+#pragma unroll
+      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+    }
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      v[f] = Uc[f] + T(0.25) * ((sgn[0] * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
+  }
+#pragma unroll
+  for (int f = 0; f < 5; ++f) U[dst + f * SLAB] = v[f];
+}
+
+// =====================================================================
+// CFL dt candidates and conserved sums, one CTA per leaf (partials), then a
+// single-CTA fixed-order finish.  Deterministic for a fixed launch shape.
+// =====================================================================
+constexpr int kReduceThreads = 256;
+
+__device__ __forceinline__ void block_reduce6(double v[6], double* sh) {
+  // v[0] min, v[1..5] sums; fixed tree: xor shuffles, then warp 0 over warps.
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+#pragma unroll
+    for (int k = 1; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sh[w * 6 + k] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = (l < nw) ? sh[l * 6 + k] : (k == 0 ? INFINITY : 0.0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+#pragma unroll
+      for (int k = 1; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+  }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh m, const T* U, double* partials) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
+  __shared__ double sh[6 * 32];
+  const int leaf = blockIdx.x;
+  const int4 lf = m.leaf[leaf];
+  const T dx = T(ldexp(m.dx0, -lf.x));
+  const T gamma = T(m.gamma), gm1 = T(m.gamma - 1.0);
+  const T* b = U + (long)leaf * 5 * SLAB;
+  double v[6] = {INFINITY, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
+    const int x = i % NB + G, y = (i / NB) % NB + G, z = i / (NB * NB) + G;
+    const long o = ((long)z * N + y) * N + x;
+    const T r0 = b[o], m1 = b[SLAB + o], m2 = b[2 * SLAB + o], m3 = b[3 * SLAB + o], E = b[4 * SLAB + o];
+    const T rho = vmax(r0, T(kRhoFloor));
+    const T u = m1 / rho, vv = m2 / rho, w = m3 / rho;
+    const T ke = (T(0.5) * rho) * (u * u + (vv * vv + w * w));
+    const T p = vmax(gm1 * (E - ke), T(kPFloor));
+    const T c = vsqrt((gamma * p) / rho);
+    const T s = vmax(vabs(u), vmax(vabs(vv), vabs(w))) + c;
+    v[0] = fmin(v[0], double(dx / s));
+    v[1] += double(r0); v[2] += double(m1); v[3] += double(m2); v[4] += double(m3); v[5] += double(E);
+  }
+  block_reduce6(v, sh);
+  if (threadIdx.x == 0) {
+    const double dxd = ldexp(m.dx0, -lf.x);
+    const double vol = dxd * dxd * dxd;
+    partials[leaf * 6 + 0] = v[0];
+    for (int k = 1; k < 6; ++k) partials[leaf * 6 + k] = v[k] * vol;
+  }
+}
+
+#ifdef CELLO_DEFINE_FINISH_KERNEL
+__global__ void __launch_bounds__(1024) reduce_finish_kernel(const double* partials, int B, double cfl,
+                                                             double* dt_next, double* totals) {
+  __shared__ double sh[6 * 32];
+  double v[6] = {INFINITY, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    v[0] = fmin(v[0], partials[i * 6]);
+    for (int k = 1; k < 6; ++k) v[k] += partials[i * 6 + k];
+  }
+  block_reduce6(v, sh);
+  if (threadIdx.x == 0) {
+    if (dt_next) *dt_next = cfl * v[0];
+    if (totals)
+      for (int k = 0; k < 5; ++k) totals[k] = v[k + 1];
+  }
+}
+#endif
+
+// =====================================================================
+// Refinement flags: relative slope of rho or p, compared in float64.
+// =====================================================================
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) flags_kernel(DevMesh m, const T* U, int field, double thr, double thr_c,
+                                                    int8_t* flags) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
+  const int leaf = blockIdx.x;
+  const int4 lf = m.leaf[leaf];
+  const T* b = U + (long)leaf * 5 * SLAB;
+  const double gm1 = m.gamma - 1.0;
+  auto q = [&](long o) -> double {
+    const double r0 = double(b[o]);
+    const double rho = r0 > kRhoFloor ? r0 : kRhoFloor;
+    if (field == 0) return rho;
+    const double u = double(b[SLAB + o]) / rho, v = double(b[2 * SLAB + o]) / rho, w = double(b[3 * SLAB + o]) / rho;
+    const double ke = (0.5 * rho) * (u * u + (v * v + w * w));
+    const double p = gm1 * (double(b[4 * SLAB + o]) - ke);
+    return p > kPFloor ? p : kPFloor;
+  };
+  int hit = 0, hit_c = 0;
+  for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
+    const int x = i % NB + G, y = (i / NB) % NB + G, z = i / (NB * NB) + G;
+    const long o = ((long)z * N + y) * N + x;
+    const double c = fabs(q(o));
+    const long st[3] = {1, N, (long)N * N};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double diff = fabs(q(o + st[a]) - q(o - st[a]));
+      hit |= diff > thr * c;
+      hit_c |= diff > thr_c * c;
+    }
+  }
+  hit = __syncthreads_or(hit);
+  hit_c = __syncthreads_or(hit_c);
+  if (threadIdx.x == 0) {
+    int8_t f = 0;
+    if (!hit_c && lf.x > 0) f = -1;
+    if (hit && lf.x < m.max_level) f = 1;
+    flags[leaf] = f;
+  }
+}
+
+// =====================================================================
+// Coarse-fine flux correction: one CTA per coarse leaf, its faces in order
+// -x, +x, -y, +y, -z, +z, arithmetic in float64.
+// =====================================================================
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) fluxcorr_kernel(DevMesh m, T* U, const CoarseFace* faces,
+                                                       const int* group_start, const double* reg,
+                                                       const double* dt) {
+  constexpr int G = kGhosts, N = NB + 2 * G, H = NB / 2;
+  constexpr long SLAB = (long)N * N * N;
+  constexpr long FS = (long)NB * NB;
+  const int f0 = group_start[blockIdx.x], f1 = group_start[blockIdx.x + 1];
+  for (int fi = f0; fi < f1; ++fi) {
+    const CoarseFace cf = faces[fi];
+    const int4 cl = m.leaf[cf.leaf];
+    const double dtdx = *dt / ldexp(m.dx0, -cl.x);
+    const int t1a = cf.axis == 0 ? 1 : 0, t2a = cf.axis == 2 ? 1 : 2;
+    for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+      const int t1 = i % NB, t2 = i / NB;
+      const int o1 = t1 / H, o2 = t2 / H;
+      const int b1 = t1 - o1 * H, b2 = t2 - o2 * H;
+      const double* Rf = reg + (long)cf.fslot[o2 * 2 + o1] * 5 * FS + (2 * b2) * NB + 2 * b1;
+      const double* Rc = reg + (long)cf.cslot * 5 * FS + t2 * NB + t1;
+      int cc[3];
+      cc[cf.axis] = cf.side > 0 ? G + NB - 1 : G;
+      cc[t1a] = G + t1;
+      cc[t2a] = G + t2;
+      T* cell = U + (long)cf.leaf * 5 * SLAB + ((long)cc[2] * N + cc[1]) * N + cc[0];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const double* r = Rf + f * FS;
+        const double mean = ((r[0] + r[1]) + (r[NB] + r[NB + 1])) * 0.25;
+        const double corr = (dtdx * (Rc[f * FS] - mean)) * double(cf.side);
+        cell[f * SLAB] = T(double(cell[f * SLAB]) + corr);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace cello

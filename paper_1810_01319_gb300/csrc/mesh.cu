@@ -1,0 +1,591 @@
+// Host side of the library: the C ABI, the array-of-octrees build from
+// refinement flags (Sec. II.B), the device block table and the per-step
+// launch sequence (ghost refresh -> three PPM sweeps -> flux correction ->
+// CFL/totals reduction), optionally replayed from a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "cello.h"
+#include "cello_internal.h"
+#include "morton.h"
+
+using namespace cello;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cello_status fail(cello_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define CELLO_CUDA(call)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? CELLO_ENOMEM : CELLO_ECUDA,           \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+struct Node {
+  int L, i, j, k;
+};
+
+inline unsigned long long pack(const Node& t) {
+  return ((unsigned long long)t.L << 60) | ((unsigned long long)t.i << 40) | ((unsigned long long)t.j << 20) |
+         (unsigned long long)t.k;
+}
+
+inline Node child(const Node& t, int o) {
+  return Node{t.L + 1, 2 * t.i + (o & 1), 2 * t.j + ((o >> 1) & 1), 2 * t.k + (o >> 2)};
+}
+
+// Leaf set with its internal (refined) ancestors, for balance queries.
+struct Tree {
+  const cello_mesh_desc& d;
+  std::unordered_set<unsigned long long> leaves, internal;
+  explicit Tree(const cello_mesh_desc& desc) : d(desc) {}
+
+  void index(const std::vector<Node>& ls) {
+    leaves.clear();
+    internal.clear();
+    for (const Node& t : ls) {
+      leaves.insert(pack(t));
+      Node p = t;
+      while (p.L > 0) {
+        p = Node{p.L - 1, p.i >> 1, p.j >> 1, p.k >> 1};
+        if (!internal.insert(pack(p)).second) break;
+      }
+    }
+  }
+
+  bool wrap(int L, int a, int& v) const {
+    const int nb = d.root[a] << L;
+    if (v >= 0 && v < nb) return true;
+    if (d.bc[a] != CELLO_PERIODIC) return false;
+    v = ((v % nb) + nb) % nb;
+    return true;
+  }
+
+  // True if a leaf two or more levels finer than node t touches it: some
+  // same-level neighbour node is refined and one of its children that
+  // touches t is refined too.
+  bool touches_deeper(const Node& t) const {
+    if (t.L + 2 > d.max_level) return false;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (!dx && !dy && !dz) continue;
+          int v[3] = {t.i + dx, t.j + dy, t.k + dz};
+          bool in = true;
+          for (int a = 0; a < 3; ++a) in = in && wrap(t.L, a, v[a]);
+          if (!in) continue;
+          const Node nb{t.L, v[0], v[1], v[2]};
+          if (!internal.count(pack(nb))) continue;
+          for (int o = 0; o < 8; ++o) {
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            if ((dx == 1 && ox) || (dx == -1 && !ox) || (dy == 1 && oy) || (dy == -1 && !oy) || (dz == 1 && oz) ||
+                (dz == -1 && !oz))
+              continue;
+            if (internal.count(pack(child(nb, o)))) return true;
+          }
+        }
+    return false;
+  }
+};
+
+unsigned long long leaf_key(const cello_mesh_desc& d, const Node& t) {
+  const int s = d.max_level - t.L;
+  return morton3((unsigned)t.i << s, (unsigned)t.j << s, (unsigned)t.k << s);
+}
+
+}  // namespace
+
+namespace cello {
+void prepare_kernels() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    prepare_kernels_f32();
+    prepare_kernels_f64();
+  });
+}
+}  // namespace cello
+
+struct GraphEntry {
+  const void* U;
+  const double* dt;
+  int parity;
+  double cfl;
+  double* dt_next;
+  double* totals;
+  cudaGraphExec_t exec;
+};
+
+struct cello_mesh {
+  cello_mesh_desc desc{};
+  int B = 0, N = 0;
+  std::vector<int4> leaves;
+  std::vector<unsigned long long> keys;
+  std::vector<int8_t> kind;
+  std::vector<int> idx, fine8, face_slot;
+  std::vector<CoarseFace> cfaces;
+  std::vector<int> group_start;
+  int nslots = 0;
+  int4* d_leaf = nullptr;
+  unsigned long long* d_keys = nullptr;
+  int8_t* d_kind = nullptr;
+  int* d_idx = nullptr;
+  int* d_fine8 = nullptr;
+  int* d_face_slot = nullptr;
+  CoarseFace* d_cfaces = nullptr;
+  int* d_group_start = nullptr;
+  double* d_reg = nullptr;
+  double* d_partials = nullptr;
+  int exec_mode = CELLO_EXEC_BATCHED;
+  std::vector<GraphEntry> graphs;
+  cudaStream_t capture_stream = nullptr;
+
+  DevMesh dev() const {
+    DevMesh m;
+    m.n = desc.n;
+    m.g = desc.ghosts;
+    m.N = N;
+    m.max_level = desc.max_level;
+    for (int a = 0; a < 3; ++a) {
+      m.root[a] = desc.root[a];
+      m.bc[a] = desc.bc[a];
+    }
+    m.dx0 = (desc.hi[0] - desc.lo[0]) / (desc.root[0] * desc.n);
+    m.gamma = desc.gamma;
+    m.B = B;
+    m.leaf = d_leaf;
+    m.kind = d_kind;
+    m.idx = d_idx;
+    m.fine8 = d_fine8;
+    m.face_slot = d_face_slot;
+    return m;
+  }
+
+  void release() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    capture_stream = nullptr;
+    void* ptrs[] = {d_leaf, d_keys, d_kind, d_idx, d_fine8, d_face_slot, d_cfaces, d_group_start, d_reg, d_partials};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    d_leaf = nullptr; d_keys = nullptr; d_kind = nullptr; d_idx = nullptr; d_fine8 = nullptr;
+    d_face_slot = nullptr; d_cfaces = nullptr; d_group_start = nullptr; d_reg = nullptr; d_partials = nullptr;
+  }
+  ~cello_mesh() { release(); }
+};
+
+namespace {
+
+cello_status check_desc(const cello_mesh_desc* d) {
+  if (!d) return fail(CELLO_EINVAL, "desc is NULL");
+  if (d->n != 8 && d->n != 16 && d->n != 32) return fail(CELLO_EINVAL, "n must be 8, 16 or 32");
+  if (d->ghosts != kGhosts) return fail(CELLO_EINVAL, "ghosts must be 4");
+  if (d->precision != 4 && d->precision != 8) return fail(CELLO_EINVAL, "precision must be 4 or 8");
+  if (d->max_level < 0 || d->max_level > 10) return fail(CELLO_EINVAL, "max_level must be in [0, 10]");
+  if (!(d->gamma > 1.0)) return fail(CELLO_EINVAL, "gamma must exceed 1");
+  double ext[3];
+  for (int a = 0; a < 3; ++a) {
+    if (d->root[a] < 1 || d->root[a] > 1024) return fail(CELLO_EINVAL, "root blocks per axis must be in [1, 1024]");
+    if (d->bc[a] != CELLO_PERIODIC && d->bc[a] != CELLO_OUTFLOW) return fail(CELLO_EINVAL, "bc must be 0 or 1");
+    ext[a] = (d->hi[a] - d->lo[a]) / d->root[a];
+    if (!(ext[a] > 0)) return fail(CELLO_EINVAL, "hi must exceed lo");
+  }
+  for (int a = 1; a < 3; ++a)
+    if (std::abs(ext[a] - ext[0]) > 1e-12 * ext[0]) return fail(CELLO_EINVAL, "cells must be cubes");
+  return CELLO_OK;
+}
+
+// New leaf list from the previous one and flags (see cello_octree_build).
+std::vector<Node> build_leaves(const cello_mesh_desc& d, const cello_mesh* prev, const int8_t* flags) {
+  std::vector<Node> cur;
+  if (!prev) {
+    for (int k = 0; k < d.root[2]; ++k)
+      for (int j = 0; j < d.root[1]; ++j)
+        for (int i = 0; i < d.root[0]; ++i) cur.push_back(Node{0, i, j, k});
+    return cur;
+  }
+  const int B = prev->B;
+  std::vector<Node> old(B);
+  for (int b = 0; b < B; ++b) {
+    const int4 l = prev->leaves[b];
+    old[b] = Node{l.x, l.y, l.z, l.w};
+  }
+  std::unordered_map<unsigned long long, int> flag_of;
+  std::unordered_set<unsigned long long> refine;
+  for (int b = 0; b < B; ++b) {
+    const int f = flags ? flags[b] : 0;
+    flag_of[pack(old[b])] = f;
+    if (f > 0 && old[b].L < d.max_level) refine.insert(pack(old[b]));
+  }
+  for (const Node& t : old) {
+    if (refine.count(pack(t)))
+      for (int o = 0; o < 8; ++o) cur.push_back(child(t, o));
+    else
+      cur.push_back(t);
+  }
+  Tree tree(d);
+  tree.index(cur);
+  // coarsening candidates: complete octets of unrefined -1 leaves
+  std::unordered_map<unsigned long long, int> kids;
+  for (const Node& t : old)
+    if (t.L > 0) kids[pack(Node{t.L - 1, t.i >> 1, t.j >> 1, t.k >> 1})]++;
+  std::vector<Node> coarsen;
+  for (const auto& kv : kids) {
+    if (kv.second != 8) continue;
+    const unsigned long long pk = kv.first;
+    const Node p{(int)(pk >> 60), (int)((pk >> 40) & 0xfffff), (int)((pk >> 20) & 0xfffff), (int)(pk & 0xfffff)};
+    bool ok = true;
+    for (int o = 0; o < 8 && ok; ++o) {
+      const unsigned long long c = pack(child(p, o));
+      auto it = flag_of.find(c);
+      ok = it != flag_of.end() && it->second < 0 && !refine.count(c);
+    }
+    if (ok && !tree.touches_deeper(p)) coarsen.push_back(p);
+  }
+  if (!coarsen.empty()) {
+    std::unordered_set<unsigned long long> gone;
+    for (const Node& p : coarsen)
+      for (int o = 0; o < 8; ++o) gone.insert(pack(child(p, o)));
+    std::vector<Node> next;
+    for (const Node& t : cur)
+      if (!gone.count(pack(t))) next.push_back(t);
+    for (const Node& p : coarsen) next.push_back(p);
+    cur.swap(next);
+  }
+  // 2:1 balance: refine every leaf touching a leaf two levels finer
+  for (;;) {
+    tree.index(cur);
+    std::vector<Node> next;
+    bool changed = false;
+    for (const Node& t : cur) {
+      if (tree.touches_deeper(t)) {
+        changed = true;
+        for (int o = 0; o < 8; ++o) next.push_back(child(t, o));
+      } else {
+        next.push_back(t);
+      }
+    }
+    cur.swap(next);
+    if (!changed) break;
+  }
+  return cur;
+}
+
+template <typename V>
+cello_status upload(V** dptr, const std::vector<V>& h) {
+  if (h.empty()) return CELLO_OK;
+  CELLO_CUDA(cudaMalloc((void**)dptr, h.size() * sizeof(V)));
+  CELLO_CUDA(cudaMemcpy(*dptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return CELLO_OK;
+}
+
+#define CELLO_TRY(expr)               \
+  do {                                \
+    cello_status st_ = (expr);        \
+    if (st_ != CELLO_OK) return st_;  \
+  } while (0)
+
+cello_status finish_build(cello_mesh* M) {
+  const cello_mesh_desc& d = M->desc;
+  const int B = M->B;
+  CELLO_TRY(upload(&M->d_leaf, M->leaves));
+  CELLO_TRY(upload(&M->d_keys, M->keys));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_kind, (size_t)B * 27));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_idx, (size_t)B * 27 * sizeof(int)));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_fine8, (size_t)B * 27 * 8 * sizeof(int)));
+  DevMesh dm = M->dev();
+  launch_neighbour_table(dm, M->d_keys, M->d_kind, M->d_idx, M->d_fine8, 0);
+  CELLO_CUDA(cudaGetLastError());
+  M->kind.resize((size_t)B * 27);
+  M->idx.resize((size_t)B * 27);
+  M->fine8.resize((size_t)B * 27 * 8);
+  CELLO_CUDA(cudaMemcpy(M->kind.data(), M->d_kind, M->kind.size(), cudaMemcpyDeviceToHost));
+  CELLO_CUDA(cudaMemcpy(M->idx.data(), M->d_idx, M->idx.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  CELLO_CUDA(cudaMemcpy(M->fine8.data(), M->d_fine8, M->fine8.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int8_t k : M->kind)
+    if (k < 0) return fail(CELLO_EINTERNAL, "2:1 balance violated: a neighbour is two levels coarser");
+  // every child of a refined neighbour node that touches the leaf must be a
+  // leaf (balance); the refresh and the slope lookups index only those
+  for (int b = 0; b < B; ++b)
+    for (int e = 0; e < 27; ++e) {
+      if (M->kind[(size_t)b * 27 + e] != kFine) continue;
+      const int dd[3] = {e % 3 - 1, (e / 3) % 3 - 1, e / 9 - 1};
+      for (int o = 0; o < 8; ++o) {
+        const int oo[3] = {o & 1, (o >> 1) & 1, o >> 2};
+        bool touch = true;
+        for (int a = 0; a < 3; ++a) touch = touch && !((dd[a] == 1 && oo[a]) || (dd[a] == -1 && !oo[a]));
+        if (touch && M->fine8[((size_t)b * 27 + e) * 8 + o] < 0)
+          return fail(CELLO_EINTERNAL, "2:1 balance violated: a touching neighbour is two levels finer");
+      }
+    }
+  // flux-register slots: faces whose neighbour is finer (coarse side) or coarser (fine side)
+  M->face_slot.assign((size_t)B * 6, -1);
+  int ns = 0;
+  for (int b = 0; b < B; ++b)
+    for (int f = 0; f < 6; ++f) {
+      const int k = M->kind[b * 27 + face_dir(f / 2, (f & 1) ? 1 : -1)];
+      if (k == kFine || k == kCoarse) M->face_slot[b * 6 + f] = ns++;
+    }
+  M->nslots = ns;
+  M->cfaces.clear();
+  M->group_start.clear();
+  for (int b = 0; b < B; ++b) {
+    bool first = true;
+    for (int f = 0; f < 6; ++f) {
+      const int axis = f / 2, side = (f & 1) ? 1 : -1;
+      const int e = b * 27 + face_dir(axis, side);
+      if (M->kind[e] != kFine) continue;
+      CoarseFace cf;
+      cf.leaf = b;
+      cf.axis = axis;
+      cf.side = side;
+      cf.cslot = M->face_slot[b * 6 + f];
+      const int t1 = axis == 0 ? 1 : 0, t2 = axis == 2 ? 1 : 2;
+      for (int o2 = 0; o2 < 2; ++o2)
+        for (int o1 = 0; o1 < 2; ++o1) {
+          int o[3];
+          o[axis] = side < 0 ? 1 : 0;
+          o[t1] = o1;
+          o[t2] = o2;
+          const int c = M->fine8[(size_t)e * 8 + o[2] * 4 + o[1] * 2 + o[0]];
+          if (c < 0) return fail(CELLO_EINTERNAL, "refined neighbour face without leaf children");
+          const int fs = M->face_slot[c * 6 + 2 * axis + (side < 0 ? 1 : 0)];
+          if (fs < 0) return fail(CELLO_EINTERNAL, "fine face without a register slot");
+          cf.fslot[o2 * 2 + o1] = fs;
+        }
+      if (first) M->group_start.push_back((int)M->cfaces.size());
+      first = false;
+      M->cfaces.push_back(cf);
+    }
+  }
+  if (!M->cfaces.empty()) M->group_start.push_back((int)M->cfaces.size());
+  CELLO_TRY(upload(&M->d_face_slot, M->face_slot));
+  CELLO_TRY(upload(&M->d_cfaces, M->cfaces));
+  CELLO_TRY(upload(&M->d_group_start, M->group_start));
+  if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * 5 * d.n * d.n * sizeof(double)));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_partials, (size_t)std::max(B, 1) * 6 * sizeof(double)));
+  CELLO_CUDA(cudaDeviceSynchronize());
+  return CELLO_OK;
+}
+
+void launch_refresh(const cello_mesh* M, const DevMesh& dm, void* U, int leaf0, int nleaf, cudaStream_t s) {
+  if (M->desc.precision == 4) launch_refresh_f32(dm, static_cast<float*>(U), leaf0, nleaf, s);
+  else launch_refresh_f64(dm, static_cast<double*>(U), leaf0, nleaf, s);
+}
+
+// The launch sequence of one step on stream s.
+void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, double cfl, double* dt_next,
+                  double* totals, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const cello_mesh_desc& d = M->desc;
+  const DevMesh dm = M->dev();
+  const int B = M->B, n = d.n, g = d.ghosts, N = M->N;
+  const bool plain = M->exec_mode == CELLO_EXEC_PLAIN && !ev;
+  if (ev) cudaEventRecord(ev[0], s);
+  if (plain)
+    for (int b = 0; b < B; ++b) launch_refresh(M, dm, U, b, 1, s);
+  else
+    launch_refresh(M, dm, U, 0, B, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  const int order[3] = {cycle % 2 == 0 ? 0 : 2, 1, cycle % 2 == 0 ? 2 : 0};
+  bool swept[3] = {false, false, false};
+  for (int oi = 0; oi < 3; ++oi) {
+    const int axis = order[oi];
+    const int ta = axis == 2 ? 1 : 2;   // transverse A: z, or y for the z sweep
+    const int tb = axis == 0 ? 1 : 0;   // transverse B: y for the x sweep, else x
+    SweepParams p{};
+    p.U = U;
+    p.axis = axis;
+    p.a0 = swept[ta] ? g : 0;
+    p.a1 = swept[ta] ? g + n : N;
+    p.b0 = swept[tb] ? g : 0;
+    p.b1 = swept[tb] ? g + n : N;
+    const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
+    p.tiles_per_leaf = (pencils + kPencilsPerTile - 1) / kPencilsPerTile;
+    p.dt = dt;
+    p.reg = M->d_reg;
+    p.work = nullptr;
+    if (plain) {
+      for (int b = 0; b < B; ++b) {
+        p.leaf0 = b;
+        p.nleaf = 1;
+        p.n_items = p.tiles_per_leaf;
+        if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
+        else launch_sweep_f64(dm, p, pencils, s);
+      }
+    } else {
+      p.leaf0 = 0;
+      p.nleaf = B;
+      p.n_items = B * p.tiles_per_leaf;
+      if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
+      else launch_sweep_f64(dm, p, pencils, s);
+    }
+    swept[axis] = true;
+    if (ev) cudaEventRecord(ev[2 + oi], s);
+  }
+  if (!M->cfaces.empty())
+    launch_fluxcorr(dm, U, d.precision, M->d_cfaces, M->d_group_start, (int)M->group_start.size() - 1, M->d_reg,
+                    dt, s);
+  if (ev) cudaEventRecord(ev[5], s);
+  if (dt_next || totals || ev) launch_reduce(dm, U, d.precision, cfl, M->d_partials, dt_next, totals, s);
+  if (ev) cudaEventRecord(ev[6], s);
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* cello_last_error(void) { return g_last_error.c_str(); }
+
+cello_status cello_octree_build(const cello_mesh_desc* desc, const cello_mesh* prev, const int8_t* flags_host,
+                                cello_mesh** out) {
+  if (!out) return fail(CELLO_EINVAL, "out is NULL");
+  *out = nullptr;
+  CELLO_TRY(check_desc(desc));
+  if (prev && std::memcmp(&prev->desc, desc, sizeof(cello_mesh_desc)) != 0)
+    return fail(CELLO_EINVAL, "prev was built from a different description");
+  prepare_kernels();
+  auto* M = new (std::nothrow) cello_mesh();
+  if (!M) return fail(CELLO_ENOMEM, "host allocation failed");
+  M->desc = *desc;
+  M->N = desc->n + 2 * desc->ghosts;
+  std::vector<Node> ls = build_leaves(*desc, prev, flags_host);
+  std::vector<std::pair<unsigned long long, Node>> keyed;
+  keyed.reserve(ls.size());
+  for (const Node& t : ls) keyed.emplace_back(leaf_key(*desc, t), t);
+  std::sort(keyed.begin(), keyed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  M->B = (int)keyed.size();
+  for (const auto& kv : keyed) {
+    M->keys.push_back(kv.first);
+    M->leaves.push_back(make_int4(kv.second.L, kv.second.i, kv.second.j, kv.second.k));
+  }
+  cello_status st = finish_build(M);
+  if (st != CELLO_OK) {
+    delete M;
+    return st;
+  }
+  *out = M;
+  return CELLO_OK;
+}
+
+void cello_mesh_free(cello_mesh* mesh) { delete mesh; }
+
+cello_status cello_mesh_info(const cello_mesh* M, int64_t* n_leaves, int64_t* leaf_elems, int64_t* n_cf) {
+  if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
+  if (n_leaves) *n_leaves = M->B;
+  if (leaf_elems) *leaf_elems = 5LL * M->N * M->N * M->N;
+  if (n_cf) *n_cf = (int64_t)M->cfaces.size();
+  return CELLO_OK;
+}
+
+cello_status cello_mesh_leaves(const cello_mesh* M, int32_t* out) {
+  if (!M || !out) return fail(CELLO_EINVAL, "NULL argument");
+  for (int b = 0; b < M->B; ++b) {
+    out[4 * b] = M->leaves[b].x;
+    out[4 * b + 1] = M->leaves[b].y;
+    out[4 * b + 2] = M->leaves[b].z;
+    out[4 * b + 3] = M->leaves[b].w;
+  }
+  return CELLO_OK;
+}
+
+cello_status cello_neighbour_table(const cello_mesh* M, int8_t* kind, int32_t* idx, int32_t* fine8) {
+  if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
+  if (kind) std::memcpy(kind, M->kind.data(), M->kind.size());
+  if (idx) std::memcpy(idx, M->idx.data(), M->idx.size() * sizeof(int));
+  if (fine8) std::memcpy(fine8, M->fine8.data(), M->fine8.size() * sizeof(int));
+  return CELLO_OK;
+}
+
+cello_status cello_refine_flags(cello_mesh* M, const void* U, int field, double tau, double tau_c, int8_t* flags,
+                                void* stream) {
+  if (!M || !U || !flags) return fail(CELLO_EINVAL, "NULL argument");
+  if (field != 0 && field != 4) return fail(CELLO_EINVAL, "field must be 0 (density) or 4 (pressure)");
+  launch_flags(M->dev(), U, M->desc.precision, field, tau, tau_c, flags, (cudaStream_t)stream);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status cello_ghost_refresh(cello_mesh* M, void* U, void* stream) {
+  if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
+  launch_refresh(M, M->dev(), U, 0, M->B, (cudaStream_t)stream);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status cello_reduce(cello_mesh* M, const void* U, double cfl, double* dt_next, double* totals, void* stream) {
+  if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
+  launch_reduce(M->dev(), U, M->desc.precision, cfl, M->d_partials, dt_next, totals, (cudaStream_t)stream);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status cello_set_exec(cello_mesh* M, int mode) {
+  if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
+  if (mode < CELLO_EXEC_PLAIN || mode > CELLO_EXEC_GRAPH) return fail(CELLO_EINVAL, "unknown exec mode");
+  M->exec_mode = mode;
+  return CELLO_OK;
+}
+
+cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycle, double cfl, double* dt_next,
+                              double* totals, void* stream) {
+  if (!M || !U || !dt) return fail(CELLO_EINVAL, "NULL argument");
+  if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (M->exec_mode != CELLO_EXEC_GRAPH) {
+    enqueue_step(M, U, dt, cycle, cfl, dt_next, totals, s);
+    CELLO_CUDA(cudaGetLastError());
+    return CELLO_OK;
+  }
+  const int parity = cycle % 2;
+  for (const GraphEntry& g : M->graphs)
+    if (g.U == U && g.dt == dt && g.parity == parity && g.cfl == cfl && g.dt_next == dt_next && g.totals == totals) {
+      CELLO_CUDA(cudaGraphLaunch(g.exec, s));
+      return CELLO_OK;
+    }
+  if (!M->capture_stream) CELLO_CUDA(cudaStreamCreateWithFlags(&M->capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  CELLO_CUDA(cudaStreamBeginCapture(M->capture_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(M, U, dt, parity, cfl, dt_next, totals, M->capture_stream);
+  CELLO_CUDA(cudaStreamEndCapture(M->capture_stream, &graph));
+  cudaGraphExec_t exec;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CELLO_CUDA(e);
+  if (M->graphs.size() >= 8) {
+    cudaGraphExecDestroy(M->graphs.front().exec);
+    M->graphs.erase(M->graphs.begin());
+  }
+  M->graphs.push_back(GraphEntry{U, dt, parity, cfl, dt_next, totals, exec});
+  CELLO_CUDA(cudaGraphLaunch(exec, s));
+  return CELLO_OK;
+}
+
+cello_status cello_profile_step(cello_mesh* M, void* U, const double* dt, int cycle, double cfl, float* phase_ms,
+                                void* stream) {
+  if (!M || !U || !dt || !phase_ms) return fail(CELLO_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) CELLO_CUDA(cudaEventCreate(&ev[i]));
+  enqueue_step(M, U, dt, cycle, cfl, nullptr, nullptr, s, ev);
+  cudaError_t e = cudaEventSynchronize(ev[6]);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&phase_ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+  CELLO_CUDA(e);
+  return CELLO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Per-cell and per-interface arithmetic of the PPM sweep (Sec. II.C: the
+// hydro Method is a modified piecewise parabolic method, Colella & Woodward
+// 1984).  Every expression is written in a fixed evaluation order so that the
+// float64 build (compiled without FMA contraction) rounds exactly like a
+// plain float64 evaluation of the same formulas.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cello {
+
+constexpr double kRhoFloor = 1e-10;
+constexpr double kPFloor = 1e-20;
+constexpr double kEpsShock = 0.33;   // shock detector: relative pressure jump
+constexpr double kOmega1 = 0.75;     // flattening ratio offset
+constexpr double kOmega2 = 10.0;     // flattening ratio slope
+constexpr int kRiemannIters = 5;     // fixed Newton steps, no early exit
+
+template <typename T> __device__ __forceinline__ T vmax(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return a < b ? a : b; }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double vabs(double a) { return fabs(a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float vcopysign(float a, float b) { return copysignf(a, b); }
+__device__ __forceinline__ double vcopysign(double a, double b) { return copysign(a, b); }
+
+// Gas constants in the working precision, derived once in float64.
+template <typename T> struct Gas {
+  T gamma, gm1, g1, inv_gm1;
+  __host__ __device__ static Gas make(double gamma) {
+    Gas s;
+    s.gamma = T(gamma);
+    s.gm1 = T(gamma - 1.0);
+    s.g1 = T((gamma + 1.0) / (2.0 * gamma));
+    s.inv_gm1 = T(1.0 / (gamma - 1.0));
+    return s;
+  }
+};
+
+// Conserved (rho, m_n, m_t1, m_t2, E) -> primitive (rho, u_n, u_t1, u_t2, p).
+template <typename T>
+__device__ __forceinline__ void to_primitive(const T U[5], const Gas<T>& gs, T W[5]) {
+  T rho = vmax(U[0], T(kRhoFloor));
+  T un = U[1] / rho;
+  T ut1 = U[2] / rho;
+  T ut2 = U[3] / rho;
+  T ke = (T(0.5) * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
+  T p = vmax(gs.gm1 * (U[4] - ke), T(kPFloor));
+  W[0] = rho; W[1] = un; W[2] = ut1; W[3] = ut2; W[4] = p;
+}
+
+// Monotonised centred slope, zero at a local extremum.
+template <typename T>
+__device__ __forceinline__ T limited_slope(T am, T a0, T ap) {
+  T dl = a0 - am;
+  T dr = ap - a0;
+  T da = T(0.5) * (ap - am);
+  T m = vmin(vabs(da), vmin(T(2) * vabs(dl), T(2) * vabs(dr)));
+  return (dl * dr > T(0)) ? vcopysign(m, da) : T(0);
+}
+
+// Interface value between cells j and j+1 in limited form.
+template <typename T>
+__device__ __forceinline__ T interface_value(T a0, T a1, T dm0, T dm1) {
+  return T(0.5) * (a0 + a1) - (dm1 - dm0) * T(1.0 / 6.0);
+}
+
+// Shock detector of the flattening coefficient.
+template <typename T>
+__device__ __forceinline__ T flatten_tilde(T pm2, T pm1, T pp1, T pp2, T um1, T up1) {
+  T dp1 = pp1 - pm1;
+  T dp2 = pp2 - pm2;
+  bool shock = (vabs(dp1) > T(kEpsShock) * vmin(pp1, pm1)) && (um1 - up1 > T(0)) && (dp2 != T(0));
+  T ratio = dp1 / ((dp2 != T(0)) ? dp2 : T(1));
+  T ft = vmax(vmin(T(kOmega2) * (ratio - T(kOmega1)), T(1)), T(0));
+  return shock ? ft : T(0);
+}
+
+// Flatten towards the cell value, then apply the monotonicity constraints.
+template <typename T>
+__device__ __forceinline__ void flatten_monotone(T a, T f, T& aL, T& aR) {
+  T l = f * a + (T(1) - f) * aL;
+  T r = f * a + (T(1) - f) * aR;
+  bool ext = (r - a) * (a - l) <= T(0);
+  T da = r - l;
+  T dm = a - T(0.5) * (l + r);
+  T t1 = da * dm;
+  T t2 = (da * da) * T(1.0 / 6.0);
+  aL = ext ? a : ((t1 > t2) ? T(3) * a - T(2) * r : l);
+  aR = ext ? a : ((-t2 > t1) ? T(3) * a - T(2) * l : r);
+}
+
+template <typename T>
+__device__ __forceinline__ T avg_right(T aL, T aR, T a6, T s) {
+  T da = aR - aL;
+  return aR - (T(0.5) * s) * (da - (T(1) - T(2.0 / 3.0) * s) * a6);
+}
+
+template <typename T>
+__device__ __forceinline__ T avg_left(T aL, T aR, T a6, T s) {
+  T da = aR - aL;
+  return aL + (T(0.5) * s) * (da + (T(1) - T(2.0 / 3.0) * s) * a6);
+}
+
+// Characteristic tracing of one cell to its two edges at the half step.
+// W = cell-centre primitives, aL/aR = monotone edge values; outputs the state
+// at the left edge (Wm, right state of interface j-1/2) and at the right edge
+// (Wp, left state of interface j+1/2).
+template <typename T>
+__device__ __forceinline__ void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
+                                      const Gas<T>& gs, T Wm[5], T Wp[5]) {
+  const T rho = W[0], un = W[1], p = W[4];
+  const T csq = (gs.gamma * p) / rho;
+  const T c = vsqrt(csq);
+  T a6[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) a6[q] = T(6) * (W[q] - T(0.5) * (aL[q] + aR[q]));
+  const T lm = un - c, l0 = un, lp = un + c;
+  const T half_rho_c = (T(0.5) * rho) / c;
+  const T half_inv_csq = T(0.5) / csq;
+  const T c_rho = c / rho;
+
+  {  // right edge: waves moving right
+    const T sp = lp * dtdx, s0 = l0 * dtdx, sm = lm * dtdx;
+    T ref[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ref[q] = (lp > T(0)) ? avg_right(aL[q], aR[q], a6[q], sp) : aR[q];
+    T bm = T(0), b0 = T(0);
+    if (lm > T(0))
+      bm = (ref[4] - avg_right(aL[4], aR[4], a6[4], sm)) * half_inv_csq -
+           (ref[1] - avg_right(aL[1], aR[1], a6[1], sm)) * half_rho_c;
+    if (l0 > T(0))
+      b0 = (ref[0] - avg_right(aL[0], aR[0], a6[0], s0)) - (ref[4] - avg_right(aL[4], aR[4], a6[4], s0)) / csq;
+    Wp[0] = vmax(ref[0] - (b0 + bm), T(kRhoFloor));
+    Wp[1] = ref[1] + c_rho * bm;
+    Wp[4] = vmax(ref[4] - csq * bm, T(kPFloor));
+    Wp[2] = (l0 > T(0)) ? avg_right(aL[2], aR[2], a6[2], s0) : ref[2];
+    Wp[3] = (l0 > T(0)) ? avg_right(aL[3], aR[3], a6[3], s0) : ref[3];
+  }
+  {  // left edge: waves moving left
+    const T tm = -lm * dtdx, t0 = -l0 * dtdx, tp = -lp * dtdx;
+    T ref[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ref[q] = (lm < T(0)) ? avg_left(aL[q], aR[q], a6[q], tm) : aL[q];
+    T bp = T(0), b0 = T(0);
+    if (lp < T(0))
+      bp = (ref[4] - avg_left(aL[4], aR[4], a6[4], tp)) * half_inv_csq +
+           (ref[1] - avg_left(aL[1], aR[1], a6[1], tp)) * half_rho_c;
+    if (l0 < T(0))
+      b0 = (ref[0] - avg_left(aL[0], aR[0], a6[0], t0)) - (ref[4] - avg_left(aL[4], aR[4], a6[4], t0)) / csq;
+    Wm[0] = vmax(ref[0] - (b0 + bp), T(kRhoFloor));
+    Wm[1] = ref[1] - c_rho * bp;
+    Wm[4] = vmax(ref[4] - csq * bp, T(kPFloor));
+    Wm[2] = (l0 < T(0)) ? avg_left(aL[2], aR[2], a6[2], t0) : ref[2];
+    Wm[3] = (l0 < T(0)) ? avg_left(aL[3], aR[3], a6[3], t0) : ref[3];
+  }
+}
+
+// Two-shock approximate Riemann solver (Colella & Woodward 1984): fixed
+// Newton steps on p* along shock curves on both sides, u* the Z-weighted
+// mean, sampled at x/t = 0 (u* >= 0 takes the left side), linear in a
+// rarefaction fan between head and tail.  Fluxes (rho, m_n, m_t1, m_t2, E).
+template <typename T>
+__device__ __forceinline__ void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+  const T rL = L[0], uL = L[1], pL = L[4];
+  const T rR = R[0], uR = R[1], pR = R[4];
+  const T CL = vsqrt((gs.gamma * pL) * rL);
+  const T CR = vsqrt((gs.gamma * pR) * rR);
+  T ps = ((CR * pL + CL * pR) + (CL * CR) * (uL - uR)) / (CL + CR);
+  ps = vmax(ps, T(kPFloor));
+  T WLs, WRs, uLs, uRs, ZL, ZR;
+#pragma unroll 1
+  for (int it = 0; it <= kRiemannIters; ++it) {
+    WLs = CL * vsqrt(T(1) + gs.g1 * (ps / pL - T(1)));
+    WRs = CR * vsqrt(T(1) + gs.g1 * (ps / pR - T(1)));
+    uLs = uL - (ps - pL) / WLs;
+    uRs = uR + (ps - pR) / WRs;
+    ZL = ((T(2) * WLs) * WLs) * WLs / (WLs * WLs + CL * CL);
+    ZR = ((T(2) * WRs) * WRs) * WRs / (WRs * WRs + CR * CR);
+    if (it == kRiemannIters) break;
+    ps = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), T(kPFloor));
+  }
+  const T us = (ZL * uLs + ZR * uRs) / (ZL + ZR);
+
+  const bool left = us >= T(0);
+  const T rs = left ? rL : rR;
+  const T u_s = left ? uL : uR;
+  const T p_s = left ? pL : pR;
+  const T W_s = left ? WLs : WRs;
+  const T t1 = left ? L[2] : R[2];
+  const T t2 = left ? L[3] : R[3];
+  const T v_s = left ? -uL : uR;
+  const T v_star = left ? -us : us;
+  const T tau = T(1) / rs - (ps - p_s) / (W_s * W_s);
+  T rstar = (tau > T(0)) ? T(1) / tau : T(kRhoFloor);
+  rstar = vmax(rstar, T(kRhoFloor));
+  const T c_s = vsqrt((gs.gamma * p_s) / rs);
+  const T c_star = vsqrt((gs.gamma * ps) / rstar);
+  const bool shock = ps > p_s;
+  const T head = shock ? v_s + W_s / rs : v_s + c_s;
+  const T tail = shock ? head : v_star + c_star;
+  const bool orig = head <= T(0);
+  const bool star = !orig && (tail > T(0));
+  T r, u, p;
+  if (orig) {
+    r = rs; u = u_s; p = p_s;
+  } else if (star) {
+    r = rstar; u = us; p = ps;
+  } else {
+    const T w = head / (head - tail);
+    r = rs + w * (rstar - rs);
+    u = u_s + w * (us - u_s);
+    p = p_s + w * (ps - p_s);
+  }
+  const T f0 = r * u;
+  F[0] = f0;
+  F[1] = f0 * u + p;
+  F[2] = f0 * t1;
+  F[3] = f0 * t2;
+  const T E = p * gs.inv_gm1 + (T(0.5) * r) * (u * u + (t1 * t1 + t2 * t2));
+  F[4] = u * (E + p);
+}
+
+}  // namespace cello
