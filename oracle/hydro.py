@@ -47,6 +47,15 @@ AXIS_DIM = {0: 4, 1: 3, 2: 2}   # tensor dim of an axis in U[B, 5, z, y, x]
 
 
 # ----------------------------------------------------------------- 1-D PPM
+def ieee_sqrt(x):
+    """Correctly rounded float64 square root.  torch's vectorised CPU sqrt
+    is not always correctly rounded (1 ulp off for about 1% of inputs); the
+    value here is numpy's IEEE sqrt, the gradient torch's."""
+    s = torch.sqrt(x)
+    exact = torch.from_numpy(np.sqrt(x.detach().cpu().numpy())).to(s.device)
+    return s + (exact - s).detach()
+
+
 def primitives(rho_c, mn, mt1, mt2, E, gamma):
     """Conserved -> primitive (rho, u_n, u_t1, u_t2, p) with density and
     pressure floors.  Kinetic energy 0.5*rho*(u_n^2 + (u_t1^2 + u_t2^2))."""
@@ -123,7 +132,7 @@ def trace(W, aL, aR, dtdx, gamma):
     each (rho, u_n, u_t1, u_t2, p), floored."""
     rho, un, p = W[0], W[1], W[4]
     csq = (gamma * p) / rho
-    c = torch.sqrt(csq)
+    c = ieee_sqrt(csq)
     a6 = [6.0 * (W[q] - 0.5 * (aL[q] + aR[q])) for q in range(5)]
     lm, l0, lp = un - c, un, un + c
     half_rho_c = (0.5 * rho) / c
@@ -172,14 +181,14 @@ def riemann_flux(WL, WR, gamma):
     rL, uL, t1L, t2L, pL = WL
     rR, uR, t1R, t2R, pR = WR
     g1 = (gamma + 1.0) / (2.0 * gamma)
-    CL = torch.sqrt((gamma * pL) * rL)
-    CR = torch.sqrt((gamma * pR) * rR)
+    CL = ieee_sqrt((gamma * pL) * rL)
+    CR = ieee_sqrt((gamma * pR) * rR)
     ps = ((CR * pL + CL * pR) + (CL * CR) * (uL - uR)) / (CL + CR)
     ps = torch.clamp_min(ps, P_FLOOR)
 
     def curves(ps):
-        WLs = CL * torch.sqrt(1.0 + g1 * (ps / pL - 1.0))
-        WRs = CR * torch.sqrt(1.0 + g1 * (ps / pR - 1.0))
+        WLs = CL * ieee_sqrt(1.0 + g1 * (ps / pL - 1.0))
+        WRs = CR * ieee_sqrt(1.0 + g1 * (ps / pR - 1.0))
         uLs = uL - (ps - pL) / WLs
         uRs = uR + (ps - pR) / WRs
         ZL = ((2.0 * WLs) * WLs) * WLs / (WLs * WLs + CL * CL)
@@ -205,8 +214,8 @@ def riemann_flux(WL, WR, gamma):
     rstar = torch.where(tau > 0.0, 1.0 / torch.where(tau > 0.0, tau, torch.ones_like(tau)),
                         torch.full_like(tau, RHO_FLOOR))
     rstar = torch.clamp_min(rstar, RHO_FLOOR)
-    c_s = torch.sqrt((gamma * p_s) / rs)
-    c_star = torch.sqrt((gamma * ps) / rstar)
+    c_s = ieee_sqrt((gamma * p_s) / rs)
+    c_star = ieee_sqrt((gamma * ps) / rstar)
     shock = ps > p_s
     head = torch.where(shock, v_s + W_s / rs, v_s + c_s)
     tail = torch.where(shock, head, v_star + c_star)
@@ -268,6 +277,13 @@ def dx_of_leaves(mesh: Mesh):
     return torch.tensor([d.dx(int(L)) for L in mesh.leaves[:, 0]], dtype=torch.float64)
 
 
+def dtdx_of_leaves(mesh: Mesh, dt: float):
+    """dt/dx per leaf, each a correctly rounded float64 quotient (torch would
+    evaluate a scalar over a tensor as a reciprocal times the scalar)."""
+    d = mesh.desc
+    return torch.tensor([dt / d.dx(int(L)) for L in mesh.leaves[:, 0]], dtype=torch.float64)
+
+
 def sweep(U, mesh: Mesh, axis: int, dt: float, rows):
     """One directional PPM sweep of every leaf.  rows = ((lo, hi), (lo, hi))
     ranges of the two transverse tensor dims (in their U order) whose pencils
@@ -280,7 +296,7 @@ def sweep(U, mesh: Mesh, axis: int, dt: float, rows):
     dim = AXIS_DIM[axis]
     comp = AXIS_COMPONENTS[axis]
     V = U.movedim(dim, -1)
-    dtdx = (dt / dx_of_leaves(mesh)).view(B, 1, 1, 1)
+    dtdx = dtdx_of_leaves(mesh, dt).view(B, 1, 1, 1)
     F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma)
     (a0, a1), (b0, b1) = rows
     V2 = V.clone()
@@ -564,7 +580,7 @@ def reduce_dt_totals(U, mesh: Mesh, cfl: float):
     n, g = d.n, d.ghosts
     I = U[:, :, g:g + n, g:g + n, g:g + n]
     rho, u, v, w, p = lab_primitives(I, d.gamma)
-    c = torch.sqrt((d.gamma * p) / rho)
+    c = ieee_sqrt((d.gamma * p) / rho)
     s = torch.maximum(torch.abs(u), torch.maximum(torch.abs(v), torch.abs(w))) + c
     dx = dx_of_leaves(mesh).view(-1, 1, 1, 1)
     dt = cfl * float(torch.min(dx / s))

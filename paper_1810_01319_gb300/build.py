@@ -78,5 +78,23 @@ def build(verbose: bool = False, force: bool = False) -> str:
     return LIB
 
 
+HOSTCHECK = os.path.join(BUILD, "libcello_hostcheck.so")
+
+
+def build_hostcheck() -> str:
+    """Host-compiled copy of the per-interface arithmetic and its adjoint
+    (csrc/hostcheck.cu), used only by the CPU unit tests."""
+    os.makedirs(BUILD, exist_ok=True)
+    src = os.path.join(CSRC, "hostcheck.cu")
+    deps = [src] + [os.path.join(CSRC, f) for f in ("ppm.cuh", "adjoint.cuh")]
+    if _stale(HOSTCHECK, deps):
+        cmd = [nvcc(), *ARCH, "-O2", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", CSRC,
+               "-shared", src, "-o", HOSTCHECK]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on hostcheck.cu:\n{r.stderr}")
+    return HOSTCHECK
+
+
 if __name__ == "__main__":
     print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))

@@ -1,0 +1,42 @@
+// Host-compiled entry points of the per-interface PPM arithmetic and its
+// hand-written adjoint, for CPU unit tests of the device math (the same
+// CELLO_HD functions the kernels run).  Built into a separate test library;
+// the product library does not contain it.
+#include "adjoint.cuh"
+
+using namespace cello;
+
+template <typename T>
+static void flux_t(const double* U, double dtdx, double gamma, double* F) {
+  T u[8][5], f[5];
+  for (int c = 0; c < 8; ++c)
+    for (int k = 0; k < 5; ++k) u[c][k] = T(U[c * 5 + k]);
+  window_flux(u, T(dtdx), Gas<T>::make(gamma), f);
+  for (int k = 0; k < 5; ++k) F[k] = double(f[k]);
+}
+
+template <typename T>
+static void vjp_t(const double* U, double dtdx, double gamma, const double* Fb, double* Ub) {
+  T u[8][5], fb[5], ub[8][5];
+  for (int c = 0; c < 8; ++c)
+    for (int k = 0; k < 5; ++k) {
+      u[c][k] = T(U[c * 5 + k]);
+      ub[c][k] = T(0);
+    }
+  for (int k = 0; k < 5; ++k) fb[k] = T(Fb[k]);
+  window_flux_vjp(u, T(dtdx), Gas<T>::make(gamma), fb, ub);
+  for (int c = 0; c < 8; ++c)
+    for (int k = 0; k < 5; ++k) Ub[c * 5 + k] = double(ub[c][k]);
+}
+
+extern "C" {
+void cello_hc_window_flux(const double* U, double dtdx, double gamma, int precision, double* F) {
+  if (precision == 4) flux_t<float>(U, dtdx, gamma, F);
+  else flux_t<double>(U, dtdx, gamma, F);
+}
+void cello_hc_window_flux_vjp(const double* U, double dtdx, double gamma, int precision, const double* Fb,
+                              double* Ub) {
+  if (precision == 4) vjp_t<float>(U, dtdx, gamma, Fb, Ub);
+  else vjp_t<double>(U, dtdx, gamma, Fb, Ub);
+}
+}

@@ -7,6 +7,12 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+#ifndef CELLO_HD
+#define CELLO_HD __host__ __device__ __forceinline__
+#endif
+
 namespace cello {
 
 constexpr double kRhoFloor = 1e-10;
@@ -16,14 +22,14 @@ constexpr double kOmega1 = 0.75;     // flattening ratio offset
 constexpr double kOmega2 = 10.0;     // flattening ratio slope
 constexpr int kRiemannIters = 5;     // fixed Newton steps, no early exit
 
-template <typename T> __device__ __forceinline__ T vmax(T a, T b) { return a > b ? a : b; }
-template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return a < b ? a : b; }
-__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
-__device__ __forceinline__ double vabs(double a) { return fabs(a); }
-__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
-__device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ float vcopysign(float a, float b) { return copysignf(a, b); }
-__device__ __forceinline__ double vcopysign(double a, double b) { return copysign(a, b); }
+template <typename T> CELLO_HD T vmax(T a, T b) { return a > b ? a : b; }
+template <typename T> CELLO_HD T vmin(T a, T b) { return a < b ? a : b; }
+CELLO_HD float vabs(float a) { return fabsf(a); }
+CELLO_HD double vabs(double a) { return fabs(a); }
+CELLO_HD float vsqrt(float a) { return sqrtf(a); }
+CELLO_HD double vsqrt(double a) { return sqrt(a); }
+CELLO_HD float vcopysign(float a, float b) { return copysignf(a, b); }
+CELLO_HD double vcopysign(double a, double b) { return copysign(a, b); }
 
 // Gas constants in the working precision, derived once in float64.
 template <typename T> struct Gas {
@@ -40,7 +46,7 @@ template <typename T> struct Gas {
 
 // Conserved (rho, m_n, m_t1, m_t2, E) -> primitive (rho, u_n, u_t1, u_t2, p).
 template <typename T>
-__device__ __forceinline__ void to_primitive(const T U[5], const Gas<T>& gs, T W[5]) {
+CELLO_HD void to_primitive(const T U[5], const Gas<T>& gs, T W[5]) {
   T rho = vmax(U[0], T(kRhoFloor));
   T un = U[1] / rho;
   T ut1 = U[2] / rho;
@@ -52,7 +58,7 @@ __device__ __forceinline__ void to_primitive(const T U[5], const Gas<T>& gs, T W
 
 // Monotonised centred slope, zero at a local extremum.
 template <typename T>
-__device__ __forceinline__ T limited_slope(T am, T a0, T ap) {
+CELLO_HD T limited_slope(T am, T a0, T ap) {
   T dl = a0 - am;
   T dr = ap - a0;
   T da = T(0.5) * (ap - am);
@@ -62,13 +68,13 @@ __device__ __forceinline__ T limited_slope(T am, T a0, T ap) {
 
 // Interface value between cells j and j+1 in limited form.
 template <typename T>
-__device__ __forceinline__ T interface_value(T a0, T a1, T dm0, T dm1) {
+CELLO_HD T interface_value(T a0, T a1, T dm0, T dm1) {
   return T(0.5) * (a0 + a1) - (dm1 - dm0) * T(1.0 / 6.0);
 }
 
 // Shock detector of the flattening coefficient.
 template <typename T>
-__device__ __forceinline__ T flatten_tilde(T pm2, T pm1, T pp1, T pp2, T um1, T up1) {
+CELLO_HD T flatten_tilde(T pm2, T pm1, T pp1, T pp2, T um1, T up1) {
   T dp1 = pp1 - pm1;
   T dp2 = pp2 - pm2;
   bool shock = (vabs(dp1) > T(kEpsShock) * vmin(pp1, pm1)) && (um1 - up1 > T(0)) && (dp2 != T(0));
@@ -79,7 +85,7 @@ __device__ __forceinline__ T flatten_tilde(T pm2, T pm1, T pp1, T pp2, T um1, T 
 
 // Flatten towards the cell value, then apply the monotonicity constraints.
 template <typename T>
-__device__ __forceinline__ void flatten_monotone(T a, T f, T& aL, T& aR) {
+CELLO_HD void flatten_monotone(T a, T f, T& aL, T& aR) {
   T l = f * a + (T(1) - f) * aL;
   T r = f * a + (T(1) - f) * aR;
   bool ext = (r - a) * (a - l) <= T(0);
@@ -92,13 +98,13 @@ __device__ __forceinline__ void flatten_monotone(T a, T f, T& aL, T& aR) {
 }
 
 template <typename T>
-__device__ __forceinline__ T avg_right(T aL, T aR, T a6, T s) {
+CELLO_HD T avg_right(T aL, T aR, T a6, T s) {
   T da = aR - aL;
   return aR - (T(0.5) * s) * (da - (T(1) - T(2.0 / 3.0) * s) * a6);
 }
 
 template <typename T>
-__device__ __forceinline__ T avg_left(T aL, T aR, T a6, T s) {
+CELLO_HD T avg_left(T aL, T aR, T a6, T s) {
   T da = aR - aL;
   return aL + (T(0.5) * s) * (da + (T(1) - T(2.0 / 3.0) * s) * a6);
 }
@@ -108,7 +114,7 @@ __device__ __forceinline__ T avg_left(T aL, T aR, T a6, T s) {
 // at the left edge (Wm, right state of interface j-1/2) and at the right edge
 // (Wp, left state of interface j+1/2).
 template <typename T>
-__device__ __forceinline__ void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
+CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
                                       const Gas<T>& gs, T Wm[5], T Wp[5]) {
   const T rho = W[0], un = W[1], p = W[4];
   const T csq = (gs.gamma * p) / rho;
@@ -162,7 +168,7 @@ __device__ __forceinline__ void trace(const T W[5], const T aL[5], const T aR[5]
 // mean, sampled at x/t = 0 (u* >= 0 takes the left side), linear in a
 // rarefaction fan between head and tail.  Fluxes (rho, m_n, m_t1, m_t2, E).
 template <typename T>
-__device__ __forceinline__ void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+CELLO_HD void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
   const T rL = L[0], uL = L[1], pL = L[4];
   const T rR = R[0], uR = R[1], pR = R[4];
   const T CL = vsqrt((gs.gamma * pL) * rL);

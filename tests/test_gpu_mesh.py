@@ -45,7 +45,9 @@ def test_refine_flags_bit_exact(precision, field):
     om, flags = H.ic_refined(od, "blobs", count=16, seed=4)
     gm = H.gpu_mesh_from_flags(od, flags, precision)
     U0 = H.state(od, om.leaves, "blobs", count=16, seed=4)
-    U0[:, 4] *= 1.0 + 0.2 * torch.rand(U0[:, 4].shape, generator=torch.Generator().manual_seed(1), dtype=torch.float64)
+    # pressure jumps large enough to flag some leaves on the pressure criterion
+    U0[:, 4] *= 1.0 + 0.8 * (torch.rand(U0[:, 4].shape, generator=torch.Generator().manual_seed(1),
+                                        dtype=torch.float64) > 0.999)
     Ug = U0.to(gm.dtype).cuda().contiguous()
     gm.ghost_refresh(Ug)
     fg = gm.refine_flags(Ug, field, 0.3, 0.075).cpu().numpy()
