@@ -124,6 +124,19 @@ cello_status cello_ghost_refresh(cello_mesh* mesh, void* U, void* stream);
 cello_status cello_hydro_step(cello_mesh* mesh, void* U, const double* dt_dev, int cycle, double cfl,
                               double* dt_next_dev, double* totals_dev, void* stream);
 
+/* Adjoint of one hydro step with dt held fixed (the reverse of the PPM
+ * sweeps of Sec. II.C and of the ghost copy of Sec. II.B):
+ * lam_inout holds the adjoint of the state after the step (interior cells;
+ * ghost entries are ignored) and receives the adjoint of the state U_n at
+ * the start of the step (ghost entries zero).  U_n is read only; cycle and
+ * dt_dev must be those of the forward step.  At a kink (min, max, branch)
+ * the derivative of the branch taken in the forward pass is used.  Needs a
+ * single-level, fully periodic mesh (no coarse-fine faces); the library
+ * keeps three states of device scratch per mesh for the recomputed forward
+ * sweeps. */
+cello_status cello_hydro_adjoint_step(cello_mesh* mesh, const void* U_n, void* lam_inout,
+                                      const double* dt_dev, int cycle, void* stream);
+
 /* The CFL dt and conserved totals of the current state (as after a step). */
 cello_status cello_reduce(cello_mesh* mesh, const void* U, double cfl, double* dt_next_dev,
                           double* totals_dev, void* stream);

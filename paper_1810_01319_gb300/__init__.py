@@ -112,6 +112,14 @@ class Mesh:
         _lib.check(_lib.lib().cello_hydro_step(self.handle, _ptr(U), _ptr(dt), int(cycle), float(cfl),
                                                _ptr(dt_next), _ptr(totals), _stream(stream)), "cello_hydro_step")
 
+    def hydro_adjoint_step(self, U_n, lam, dt, cycle, stream=None):
+        """lam (adjoint of the state after the step) -> adjoint of U_n, in
+        place; dt as in the forward step (held fixed)."""
+        self._check_state(U_n)
+        self._check_state(lam)
+        _lib.check(_lib.lib().cello_hydro_adjoint_step(self.handle, _ptr(U_n), _ptr(lam), _ptr(dt), int(cycle),
+                                                       _stream(stream)), "cello_hydro_adjoint_step")
+
     def reduce(self, U, cfl=0.4, dt_next=None, totals=None, stream=None):
         self._check_state(U)
         _lib.check(_lib.lib().cello_reduce(self.handle, _ptr(U), float(cfl), _ptr(dt_next), _ptr(totals),

@@ -23,7 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", INCLUDE, "-I", CSRC]
 UNITS = {
-    "k_f32.cu": [],
+    # float32 bulk path: hardware-approximate division and square root
+    "k_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "k_f64.cu": ["-fmad=false"],
     "table.cu": [],
     "mesh.cu": [],

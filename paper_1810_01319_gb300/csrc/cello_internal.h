@@ -10,6 +10,7 @@ namespace cello {
 constexpr int kGhosts = 4;
 constexpr int kFields = 5;
 constexpr int kPencilsPerTile = 8;   // pencils per sweep CTA
+constexpr int kAdjPencils = 4;       // pencils per adjoint-sweep CTA
 
 // Neighbour kinds of the 27-entry table.
 enum NbKind : int8_t { kSame = 0, kCoarse = 1, kFine = 2, kBoundary = 3 };
@@ -57,6 +58,17 @@ struct SweepParams {
   int n_items;
 };
 
+struct AdjSweepParams {
+  const void* U;           // state entering the forward sweep (ghosts refreshed)
+  void* lam;               // adjoint, updated in place
+  int leaf0, nleaf;
+  int axis;
+  int a0, a1, b0, b1;
+  int tiles_per_leaf;
+  const double* dt;
+  int n_items;
+};
+
 // One-time kernel attribute set-up (dynamic shared memory limits), done
 // outside any stream capture.
 void prepare_kernels();
@@ -75,6 +87,10 @@ void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace*
                      cudaStream_t s);
 void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
                    double* dt_next, double* totals, cudaStream_t s);
+void launch_adjoint_sweep_f32(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
+void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
+void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStream_t s);
+void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);
 

@@ -3,13 +3,14 @@
 // results round exactly like the same formulas evaluated term by term.
 #define CELLO_DEFINE_FINISH_KERNEL
 #include "kernels.cuh"
+#include "adjoint_kernels.cuh"
 
 namespace cello {
 
 template <int NB, int P>
 static void sweep_f64_n(const DevMesh& m, const SweepParams& p, cudaStream_t s) {
   constexpr int N = NB + 2 * kGhosts;
-  const size_t smem = sizeof(double) * 21 * N * (P + 1);
+  const size_t smem = sizeof(double) * 21 * N * P;
   auto k = sweep_kernel<double, NB, P>;
   k<<<p.n_items, N * P, smem, s>>>(m, p);
 }
@@ -18,10 +19,40 @@ template <int NB, int P>
 static void prepare_n() {
   constexpr int N = NB + 2 * kGhosts;
   cudaFuncSetAttribute(sweep_kernel<double, NB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(double) * 21 * N * (P + 1)));
+                       (int)(sizeof(double) * 21 * N * P));
+}
+
+template <int NB, int P>
+static size_t adj_smem() {
+  constexpr int N = NB + 2 * kGhosts;
+  return sizeof(double) * (10 * N * (P + 1) + (NB + 1) * 40 * P);
+}
+
+template <int NB>
+static void prepare_adj() {
+  cudaFuncSetAttribute(adjoint_sweep_kernel<double, NB, kAdjPencils>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)adj_smem<NB, kAdjPencils>());
+}
+
+template <int NB>
+static void adj_sweep_n(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  adjoint_sweep_kernel<double, NB, kAdjPencils><<<p.n_items, N * kAdjPencils, adj_smem<NB, kAdjPencils>(), s>>>(m, p);
+}
+
+void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s) {
+  if (p.n_items <= 0) return;
+  switch (m.n) {
+    case 8: adj_sweep_n<8>(m, p, s); break;
+    case 16: adj_sweep_n<16>(m, p, s); break;
+    case 32: adj_sweep_n<32>(m, p, s); break;
+  }
 }
 
 void prepare_kernels_f64() {
+  prepare_adj<8>();
+  prepare_adj<16>();
+  prepare_adj<32>();
   prepare_n<8, kPencilsPerTile>();
   prepare_n<16, kPencilsPerTile>();
   prepare_n<32, kPencilsPerTile>();
@@ -79,6 +110,46 @@ void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, d
   if (precision == 4) { CELLO_RED(float) } else { CELLO_RED(double) }
 #undef CELLO_RED
   reduce_finish_kernel<<<1, 1024, 0, s>>>(partials, m.B, cfl, dt_next, totals);
+}
+
+template <typename T, int NB>
+static void adj_refresh_n(const DevMesh& m, T* lam, cudaStream_t s) {
+  const long cells = (long)m.B * NB * NB * NB;
+  adjoint_refresh_gather_kernel<T, NB><<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(m, lam);
+  constexpr int N = NB + 2 * kGhosts;
+  const long ng = (long)m.B * ((long)N * N * N - (long)NB * NB * NB);
+  zero_ghosts_kernel<T, NB><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(lam, m.B);
+}
+
+template <typename T, int NB>
+static void zero_n(const DevMesh& m, T* lam, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  const long ng = (long)m.B * ((long)N * N * N - (long)NB * NB * NB);
+  zero_ghosts_kernel<T, NB><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(lam, m.B);
+}
+
+void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStream_t s) {
+  if (m.B <= 0) return;
+#define CELLO_AR(T)                                                  \
+  switch (m.n) {                                                     \
+    case 8: adj_refresh_n<T, 8>(m, static_cast<T*>(lam), s); break;  \
+    case 16: adj_refresh_n<T, 16>(m, static_cast<T*>(lam), s); break;\
+    case 32: adj_refresh_n<T, 32>(m, static_cast<T*>(lam), s); break;\
+  }
+  if (precision == 4) { CELLO_AR(float) } else { CELLO_AR(double) }
+#undef CELLO_AR
+}
+
+void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s) {
+  if (m.B <= 0) return;
+#define CELLO_ZG(T)                                           \
+  switch (m.n) {                                              \
+    case 8: zero_n<T, 8>(m, static_cast<T*>(lam), s); break;  \
+    case 16: zero_n<T, 16>(m, static_cast<T*>(lam), s); break;\
+    case 32: zero_n<T, 32>(m, static_cast<T*>(lam), s); break;\
+  }
+  if (precision == 4) { CELLO_ZG(float) } else { CELLO_ZG(double) }
+#undef CELLO_ZG
 }
 
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,

@@ -19,8 +19,9 @@ __device__ __forceinline__ T minmod(T a, T b) {
 
 // =====================================================================
 // Directional PPM sweep.  One CTA item = P pencils of one leaf; a thread
-// owns one cell of one pencil.  Shared arrays are [5][N][P+1] (pencil
-// fastest, padded against bank conflicts).  Phases:
+// owns one cell of one pencil (pencil index fastest across the threads of a
+// warp).  Shared arrays are [5][N][P], pencil fastest, so that a warp's
+// accesses at one stencil offset fall in consecutive banks.  Phases:
 //   1 load + primitives  2 limited slopes, shock detector  3 interface
 //   values  4 flatten + monotone + trace  5 Riemann flux (+ face registers)
 //   6 conservative update of cells g..g+n-1.
@@ -28,7 +29,7 @@ __device__ __forceinline__ T minmod(T a, T b) {
 template <typename T, int NB, int P>
 __global__ void __launch_bounds__((NB + 8) * P)
 sweep_kernel(DevMesh m, SweepParams prm) {
-  constexpr int G = kGhosts, N = NB + 2 * G, S = P + 1, A = N * S;
+  constexpr int G = kGhosts, N = NB + 2 * G, S = P, A = N * S;
   constexpr long SLAB = (long)N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sW = reinterpret_cast<T*>(smem_raw);
@@ -50,9 +51,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
   comp[3] = axis == 2 ? 2 : 3;
 
   const int t = threadIdx.x;
-  const int lc = axis == 0 ? t % N : t / P;   // load mapping: cell
-  const int lp = axis == 0 ? t / N : t % P;   //               pencil
-  const int cp = t % P, cj = t / P;           // compute mapping
+  const int lc = t / P, lp = t % P;           // this thread's cell and pencil
+  const int cp = lp, cj = lc;
 
   for (int item = blockIdx.x; item < prm.n_items; item += gridDim.x) {
     const int leaf = prm.leaf0 + item / prm.tiles_per_leaf;

@@ -149,6 +149,8 @@ struct cello_mesh {
   double* d_reg = nullptr;
   double* d_partials = nullptr;
   int exec_mode = CELLO_EXEC_BATCHED;
+  void* adj_scratch = nullptr;   // three states for the adjoint's forward recomputation
+  size_t adj_bytes = 0;
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
 
@@ -178,6 +180,8 @@ struct cello_mesh {
     graphs.clear();
     if (capture_stream) cudaStreamDestroy(capture_stream);
     capture_stream = nullptr;
+    if (adj_scratch) cudaFree(adj_scratch);
+    adj_scratch = nullptr;
     void* ptrs[] = {d_leaf, d_keys, d_kind, d_idx, d_fine8, d_face_slot, d_cfaces, d_group_start, d_reg, d_partials};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -386,12 +390,24 @@ void launch_refresh(const cello_mesh* M, const DevMesh& dm, void* U, int leaf0, 
   else launch_refresh_f64(dm, static_cast<double*>(U), leaf0, nleaf, s);
 }
 
+// Transverse pencil ranges of a sweep along `axis`: a transverse axis already
+// swept this step needs interior rows only, one not yet swept all N rows.
+void sweep_ranges(const cello_mesh* M, int axis, const bool swept[3], int& a0, int& a1, int& b0, int& b1) {
+  const int n = M->desc.n, g = M->desc.ghosts, N = M->N;
+  const int ta = axis == 2 ? 1 : 2;   // transverse A: z, or y for the z sweep
+  const int tb = axis == 0 ? 1 : 0;   // transverse B: y for the x sweep, else x
+  a0 = swept[ta] ? g : 0;
+  a1 = swept[ta] ? g + n : N;
+  b0 = swept[tb] ? g : 0;
+  b1 = swept[tb] ? g + n : N;
+}
+
 // The launch sequence of one step on stream s.
 void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, double cfl, double* dt_next,
                   double* totals, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const cello_mesh_desc& d = M->desc;
   const DevMesh dm = M->dev();
-  const int B = M->B, n = d.n, g = d.ghosts, N = M->N;
+  const int B = M->B;
   const bool plain = M->exec_mode == CELLO_EXEC_PLAIN && !ev;
   if (ev) cudaEventRecord(ev[0], s);
   if (plain)
@@ -403,15 +419,10 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
   bool swept[3] = {false, false, false};
   for (int oi = 0; oi < 3; ++oi) {
     const int axis = order[oi];
-    const int ta = axis == 2 ? 1 : 2;   // transverse A: z, or y for the z sweep
-    const int tb = axis == 0 ? 1 : 0;   // transverse B: y for the x sweep, else x
     SweepParams p{};
     p.U = U;
     p.axis = axis;
-    p.a0 = swept[ta] ? g : 0;
-    p.a1 = swept[ta] ? g + n : N;
-    p.b0 = swept[tb] ? g : 0;
-    p.b1 = swept[tb] ? g + n : N;
+    sweep_ranges(M, axis, swept, p.a0, p.a1, p.b0, p.b1);
     const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
     p.tiles_per_leaf = (pencils + kPencilsPerTile - 1) / kPencilsPerTile;
     p.dt = dt;
@@ -441,6 +452,76 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
   if (ev) cudaEventRecord(ev[5], s);
   if (dt_next || totals || ev) launch_reduce(dm, U, d.precision, cfl, M->d_partials, dt_next, totals, s);
   if (ev) cudaEventRecord(ev[6], s);
+}
+
+cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double* dt, int cycle, cudaStream_t s) {
+  const cello_mesh_desc& d = M->desc;
+  for (int a = 0; a < 3; ++a)
+    if (d.bc[a] != CELLO_PERIODIC) return fail(CELLO_EINVAL, "the adjoint step needs periodic boundaries");
+  for (int b = 1; b < M->B; ++b)
+    if (M->leaves[b].x != M->leaves[0].x) return fail(CELLO_EINVAL, "the adjoint step needs a single-level mesh");
+  const size_t state = (size_t)M->B * 5 * M->N * M->N * M->N * d.precision;
+  if (M->adj_bytes < 3 * state) {
+    if (M->adj_scratch) cudaFree(M->adj_scratch);
+    M->adj_scratch = nullptr;
+    M->adj_bytes = 0;
+    CELLO_CUDA(cudaMalloc(&M->adj_scratch, 3 * state));
+    M->adj_bytes = 3 * state;
+  }
+  char* S0 = static_cast<char*>(M->adj_scratch);
+  char* S1 = S0 + state;
+  char* S2 = S1 + state;
+  const DevMesh dm = M->dev();
+  const int B = M->B;
+  // forward recomputation: refreshed start state, then the states entering
+  // the second and third sweeps
+  CELLO_CUDA(cudaMemcpyAsync(S0, Un, state, cudaMemcpyDeviceToDevice, s));
+  launch_refresh(M, dm, S0, 0, B, s);
+  const int order[3] = {cycle % 2 == 0 ? 0 : 2, 1, cycle % 2 == 0 ? 2 : 0};
+  char* entry[3] = {S0, S1, S2};
+  bool swept[3] = {false, false, false};
+  int rng[3][4];
+  for (int oi = 0; oi < 3; ++oi) {
+    const int axis = order[oi];
+    sweep_ranges(M, axis, swept, rng[oi][0], rng[oi][1], rng[oi][2], rng[oi][3]);
+    if (oi < 2) {
+      CELLO_CUDA(cudaMemcpyAsync(entry[oi + 1], entry[oi], state, cudaMemcpyDeviceToDevice, s));
+      SweepParams p{};
+      p.U = entry[oi + 1];
+      p.axis = axis;
+      p.a0 = rng[oi][0]; p.a1 = rng[oi][1]; p.b0 = rng[oi][2]; p.b1 = rng[oi][3];
+      const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
+      p.tiles_per_leaf = (pencils + kPencilsPerTile - 1) / kPencilsPerTile;
+      p.dt = dt;
+      p.reg = nullptr;
+      p.leaf0 = 0;
+      p.nleaf = B;
+      p.n_items = B * p.tiles_per_leaf;
+      if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
+      else launch_sweep_f64(dm, p, pencils, s);
+    }
+    swept[axis] = true;
+  }
+  // reverse: the adjoint of U_{n+1} lives on interior cells only
+  launch_zero_ghosts(dm, lam, d.precision, s);
+  for (int oi = 2; oi >= 0; --oi) {
+    AdjSweepParams p{};
+    p.U = entry[oi];
+    p.lam = lam;
+    p.axis = order[oi];
+    p.a0 = rng[oi][0]; p.a1 = rng[oi][1]; p.b0 = rng[oi][2]; p.b1 = rng[oi][3];
+    const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
+    p.tiles_per_leaf = (pencils + kAdjPencils - 1) / kAdjPencils;
+    p.dt = dt;
+    p.leaf0 = 0;
+    p.nleaf = B;
+    p.n_items = B * p.tiles_per_leaf;
+    if (d.precision == 4) launch_adjoint_sweep_f32(dm, p, s);
+    else launch_adjoint_sweep_f64(dm, p, s);
+  }
+  launch_adjoint_refresh(dm, lam, d.precision, s);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
 }
 
 }  // namespace
@@ -572,6 +653,13 @@ cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycl
   M->graphs.push_back(GraphEntry{U, dt, parity, cfl, dt_next, totals, exec});
   CELLO_CUDA(cudaGraphLaunch(exec, s));
   return CELLO_OK;
+}
+
+cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, const double* dt, int cycle,
+                                      void* stream) {
+  if (!M || !Un || !lam || !dt) return fail(CELLO_EINVAL, "NULL argument");
+  if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
+  return adjoint_step(M, Un, lam, dt, cycle, (cudaStream_t)stream);
 }
 
 cello_status cello_profile_step(cello_mesh* M, void* U, const double* dt, int cycle, double cfl, float* phase_ms,

@@ -1,0 +1,135 @@
+"""GPU adjoint of the hydro step (dt fixed) against torch autograd through
+the float64 oracle, against central finite differences of the GPU forward,
+and float32 against float64."""
+import numpy as np
+import pytest
+import torch
+
+import helpers as H
+from oracle import hydro as OH
+from oracle import mesh as OM
+
+pytestmark = pytest.mark.gpu
+
+
+def _periodic(root=(2, 2, 2), n=8):
+    od = OM.Desc(root=root, n=n, ghosts=4, max_level=0, bc=(OM.PERIODIC,) * 3, gamma=5.0 / 3.0,
+                 hi=tuple(r / max(root) for r in root))
+    return od, OM.root_mesh(od)
+
+
+def _moving_state(od, om, seed):
+    U = H.state(od, om.leaves, "blobs", count=6, seed=seed)
+    g = torch.Generator().manual_seed(seed)
+    U[:, 0] *= 1.0 + 0.2 * torch.rand(U[:, 0].shape, generator=g, dtype=torch.float64)
+    U[:, 4] *= 1.0 + 0.5 * torch.rand(U[:, 4].shape, generator=g, dtype=torch.float64)
+    return U
+
+
+@pytest.mark.parametrize("steps,n", [(1, 8), (2, 8), (3, 16)])
+def test_adjoint_matches_oracle_autograd(steps, n):
+    od, om = _periodic(n=n)
+    U0 = _moving_state(od, om, 3)
+    _, dts = OH.run(U0, om, steps, 0.4)
+    w = torch.randn(U0.shape, generator=torch.Generator().manual_seed(7), dtype=torch.float64)
+    g4 = od.ghosts
+    wi = torch.zeros_like(w)
+    wi[:, :, g4:g4 + n, g4:g4 + n, g4:g4 + n] = w[:, :, g4:g4 + n, g4:g4 + n, g4:g4 + n]
+    # oracle gradient of sum(w * U_final) by autograd
+    Ut = U0.clone().requires_grad_(True)
+    plan = OH.RefreshPlan(om)
+    V = Ut
+    for s, dt in enumerate(dts):
+        V = OH.step(V, om, dt, s, plan)
+    (go,) = torch.autograd.grad((V * wi).sum(), Ut)
+    # GPU adjoint
+    gm = H.gpu_mesh_from_flags(od, [], 8)
+    U = U0.cuda().contiguous()
+    states = []
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for s, v in enumerate(dts):
+        states.append(U.clone())
+        dt.fill_(v)
+        gm.hydro_step(U, dt, s)
+    lam = wi.cuda().contiguous()
+    for s in range(steps - 1, -1, -1):
+        dt.fill_(dts[s])
+        gm.hydro_adjoint_step(states[s], lam, dt, s)
+    torch.cuda.synchronize()
+    gg = lam.cpu()
+    err = float((gg - go).abs().max() / go.abs().max())
+    assert err < 1e-10, err
+
+
+def _loss(gm, rho0, base, dts, target, every=5):
+    from paper_1810_01319_gb300.autograd import rollout
+    U0 = base.clone()
+    U0[:, 0] = rho0
+    U0[:, 4] = base[:, 4]                 # p = 1, v = 0: E does not depend on rho
+    Uf = rollout(gm, U0, dts, 0, every)
+    g = 4
+    n = gm.desc.n
+    rho = Uf[:, 0, g:g + n, g:g + n, g:g + n]
+    return ((rho - target) ** 2).sum()
+
+
+@pytest.mark.parametrize("root,n,steps,ndir", [((2, 2, 2), 16, 20, 6)])
+def test_gradient_against_finite_differences(root, n, steps, ndir):
+    """Adjoint workload: rho0 = 1 + 0.1 GRF(k^-2, seed 0), p = 1, v = 0,
+    gamma 5/3, periodic; loss = sum (rho_final - rho_target)^2 with the
+    target from seed 1; gradient wrt rho0 checked on random directions by
+    central differences (float64, frozen dt)."""
+    od, om = _periodic(root=root, n=n)
+    gm = H.gpu_mesh_from_flags(od, [], 8)
+    base = H.state(od, om.leaves, "grf", seed=0).cuda()
+    tgt0 = H.state(od, om.leaves, "grf", seed=1).cuda()
+    dts = []
+    U = base.clone().contiguous()
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for s in range(steps):
+        gm.reduce(U, 0.4, dt_next=dt)
+        dts.append(float(dt))
+        gm.hydro_step(U, dt, s)
+    from paper_1810_01319_gb300.autograd import rollout
+    Ut = rollout(gm, tgt0.contiguous(), dts, 0, 10)
+    target = Ut[:, 0, 4:4 + n, 4:4 + n, 4:4 + n].clone()
+    rho0 = base[:, 0].clone().requires_grad_(True)
+    L = _loss(gm, rho0, base, dts, target)
+    (grad,) = torch.autograd.grad(L, rho0)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    worst = 0.0
+    for k in range(ndir):
+        d = torch.randn(rho0.shape, generator=gen, device="cuda", dtype=torch.float64)
+        d[:, :4] = 0; d[:, -4:] = 0; d[:, :, :4] = 0; d[:, :, -4:] = 0; d[:, :, :, :4] = 0; d[:, :, :, -4:] = 0
+        d /= d.norm()
+        eps = 1e-6 * float(rho0.detach().norm()) / np.sqrt(rho0.numel())
+        with torch.no_grad():
+            lp = float(_loss(gm, rho0.detach() + eps * d, base, dts, target))
+            lm = float(_loss(gm, rho0.detach() - eps * d, base, dts, target))
+        fd = (lp - lm) / (2 * eps)
+        an = float((grad * d).sum())
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-30))
+    assert worst < 1e-4, worst
+
+
+def test_float32_adjoint_close_to_float64():
+    od, om = _periodic(n=16)
+    U0 = _moving_state(od, om, 9)
+    _, dts = OH.run(U0, om, 2, 0.4)
+    out = {}
+    for prec in (8, 4):
+        gm = H.gpu_mesh_from_flags(od, [], prec)
+        U = U0.to(gm.dtype).cuda().contiguous()
+        states = []
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for s, v in enumerate(dts):
+            states.append(U.clone())
+            dt.fill_(v)
+            gm.hydro_step(U, dt, s)
+        lam = torch.ones_like(U)
+        for s in (1, 0):
+            dt.fill_(dts[s])
+            gm.hydro_adjoint_step(states[s], lam, dt, s)
+        out[prec] = lam.double().cpu()
+    err = float((out[4] - out[8]).abs().max() / out[8].abs().max())
+    assert err < 1e-3, err
