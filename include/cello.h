@@ -156,6 +156,22 @@ cello_status cello_set_exec(cello_mesh* mesh, int mode);
 cello_status cello_profile_step(cello_mesh* mesh, void* U, const double* dt_dev, int cycle, double cfl,
                                 float* phase_ms_host, void* stream);
 
+/* The same reduction as cello_reduce (same kernels, same results) for
+ * callers that cannot let a library allocate device memory where it is
+ * used: allocation-free stream captures, hosts that hand out a fixed device
+ * budget up front, runtimes whose own allocator owns the device.  The paper
+ * has no counterpart; this is an interface convenience.  Its scratch (six
+ * doubles per leaf) is a fixed 1.5 MiB __device__ array of the library, held
+ * by every GPU that loads the library until the process exits, so meshes
+ * of more than 32768 leaves are rejected with CELLO_EINVAL.  The call
+ * allocates nothing.  Its first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the one array and
+ * every call writes the entries it reads before reading them, so nothing
+ * has to start at zero; calls that overlap on the GPU race on it. */
+cello_status cello_reduce_noalloc(cello_mesh* mesh, const void* U, double cfl, double* dt_next_dev,
+                                  double* totals_dev, void* stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* cello_last_error(void);
 

@@ -125,6 +125,13 @@ class Mesh:
         _lib.check(_lib.lib().cello_reduce(self.handle, _ptr(U), float(cfl), _ptr(dt_next), _ptr(totals),
                                            _stream(stream)), "cello_reduce")
 
+    def reduce_noalloc(self, U, cfl=0.4, dt_next=None, totals=None, stream=None):
+        """reduce() through the entry point that allocates nothing (its scratch
+        is a fixed array of the library, at most 32768 leaves)."""
+        self._check_state(U)
+        _lib.check(_lib.lib().cello_reduce_noalloc(self.handle, _ptr(U), float(cfl), _ptr(dt_next), _ptr(totals),
+                                                   _stream(stream)), "cello_reduce_noalloc")
+
     def profile_step(self, U, dt, cycle, cfl=0.4, stream=None):
         """Device milliseconds of each phase of one batched step: refresh,
         sweep 1, 2, 3, flux correction, reduction.  Advances U by one step."""

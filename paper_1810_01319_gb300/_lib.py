@@ -41,6 +41,7 @@ SIGNATURES = {
     "cello_ghost_refresh": (ctypes.c_int, [_vp, _vp, _vp]),
     "cello_hydro_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    "cello_reduce_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_set_exec": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cello_hydro_adjoint_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "cello_profile_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp]),

@@ -28,6 +28,7 @@ UNITS = {
     "k_f64.cu": ["-fmad=false"],
     "table.cu": [],
     "mesh.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cello.h"
+
 namespace cello {
 
 constexpr int kGhosts = 4;
@@ -68,6 +70,11 @@ struct AdjSweepParams {
   const double* dt;
   int n_items;
 };
+
+// Accessors for translation units that see cello_mesh only as an opaque type.
+DevMesh mesh_dev(const cello_mesh* mesh);
+int mesh_precision(const cello_mesh* mesh);
+cello_status set_error(cello_status status, const char* message);
 
 // One-time kernel attribute set-up (dynamic shared memory limits), done
 // outside any stream capture.

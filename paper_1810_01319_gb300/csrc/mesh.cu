@@ -526,6 +526,12 @@ cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double
 
 }  // namespace
 
+namespace cello {
+DevMesh mesh_dev(const cello_mesh* mesh) { return mesh->dev(); }
+int mesh_precision(const cello_mesh* mesh) { return mesh->desc.precision; }
+cello_status set_error(cello_status status, const char* message) { return fail(status, message); }
+}  // namespace cello
+
 // ====================================================================== ABI
 extern "C" {
 
