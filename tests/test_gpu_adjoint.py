@@ -73,12 +73,15 @@ def _loss(gm, rho0, base, dts, target, every=5):
     return ((rho - target) ** 2).sum()
 
 
-@pytest.mark.parametrize("root,n,steps,ndir", [((2, 2, 2), 16, 20, 6)])
+@pytest.mark.parametrize("root,n,steps,ndir", [((2, 2, 2), 16, 20, 6), ((4, 4, 4), 32, 50, 16)])
 def test_gradient_against_finite_differences(root, n, steps, ndir):
     """Adjoint workload: rho0 = 1 + 0.1 GRF(k^-2, seed 0), p = 1, v = 0,
     gamma 5/3, periodic; loss = sum (rho_final - rho_target)^2 with the
     target from seed 1; gradient wrt rho0 checked on random directions by
-    central differences (float64, frozen dt)."""
+    central differences (float64, frozen dt).  The step is 1e-4 of the rms
+    density along a unit direction: smaller steps are dominated by the
+    rounding noise of 50 nonlinear steps (measured: relative FD error 4e-7 at
+    1e-4, 2e-5 at 1e-5, 3e-4 at 1e-6)."""
     od, om = _periodic(root=root, n=n)
     gm = H.gpu_mesh_from_flags(od, [], 8)
     base = H.state(od, om.leaves, "grf", seed=0).cuda()
@@ -102,7 +105,7 @@ def test_gradient_against_finite_differences(root, n, steps, ndir):
         d = torch.randn(rho0.shape, generator=gen, device="cuda", dtype=torch.float64)
         d[:, :4] = 0; d[:, -4:] = 0; d[:, :, :4] = 0; d[:, :, -4:] = 0; d[:, :, :, :4] = 0; d[:, :, :, -4:] = 0
         d /= d.norm()
-        eps = 1e-6 * float(rho0.detach().norm()) / np.sqrt(rho0.numel())
+        eps = 1e-4 * float(rho0.detach().norm()) / np.sqrt(rho0.numel())
         with torch.no_grad():
             lp = float(_loss(gm, rho0.detach() + eps * d, base, dts, target))
             lm = float(_loss(gm, rho0.detach() - eps * d, base, dts, target))

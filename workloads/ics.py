@@ -160,7 +160,7 @@ def grf_density(N, seed, amp=0.1, slope=-2.0):
     shape = np.zeros_like(k)
     nz = k > 0
     shape[nz] = k[nz] ** (slope / 2.0)
-    delta = np.fft.irfftn(F * shape, s=(N, N, N))
+    delta = np.fft.irfftn(F * shape, s=(N, N, N), axes=(0, 1, 2))
     delta = (delta - delta.mean()) / delta.std()
     return 1.0 + amp * delta
 
