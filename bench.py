@@ -222,6 +222,8 @@ def main():
     mesh, U = build_workload(cfg, 4, log=log)
     log(f"[bench] workload ready in {time.time() - t_setup:.1f}s: {mesh.n_leaves} leaves, "
         f"{mesh.n_coarse_fine} coarse-fine faces")
+    variant, variant_ms = mesh.autotune(U)
+    log(f"[bench] autotuned sweep variant {variant}: {['%.2f' % t for t in variant_ms]} ms")
     mesh.set_exec(EXEC_GRAPH)
     cells = mesh.n_leaves * cfg["n"] ** 3
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -319,6 +321,7 @@ def main():
         rates = {}
         for prec, mode, steps in ((8, EXEC_PLAIN, 2), (4, EXEC_GRAPH, 5)):
             m2, U2 = build_workload(sub, prec, log=lambda *a: None)
+            m2.autotune(U2)
             m2.set_exec(mode)
             d2 = torch.zeros(1, dtype=torch.float64, device="cuda")
             m2.reduce(U2, cfg["cfl"], dt_next=d2)
@@ -347,7 +350,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(cfg, leaves=mesh.n_leaves, cells=cells, coarse_fine_faces=mesh.n_coarse_fine),
+                "config": dict(cfg, leaves=mesh.n_leaves, cells=cells, coarse_fine_faces=mesh.n_coarse_fine,
+                               sweep_variant=variant, sweep_variant_ms=variant_ms),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
                 "hbm_frac_algorithmic": value * 40 / (hbm * 1e9)}

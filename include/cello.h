@@ -148,6 +148,22 @@ cello_status cello_reduce(cello_mesh* mesh, const void* U, double cfl, double* d
 enum { CELLO_EXEC_PLAIN = 0, CELLO_EXEC_BATCHED = 1, CELLO_EXEC_GRAPH = 2 };
 cello_status cello_set_exec(cello_mesh* mesh, int mode);
 
+/* Launch variant of the PPM sweep kernel used by cello_hydro_step and the
+ * adjoint: pencils per CTA, register bound (minimum resident CTAs per SM)
+ * and schedule (one CTA per work item, or one resident wave pulling items
+ * from a device counter).  Float32 has 8 variants, float64 2; every variant
+ * computes the same values.  Cached graphs are dropped. */
+cello_status cello_set_sweep_variant(cello_mesh* mesh, int variant);
+
+/* Autotuner (Sec. IV: agglomerated work units on accelerators): times the
+ * three sweeps of a step for every sweep variant on up to 4096 leaves of U
+ * with dt = 0 (U is left bit-for-bit unchanged), keeps the fastest for this
+ * mesh and returns it in *variant_out (nullable); ms_out (host, nullable,
+ * ms_len entries) receives the best time of each variant.  Blocks until
+ * done; call it outside any stream capture. */
+cello_status cello_autotune(cello_mesh* mesh, void* U, int* variant_out, float* ms_out, int ms_len,
+                            void* stream);
+
 /* One batched step (as cello_hydro_step, without dt_next/totals) with CUDA
  * events recorded between its phases; blocks until it completes and writes
  * the device time of each phase in milliseconds to phase_ms_host[6]:

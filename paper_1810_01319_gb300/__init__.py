@@ -142,5 +142,19 @@ class Mesh:
                    "cello_profile_step")
         return list(out)
 
+    def set_sweep_variant(self, variant: int):
+        _lib.check(_lib.lib().cello_set_sweep_variant(self.handle, int(variant)), "cello_set_sweep_variant")
+
+    def autotune(self, U, stream=None):
+        """Pick the fastest sweep variant for this mesh (U is not changed).
+        Returns (chosen variant, best milliseconds of each variant)."""
+        self._check_state(U)
+        v = ctypes.c_int()
+        ms = (ctypes.c_float * 16)()
+        _lib.check(_lib.lib().cello_autotune(self.handle, _ptr(U), ctypes.byref(v), ctypes.cast(ms, ctypes.c_void_p),
+                                             16, _stream(stream)), "cello_autotune")
+        nv = 8 if self.desc.precision == 4 else 2
+        return v.value, list(ms)[:nv]
+
     def set_exec(self, mode: int):
         _lib.check(_lib.lib().cello_set_exec(self.handle, int(mode)), "cello_set_exec")

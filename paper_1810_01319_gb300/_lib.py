@@ -43,6 +43,8 @@ SIGNATURES = {
     "cello_reduce": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_set_exec": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "cello_set_sweep_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "cello_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "cello_hydro_adjoint_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "cello_profile_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp]),
     "cello_last_error": (ctypes.c_char_p, []),

@@ -11,8 +11,21 @@ namespace cello {
 
 constexpr int kGhosts = 4;
 constexpr int kFields = 5;
-constexpr int kPencilsPerTile = 8;   // pencils per sweep CTA
 constexpr int kAdjPencils = 4;       // pencils per adjoint-sweep CTA
+
+// Launch variants of the PPM sweep: pencils per CTA, the minimum number of
+// resident CTAs per SM the register allocation is bounded for, and the
+// schedule (static: one CTA per item; persistent: one resident wave of CTAs
+// pulling items from a device counter).  The autotuner times them.
+struct SweepVariant {
+  int pencils;
+  int min_blocks;
+  bool persistent;
+};
+int sweep_variant_count_f32();
+int sweep_variant_count_f64();
+SweepVariant sweep_variant_f32(int v);
+SweepVariant sweep_variant_f64(int v);
 
 // Neighbour kinds of the 27-entry table.
 enum NbKind : int8_t { kSame = 0, kCoarse = 1, kFine = 2, kBoundary = 3 };
@@ -53,11 +66,12 @@ struct SweepParams {
   int leaf0, nleaf;        // leaves [leaf0, leaf0 + nleaf)
   int axis;
   int a0, a1, b0, b1;      // transverse ranges (padded coordinates)
-  int tiles_per_leaf;
+  int tiles_per_leaf;      // set by the launcher from the variant's pencils per CTA
   const double* dt;        // device scalar
   double* reg;             // flux registers (may be null)
-  unsigned* work;          // persistent work counter (null: static schedule)
-  int n_items;
+  unsigned* work;          // work counter for persistent variants (device, 4 bytes)
+  int n_items;             // set by the launcher
+  int variant;             // index into the sweep variants of the precision
 };
 
 struct AdjSweepParams {

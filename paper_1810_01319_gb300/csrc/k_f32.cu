@@ -4,20 +4,77 @@
 
 namespace cello {
 
-template <int NB, int P>
-static void sweep_f32_n(const DevMesh& m, const SweepParams& p, cudaStream_t s) {
+// Float32 sweep variants: {pencils per CTA, min resident CTAs per SM, persistent}.
+static const SweepVariant kVariants[] = {
+    {8, 3, false}, {8, 4, false}, {4, 6, false}, {16, 1, false},
+    {8, 3, true},  {8, 4, true},  {4, 6, true},  {16, 1, true},
+};
+constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
+static int g_resident[4][kNV];   // resident CTAs per GPU by [n index][variant], from the occupancy API
+
+static int nb_index(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
+
+template <int NB, int P, int MINB>
+static size_t sweep_smem() {
   constexpr int N = NB + 2 * kGhosts;
-  const size_t smem = sizeof(float) * 21 * N * P;
-  auto k = sweep_kernel<float, NB, P>;
-  const int grid = p.n_items;
-  k<<<grid, N * P, smem, s>>>(m, p);
+  return sizeof(float) * 21 * N * P;
 }
 
-template <int NB, int P>
-static void prepare_n() {
+template <int NB, int P, int MINB>
+static void prepare_variant(int v, int sms) {
   constexpr int N = NB + 2 * kGhosts;
-  cudaFuncSetAttribute(sweep_kernel<float, NB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(float) * 21 * N * P));
+  auto k = sweep_kernel<float, NB, P, MINB>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<NB, P, MINB>());
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, N * P, sweep_smem<NB, P, MINB>());
+  g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
+}
+
+template <int NB, int P, int MINB>
+static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  p.tiles_per_leaf = (pencils + P - 1) / P;
+  p.n_items = p.nleaf * p.tiles_per_leaf;
+  if (p.n_items <= 0) return;
+  int grid = p.n_items;
+  if (kVariants[v].persistent && p.work) {
+    cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
+    grid = g_resident[nb_index(NB)][v] < grid ? g_resident[nb_index(NB)][v] : grid;
+  } else {
+    p.work = nullptr;
+  }
+  sweep_kernel<float, NB, P, MINB><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
+}
+
+template <int NB>
+static void prepare_nb(int sms) {
+  prepare_variant<NB, 8, 3>(0, sms);
+  prepare_variant<NB, 8, 4>(1, sms);
+  prepare_variant<NB, 4, 6>(2, sms);
+  prepare_variant<NB, 16, 1>(3, sms);
+  for (int v = 4; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - 4];
+}
+
+template <int NB>
+static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
+  const int v = (p.variant >= 0 && p.variant < kNV) ? p.variant : 0;
+  switch (v % 4) {
+    case 0: launch_variant<NB, 8, 3>(m, p, pencils, v, s); break;
+    case 1: launch_variant<NB, 8, 4>(m, p, pencils, v, s); break;
+    case 2: launch_variant<NB, 4, 6>(m, p, pencils, v, s); break;
+    case 3: launch_variant<NB, 16, 1>(m, p, pencils, v, s); break;
+  }
+}
+
+int sweep_variant_count_f32() { return kNV; }
+SweepVariant sweep_variant_f32(int v) { return kVariants[v]; }
+
+void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
+  switch (m.n) {
+    case 8: launch_nb<8>(m, p, pencils, s); break;
+    case 16: launch_nb<16>(m, p, pencils, s); break;
+    case 32: launch_nb<32>(m, p, pencils, s); break;
+  }
 }
 
 template <int NB, int P>
@@ -48,22 +105,16 @@ void launch_adjoint_sweep_f32(const DevMesh& m, const AdjSweepParams& p, cudaStr
 }
 
 void prepare_kernels_f32() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  prepare_nb<8>(sms);
+  prepare_nb<16>(sms);
+  prepare_nb<32>(sms);
   prepare_adj<8>();
   prepare_adj<16>();
   prepare_adj<32>();
-  prepare_n<8, kPencilsPerTile>();
-  prepare_n<16, kPencilsPerTile>();
-  prepare_n<32, kPencilsPerTile>();
 }
 
-void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
-  (void)pencils;
-  if (p.n_items <= 0) return;
-  switch (m.n) {
-    case 8: sweep_f32_n<8, kPencilsPerTile>(m, p, s); break;
-    case 16: sweep_f32_n<16, kPencilsPerTile>(m, p, s); break;
-    case 32: sweep_f32_n<32, kPencilsPerTile>(m, p, s); break;
-  }
-}
 
 }  // namespace cello

@@ -7,19 +7,55 @@
 
 namespace cello {
 
-template <int NB, int P>
-static void sweep_f64_n(const DevMesh& m, const SweepParams& p, cudaStream_t s) {
+// Float64 sweep variants: {pencils per CTA, min resident CTAs per SM, persistent}.
+static const SweepVariant kVariants64[] = {{8, 2, false}, {8, 2, true}};
+constexpr int kNV64 = 2;
+static int g_resident64[3];
+
+static int nb_index64(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
+
+template <int NB>
+static size_t sweep_smem64() {
   constexpr int N = NB + 2 * kGhosts;
-  const size_t smem = sizeof(double) * 21 * N * P;
-  auto k = sweep_kernel<double, NB, P>;
-  k<<<p.n_items, N * P, smem, s>>>(m, p);
+  return sizeof(double) * 21 * N * 8;
 }
 
-template <int NB, int P>
-static void prepare_n() {
+template <int NB>
+static void prepare_nb64(int sms) {
   constexpr int N = NB + 2 * kGhosts;
-  cudaFuncSetAttribute(sweep_kernel<double, NB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(double) * 21 * N * P));
+  auto k = sweep_kernel<double, NB, 8, 2>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem64<NB>());
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, N * 8, sweep_smem64<NB>());
+  g_resident64[nb_index64(NB)] = (nb > 0 ? nb : 1) * sms;
+}
+
+template <int NB>
+static void launch_nb64(const DevMesh& m, SweepParams p, int pencils, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  const int v = (p.variant >= 0 && p.variant < kNV64) ? p.variant : 0;
+  p.tiles_per_leaf = (pencils + 7) / 8;
+  p.n_items = p.nleaf * p.tiles_per_leaf;
+  if (p.n_items <= 0) return;
+  int grid = p.n_items;
+  if (kVariants64[v].persistent && p.work) {
+    cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
+    grid = g_resident64[nb_index64(NB)] < grid ? g_resident64[nb_index64(NB)] : grid;
+  } else {
+    p.work = nullptr;
+  }
+  sweep_kernel<double, NB, 8, 2><<<grid, N * 8, sweep_smem64<NB>(), s>>>(m, p);
+}
+
+int sweep_variant_count_f64() { return kNV64; }
+SweepVariant sweep_variant_f64(int v) { return kVariants64[v]; }
+
+void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
+  switch (m.n) {
+    case 8: launch_nb64<8>(m, p, pencils, s); break;
+    case 16: launch_nb64<16>(m, p, pencils, s); break;
+    case 32: launch_nb64<32>(m, p, pencils, s); break;
+  }
 }
 
 template <int NB, int P>
@@ -50,22 +86,15 @@ void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStr
 }
 
 void prepare_kernels_f64() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  prepare_nb64<8>(sms);
+  prepare_nb64<16>(sms);
+  prepare_nb64<32>(sms);
   prepare_adj<8>();
   prepare_adj<16>();
   prepare_adj<32>();
-  prepare_n<8, kPencilsPerTile>();
-  prepare_n<16, kPencilsPerTile>();
-  prepare_n<32, kPencilsPerTile>();
-}
-
-void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
-  (void)pencils;
-  if (p.n_items <= 0) return;
-  switch (m.n) {
-    case 8: sweep_f64_n<8, kPencilsPerTile>(m, p, s); break;
-    case 16: sweep_f64_n<16, kPencilsPerTile>(m, p, s); break;
-    case 32: sweep_f64_n<32, kPencilsPerTile>(m, p, s); break;
-  }
 }
 
 template <typename T, int NB>

@@ -26,8 +26,8 @@ __device__ __forceinline__ T minmod(T a, T b) {
 //   values  4 flatten + monotone + trace  5 Riemann flux (+ face registers)
 //   6 conservative update of cells g..g+n-1.
 // =====================================================================
-template <typename T, int NB, int P>
-__global__ void __launch_bounds__((NB + 8) * P)
+template <typename T, int NB, int P, int MINB>
+__global__ void __launch_bounds__((NB + 8) * P, MINB)
 sweep_kernel(DevMesh m, SweepParams prm) {
   constexpr int G = kGhosts, N = NB + 2 * G, S = P, A = N * S;
   constexpr long SLAB = (long)N * N * N;
@@ -53,8 +53,15 @@ sweep_kernel(DevMesh m, SweepParams prm) {
   const int t = threadIdx.x;
   const int lc = t / P, lp = t % P;           // this thread's cell and pencil
   const int cp = lp, cj = lc;
+  __shared__ int s_item;
 
-  for (int item = blockIdx.x; item < prm.n_items; item += gridDim.x) {
+  int item = blockIdx.x;
+  if (prm.work) {
+    if (t == 0) s_item = (int)atomicAdd(prm.work, 1u);
+    __syncthreads();
+    item = s_item;
+  }
+  while (item < prm.n_items) {
     const int leaf = prm.leaf0 + item / prm.tiles_per_leaf;
     const int tile = item % prm.tiles_per_leaf;
     const int4 lf = m.leaf[leaf];
@@ -162,6 +169,13 @@ sweep_kernel(DevMesh m, SweepParams prm) {
       }
     }
     __syncthreads();
+    if (prm.work) {
+      if (t == 0) s_item = (int)atomicAdd(prm.work, 1u);
+      __syncthreads();
+      item = s_item;
+    } else {
+      item += gridDim.x;
+    }
   }
 }
 

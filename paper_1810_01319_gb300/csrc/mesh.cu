@@ -149,6 +149,9 @@ struct cello_mesh {
   double* d_reg = nullptr;
   double* d_partials = nullptr;
   int exec_mode = CELLO_EXEC_BATCHED;
+  int sweep_variant = 0;           // chosen by cello_autotune or cello_set_sweep_variant
+  unsigned* d_work = nullptr;      // work counter of the persistent sweep variants
+  double* d_zero = nullptr;        // dt = 0, for timing sweeps without changing the state
   void* adj_scratch = nullptr;   // three states for the adjoint's forward recomputation
   size_t adj_bytes = 0;
   std::vector<GraphEntry> graphs;
@@ -182,6 +185,10 @@ struct cello_mesh {
     capture_stream = nullptr;
     if (adj_scratch) cudaFree(adj_scratch);
     adj_scratch = nullptr;
+    if (d_work) cudaFree(d_work);
+    if (d_zero) cudaFree(d_zero);
+    d_work = nullptr;
+    d_zero = nullptr;
     void* ptrs[] = {d_leaf, d_keys, d_kind, d_idx, d_fine8, d_face_slot, d_cfaces, d_group_start, d_reg, d_partials};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -381,6 +388,9 @@ cello_status finish_build(cello_mesh* M) {
   CELLO_TRY(upload(&M->d_group_start, M->group_start));
   if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * 5 * d.n * d.n * sizeof(double)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_partials, (size_t)std::max(B, 1) * 6 * sizeof(double)));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_work, sizeof(unsigned)));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_zero, sizeof(double)));
+  CELLO_CUDA(cudaMemset(M->d_zero, 0, sizeof(double)));
   CELLO_CUDA(cudaDeviceSynchronize());
   return CELLO_OK;
 }
@@ -424,22 +434,20 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
     p.axis = axis;
     sweep_ranges(M, axis, swept, p.a0, p.a1, p.b0, p.b1);
     const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
-    p.tiles_per_leaf = (pencils + kPencilsPerTile - 1) / kPencilsPerTile;
     p.dt = dt;
     p.reg = M->d_reg;
-    p.work = nullptr;
+    p.work = M->d_work;
+    p.variant = M->sweep_variant;
     if (plain) {
       for (int b = 0; b < B; ++b) {
         p.leaf0 = b;
         p.nleaf = 1;
-        p.n_items = p.tiles_per_leaf;
         if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
         else launch_sweep_f64(dm, p, pencils, s);
       }
     } else {
       p.leaf0 = 0;
       p.nleaf = B;
-      p.n_items = B * p.tiles_per_leaf;
       if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
       else launch_sweep_f64(dm, p, pencils, s);
     }
@@ -491,12 +499,12 @@ cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double
       p.axis = axis;
       p.a0 = rng[oi][0]; p.a1 = rng[oi][1]; p.b0 = rng[oi][2]; p.b1 = rng[oi][3];
       const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
-      p.tiles_per_leaf = (pencils + kPencilsPerTile - 1) / kPencilsPerTile;
       p.dt = dt;
       p.reg = nullptr;
+      p.work = M->d_work;
+      p.variant = M->sweep_variant;
       p.leaf0 = 0;
       p.nleaf = B;
-      p.n_items = B * p.tiles_per_leaf;
       if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
       else launch_sweep_f64(dm, p, pencils, s);
     }
@@ -666,6 +674,68 @@ cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, 
   if (!M || !Un || !lam || !dt) return fail(CELLO_EINVAL, "NULL argument");
   if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
   return adjoint_step(M, Un, lam, dt, cycle, (cudaStream_t)stream);
+}
+
+cello_status cello_set_sweep_variant(cello_mesh* M, int variant) {
+  if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
+  const int nv = M->desc.precision == 4 ? sweep_variant_count_f32() : sweep_variant_count_f64();
+  if (variant < 0 || variant >= nv) return fail(CELLO_EINVAL, "sweep variant out of range");
+  M->sweep_variant = variant;
+  for (auto& g : M->graphs) cudaGraphExecDestroy(g.exec);
+  M->graphs.clear();
+  return CELLO_OK;
+}
+
+cello_status cello_autotune(cello_mesh* M, void* U, int* variant_out, float* ms_out, int ms_len, void* stream) {
+  if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const cello_mesh_desc& d = M->desc;
+  const DevMesh dm = M->dev();
+  const int nv = d.precision == 4 ? sweep_variant_count_f32() : sweep_variant_count_f64();
+  const int nleaf = std::min(M->B, 4096);   // per-leaf cost is uniform: a sample of leaves suffices
+  cudaEvent_t e0, e1;
+  CELLO_CUDA(cudaEventCreate(&e0));
+  CELLO_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int v = 0; v < nv; ++v) {
+    float vbest = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, s);
+      bool swept[3] = {false, false, false};
+      for (int axis = 0; axis < 3; ++axis) {   // the three sweeps of an even cycle, dt = 0 (state unchanged)
+        SweepParams p{};
+        p.U = U;
+        p.axis = axis;
+        sweep_ranges(M, axis, swept, p.a0, p.a1, p.b0, p.b1);
+        const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
+        p.dt = M->d_zero;
+        p.reg = nullptr;
+        p.work = M->d_work;
+        p.variant = v;
+        p.leaf0 = 0;
+        p.nleaf = nleaf;
+        if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
+        else launch_sweep_f64(dm, p, pencils, s);
+        swept[axis] = true;
+      }
+      cudaEventRecord(e1, s);
+      CELLO_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < vbest) vbest = ms;   // the first repetition warms up
+    }
+    if (ms_out && v < ms_len) ms_out[v] = vbest;
+    if (vbest < best_ms) {
+      best_ms = vbest;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CELLO_CUDA(cudaGetLastError());
+  if (variant_out) *variant_out = best;
+  return cello_set_sweep_variant(M, best);
 }
 
 cello_status cello_profile_step(cello_mesh* M, void* U, const double* dt, int cycle, double cfl, float* phase_ms,

@@ -129,3 +129,25 @@ def test_exec_modes_bit_identical(blob_amr, precision):
         outs.append((U.cpu(), tot))
     for U, tot in outs[1:]:
         assert torch.equal(U, outs[0][0]) and torch.equal(tot, outs[0][1])
+
+
+@pytest.mark.parametrize("precision", [4, 8])
+def test_sweep_variants_identical_and_autotune(blob_amr, precision):
+    """Every launch variant of the sweep (tile shape, register bound,
+    persistent schedule) computes the same values; the autotuner leaves the
+    state unchanged and picks one of them."""
+    od, om, flags, U0, Uo, dts = blob_amr
+    gm = H.gpu_mesh_from_flags(od, flags, precision)
+    nv = 8 if precision == 4 else 2
+    outs = []
+    for v in range(nv):
+        gm.set_sweep_variant(v)
+        U, _, tot = _run_gpu(gm, U0, 3, dts=dts)
+        outs.append(U.cpu())
+    for v in range(1, nv):
+        assert torch.equal(outs[v], outs[0]), v
+    U = U0.to(gm.dtype).cuda().contiguous()
+    before = U.clone()
+    best, ms = gm.autotune(U)
+    assert torch.equal(U, before)
+    assert 0 <= best < nv and len(ms) == nv and min(ms) > 0
