@@ -151,7 +151,7 @@ cello_status cello_set_exec(cello_mesh* mesh, int mode);
 /* Launch variant of the PPM sweep kernel used by cello_hydro_step and the
  * adjoint: pencils per CTA, register bound (minimum resident CTAs per SM)
  * and schedule (one CTA per work item, or one resident wave pulling items
- * from a device counter).  Float32 has 8 variants, float64 2; every variant
+ * from a device counter).  Float32 has 10 variants, float64 2; every variant
  * computes the same values.  Cached graphs are dropped. */
 cello_status cello_set_sweep_variant(cello_mesh* mesh, int variant);
 

@@ -153,8 +153,7 @@ class Mesh:
         ms = (ctypes.c_float * 16)()
         _lib.check(_lib.lib().cello_autotune(self.handle, _ptr(U), ctypes.byref(v), ctypes.cast(ms, ctypes.c_void_p),
                                              16, _stream(stream)), "cello_autotune")
-        nv = 8 if self.desc.precision == 4 else 2
-        return v.value, list(ms)[:nv]
+        return v.value, [t for t in ms if t > 0]
 
     def set_exec(self, mode: int):
         _lib.check(_lib.lib().cello_set_exec(self.handle, int(mode)), "cello_set_exec")

@@ -99,8 +99,14 @@ void prepare_kernels_f64();
 // Launchers (defined in the kernel translation units).
 void launch_neighbour_table(const DevMesh& m, const unsigned long long* keys, int8_t* kind, int* idx,
                             int* fine8, cudaStream_t s);
-void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, cudaStream_t s);
-void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, cudaStream_t s);
+// Ghost refresh of leaves [leaf0, leaf0+nleaf): vector copies of same-level
+// runs, then the listed slow runs (leaf * runs_per_leaf + run) cell by cell.
+void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const long long* slow, int nslow,
+                        cudaStream_t s);
+void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const long long* slow, int nslow,
+                        cudaStream_t s);
+int ghost_run_count(int n);
+void launch_classify_runs(const DevMesh& m, int leaf0, int nleaf, unsigned char* out, cudaStream_t s);
 void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces,
@@ -112,6 +118,7 @@ void launch_adjoint_sweep_f32(const DevMesh& m, const AdjSweepParams& p, cudaStr
 void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStream_t s);
 void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s);
+void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);
 

@@ -6,11 +6,12 @@ namespace cello {
 
 // Float32 sweep variants: {pencils per CTA, min resident CTAs per SM, persistent}.
 static const SweepVariant kVariants[] = {
-    {8, 3, false}, {8, 4, false}, {4, 6, false}, {16, 1, false},
-    {8, 3, true},  {8, 4, true},  {4, 6, true},  {16, 1, true},
+    {8, 3, false}, {8, 4, false}, {4, 6, false}, {16, 1, false}, {4, 8, false},
+    {8, 3, true},  {8, 4, true},  {4, 6, true},  {16, 1, true},  {4, 8, true},
 };
+constexpr int kNT = 5;   // distinct kernel instantiations; variant v uses template v % kNT
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
-static int g_resident[4][kNV];   // resident CTAs per GPU by [n index][variant], from the occupancy API
+static int g_resident[3][kNV];   // resident CTAs per GPU by [n index][variant], from the occupancy API
 
 static int nb_index(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
 
@@ -52,17 +53,27 @@ static void prepare_nb(int sms) {
   prepare_variant<NB, 8, 4>(1, sms);
   prepare_variant<NB, 4, 6>(2, sms);
   prepare_variant<NB, 16, 1>(3, sms);
-  for (int v = 4; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - 4];
+  prepare_variant<NB, 4, 8>(4, sms);
+  for (int v = kNT; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - kNT];
 }
 
 template <int NB>
 static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s) {
   const int v = (p.variant >= 0 && p.variant < kNV) ? p.variant : 0;
-  switch (v % 4) {
+  switch (v % kNT) {
     case 0: launch_variant<NB, 8, 3>(m, p, pencils, v, s); break;
     case 1: launch_variant<NB, 8, 4>(m, p, pencils, v, s); break;
     case 2: launch_variant<NB, 4, 6>(m, p, pencils, v, s); break;
     case 3: launch_variant<NB, 16, 1>(m, p, pencils, v, s); break;
+    case 4: launch_variant<NB, 4, 8>(m, p, pencils, v, s); break;
+  }
+}
+
+void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s) {
+  switch (m.n) {
+    case 8: reduce_partials_f32_kernel<8><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+    case 16: reduce_partials_f32_kernel<16><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+    case 32: reduce_partials_f32_kernel<32><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
   }
 }
 

@@ -98,28 +98,43 @@ void prepare_kernels_f64() {
 }
 
 template <typename T, int NB>
-static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, cudaStream_t s) {
-  constexpr int N = NB + 2 * kGhosts;
-  constexpr long NG = (long)N * N * N - (long)NB * NB * NB;
-  const long threads = NG * nleaf;
-  if (threads <= 0) return;
-  refresh_kernel<T, NB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, U, leaf0, nleaf);
+static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, const long long* slow, int nslow,
+                      cudaStream_t s) {
+  const long threads = (long)ghost_runs<NB>() * nleaf;
+  if (threads > 0) refresh_kernel<T, NB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, U, leaf0, nleaf);
+  if (nslow > 0) refresh_slow_kernel<T, NB><<<(nslow * 4 + 127) / 128, 128, 0, s>>>(m, U, slow, nslow);
 }
 
 template <typename T>
-static void refresh_t(const DevMesh& m, T* U, int leaf0, int nleaf, cudaStream_t s) {
+static void refresh_t(const DevMesh& m, T* U, int leaf0, int nleaf, const long long* slow, int nslow,
+                      cudaStream_t s) {
   switch (m.n) {
-    case 8: refresh_n<T, 8>(m, U, leaf0, nleaf, s); break;
-    case 16: refresh_n<T, 16>(m, U, leaf0, nleaf, s); break;
-    case 32: refresh_n<T, 32>(m, U, leaf0, nleaf, s); break;
+    case 8: refresh_n<T, 8>(m, U, leaf0, nleaf, slow, nslow, s); break;
+    case 16: refresh_n<T, 16>(m, U, leaf0, nleaf, slow, nslow, s); break;
+    case 32: refresh_n<T, 32>(m, U, leaf0, nleaf, slow, nslow, s); break;
   }
 }
 
-void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, cudaStream_t s) {
-  refresh_t<float>(m, U, leaf0, nleaf, s);
+void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const long long* slow, int nslow,
+                        cudaStream_t s) {
+  refresh_t<float>(m, U, leaf0, nleaf, slow, nslow, s);
 }
-void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, cudaStream_t s) {
-  refresh_t<double>(m, U, leaf0, nleaf, s);
+void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const long long* slow, int nslow,
+                        cudaStream_t s) {
+  refresh_t<double>(m, U, leaf0, nleaf, slow, nslow, s);
+}
+
+int ghost_run_count(int n) { return n == 8 ? ghost_runs<8>() : (n == 16 ? ghost_runs<16>() : ghost_runs<32>()); }
+
+void launch_classify_runs(const DevMesh& m, int leaf0, int nleaf, unsigned char* out, cudaStream_t s) {
+  const long threads = (long)ghost_run_count(m.n) * nleaf;
+  if (threads <= 0) return;
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+  switch (m.n) {
+    case 8: classify_runs_kernel<8><<<grid, 256, 0, s>>>(m, leaf0, nleaf, out); break;
+    case 16: classify_runs_kernel<16><<<grid, 256, 0, s>>>(m, leaf0, nleaf, out); break;
+    case 32: classify_runs_kernel<32><<<grid, 256, 0, s>>>(m, leaf0, nleaf, out); break;
+  }
 }
 
 template <typename T, int NB>
@@ -136,7 +151,11 @@ void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, d
     case 16: reduce_n<T, 16>(m, U, partials, s); break;         \
     case 32: reduce_n<T, 32>(m, U, partials, s); break;         \
   }
-  if (precision == 4) { CELLO_RED(float) } else { CELLO_RED(double) }
+  if (precision == 4) {
+    launch_reduce_partials_f32(m, static_cast<const float*>(U), partials, s);
+  } else {
+    CELLO_RED(double)
+  }
 #undef CELLO_RED
   reduce_finish_kernel<<<1, 1024, 0, s>>>(partials, m.B, cfl, dt_next, totals);
 }

@@ -271,16 +271,11 @@ __device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int r
   }
 }
 
+// Value of one ghost cell (padded coords c, already inside the block
+// array) of leaf `leaf`: same-level copy, restriction or prolongation.
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
-  constexpr int G = kGhosts, N = NB + 2 * G, NG = N * N * N - NB * NB * NB, H = NB / 2;
-  constexpr long SLAB = (long)N * N * N;
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long)nleaf * NG) return;
-  const int leaf = leaf0 + (int)(gid / NG);
-  int c[3];
-  ghost_coord<NB>((int)(gid % NG), c[0], c[1], c[2]);
-  const long dst = (long)leaf * 5 * SLAB + ((long)c[2] * N + c[1]) * N + c[0];
+__device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T v[5]) {
+  constexpr int G = kGhosts, H = NB / 2;
   int d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -292,7 +287,6 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0
   }
   const int e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
   const int8_t k = m.kind[e];
-  T v[5];
   if (k == kSame) {
     load5<T, NB>(U, m.idx[e], c[0] - d[0] * NB, c[1] - d[1] * NB, c[2] - d[2] * NB, v);
   } else if (k == kFine) {
@@ -339,8 +333,108 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0
     for (int f = 0; f < 5; ++f)
       v[f] = Uc[f] + T(0.25) * ((sgn[0] * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
   }
+}
+
+// 16-byte vector of four consecutive cells.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  float4 a;
+  __device__ __forceinline__ void load(const float* p) { a = *reinterpret_cast<const float4*>(p); }
+  __device__ __forceinline__ void store(float* p) const { *reinterpret_cast<float4*>(p) = a; }
+};
+template <> struct Vec4<double> {
+  double2 a, b;
+  __device__ __forceinline__ void load(const double* p) {
+    a = reinterpret_cast<const double2*>(p)[0];
+    b = reinterpret_cast<const double2*>(p)[1];
+  }
+  __device__ __forceinline__ void store(double* p) const {
+    reinterpret_cast<double2*>(p)[0] = a;
+    reinterpret_cast<double2*>(p)[1] = b;
+  }
+};
+
+// Ghost runs: four consecutive ghost cells along x.  Every run starts at a
+// multiple of four cells, so source and destination are 16-byte aligned.
+template <int NB>
+__host__ __device__ constexpr int ghost_runs() {
+  return ((NB + 8) * (NB + 8) * (NB + 8) - NB * NB * NB) / 4;
+}
+
+// Direction of a run after the outflow clamp on y and z; false if the run
+// is not a plain same-level copy (coarser or finer neighbour, or clamped
+// along x).
+template <int NB>
+__device__ __forceinline__ bool run_is_copy(const DevMesh& m, int leaf, int x0, int y, int z, int c[3], int d[3],
+                                            int& e) {
+  constexpr int G = kGhosts;
+  d[0] = x0 < G ? -1 : (x0 >= G + NB ? 1 : 0);
+  d[1] = y < G ? -1 : (y >= G + NB ? 1 : 0);
+  d[2] = z < G ? -1 : (z >= G + NB ? 1 : 0);
+  c[0] = x0; c[1] = y; c[2] = z;
+  if (d[0] != 0 && m.kind[leaf * 27 + face_dir(0, d[0])] == kBoundary) return false;
+  for (int a = 1; a < 3; ++a)
+    if (d[a] != 0 && m.kind[leaf * 27 + face_dir(a, d[a])] == kBoundary) {
+      c[a] = d[a] < 0 ? G : G + NB - 1;
+      d[a] = 0;
+    }
+  e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
+  return m.kind[e] == kSame;
+}
+
+// Same-level copies: one thread per run, one 16-byte vector per field.  Runs
+// that are not plain copies are left to refresh_slow_kernel.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
+  constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
+  constexpr long SLAB = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)nleaf * NS) return;
+  const int leaf = leaf0 + (int)(gid / NS);
+  int x0, y, z, c[3], d[3], e;
+  ghost_coord<NB>((int)(gid % NS) * 4, x0, y, z);
+  if (!run_is_copy<NB>(m, leaf, x0, y, z, c, d, e)) return;
+  const long dst = (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x0;
+  const long src = (long)m.idx[e] * 5 * SLAB + ((long)(c[2] - d[2] * NB) * N + (c[1] - d[1] * NB)) * N +
+                   (c[0] - d[0] * NB);
+  Vec4<T> v[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) v[f].load(U + src + f * SLAB);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) v[f].store(U + dst + f * SLAB);
+}
+
+// The remaining runs (listed per mesh as leaf * runs + run), cell by cell:
+// restriction, prolongation, or clamped copies at outflow boundaries.
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, const long long* runs, int nruns) {
+  constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
+  constexpr long SLAB = (long)N * N * N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nruns * 4) return;
+  const long long r = runs[i >> 2];
+  const int leaf = (int)(r / NS);
+  int x0, y, z;
+  ghost_coord<NB>((int)(r % NS) * 4, x0, y, z);
+  int cc[3] = {x0 + (i & 3), y, z};
+  const long dst = (long)leaf * 5 * SLAB + ((long)z * N + y) * N + cc[0];
+  T v[5];
+  ghost_value<T, NB>(m, U, leaf, cc, v);
 #pragma unroll
   for (int f = 0; f < 5; ++f) U[dst + f * SLAB] = v[f];
+}
+
+// Classification of every run of some leaves, for the host's slow-run list:
+// out[(leaf - leaf0) * runs + run] = 1 if the run is not a plain copy.
+template <int NB>
+__global__ void __launch_bounds__(256) classify_runs_kernel(DevMesh m, int leaf0, int nleaf, unsigned char* out) {
+  constexpr int NS = ghost_runs<NB>();
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)nleaf * NS) return;
+  const int leaf = leaf0 + (int)(gid / NS);
+  int x0, y, z, c[3], d[3], e;
+  ghost_coord<NB>((int)(gid % NS) * 4, x0, y, z);
+  out[gid] = run_is_copy<NB>(m, leaf, x0, y, z, c, d, e) ? 0 : 1;
 }
 
 // =====================================================================
@@ -398,6 +492,60 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh
     v[0] = fmin(v[0], double(dx / s));
     v[1] += double(r0); v[2] += double(m1); v[3] += double(m2); v[4] += double(m3); v[5] += double(E);
   }
+  block_reduce6(v, sh);
+  if (threadIdx.x == 0) {
+    const double dxd = ldexp(m.dx0, -lf.x);
+    const double vol = dxd * dxd * dxd;
+    partials[leaf * 6 + 0] = v[0];
+    for (int k = 1; k < 6; ++k) partials[leaf * 6 + k] = v[k] * vol;
+  }
+}
+
+// Float32 state: per-thread sums carried as unevaluated float pairs (Knuth's
+// TwoSum keeps each addition's rounding error), the dt candidate minimum in
+// float32 (the same value as a float64 minimum of the converted candidates);
+// each thread converts once to float64 and the tree runs in float64.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(DevMesh m, const float* U,
+                                                                             double* partials) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
+  __shared__ double sh[6 * 32];
+  const int leaf = blockIdx.x;
+  const int4 lf = m.leaf[leaf];
+  const float dx = float(ldexp(m.dx0, -lf.x));
+  const float gamma = float(m.gamma), gm1 = float(m.gamma - 1.0);
+  const float* b = U + (long)leaf * 5 * SLAB;
+  float mn = INFINITY, hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
+    const int x = i % NB + G, y = (i / NB) % NB + G, z = i / (NB * NB) + G;
+    const long o = ((long)z * N + y) * N + x;
+    const float r0 = b[o], m1 = b[SLAB + o], m2 = b[2 * SLAB + o], m3 = b[3 * SLAB + o], E = b[4 * SLAB + o];
+    const float rho = vmax(r0, float(kRhoFloor));
+    const float u = m1 / rho, vv = m2 / rho, w = m3 / rho;
+    const float ke = (0.5f * rho) * (u * u + (vv * vv + w * w));
+    const float p = vmax(gm1 * (E - ke), float(kPFloor));
+    const float c = sqrtf((gamma * p) / rho);
+    const float s = vmax(fabsf(u), vmax(fabsf(vv), fabsf(w))) + c;
+    mn = fminf(mn, dx / s);
+    two_sum_acc(hi[0], lo[0], r0);
+    two_sum_acc(hi[1], lo[1], m1);
+    two_sum_acc(hi[2], lo[2], m2);
+    two_sum_acc(hi[3], lo[3], m3);
+    two_sum_acc(hi[4], lo[4], E);
+  }
+  double v[6];
+  v[0] = double(mn);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k + 1] = double(hi[k]) + double(lo[k]);
   block_reduce6(v, sh);
   if (threadIdx.x == 0) {
     const double dxd = ldexp(m.dx0, -lf.x);

@@ -148,6 +148,8 @@ struct cello_mesh {
   int* d_group_start = nullptr;
   double* d_reg = nullptr;
   double* d_partials = nullptr;
+  long long* d_slow = nullptr;     // ghost runs that are not same-level copies (leaf * runs + run)
+  std::vector<int> slow_start;     // per-leaf offsets into d_slow, B + 1 entries
   int exec_mode = CELLO_EXEC_BATCHED;
   int sweep_variant = 0;           // chosen by cello_autotune or cello_set_sweep_variant
   unsigned* d_work = nullptr;      // work counter of the persistent sweep variants
@@ -189,6 +191,8 @@ struct cello_mesh {
     if (d_zero) cudaFree(d_zero);
     d_work = nullptr;
     d_zero = nullptr;
+    if (d_slow) cudaFree(d_slow);
+    d_slow = nullptr;
     void* ptrs[] = {d_leaf, d_keys, d_kind, d_idx, d_fine8, d_face_slot, d_cfaces, d_group_start, d_reg, d_partials};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -388,6 +392,51 @@ cello_status finish_build(cello_mesh* M) {
   CELLO_TRY(upload(&M->d_group_start, M->group_start));
   if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * 5 * d.n * d.n * sizeof(double)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_partials, (size_t)std::max(B, 1) * 6 * sizeof(double)));
+  // ghost runs the vector-copy refresh leaves to the per-cell kernel
+  {
+    const int NS = ghost_run_count(d.n);
+    std::vector<long long> slow;
+    M->slow_start.assign((size_t)B + 1, 0);
+    std::vector<int> cand;
+    for (int b = 0; b < B; ++b) {
+      bool all_same = true;
+      for (int e = 0; e < 27 && all_same; ++e) all_same = M->kind[(size_t)b * 27 + e] == kSame;
+      if (!all_same) cand.push_back(b);
+    }
+    const int chunk = 4096;
+    unsigned char* d_cls = nullptr;
+    std::vector<unsigned char> cls;
+    if (!cand.empty()) {
+      CELLO_CUDA(cudaMalloc((void**)&d_cls, (size_t)chunk * NS));
+      cls.resize((size_t)chunk * NS);
+    }
+    size_t ci = 0;
+    for (int b = 0; b < B; ++b) {
+      M->slow_start[b] = (int)slow.size();
+      if (ci < cand.size() && cand[ci] == b) {
+        // classify a run of consecutive candidate leaves in one launch
+        size_t cj = ci;
+        while (cj < cand.size() && cand[cj] == b + (int)(cj - ci) && (int)(cj - ci) < chunk) ++cj;
+        const int nl = (int)(cj - ci);
+        launch_classify_runs(dm, b, nl, d_cls, 0);
+        cudaError_t e = cudaMemcpy(cls.data(), d_cls, (size_t)nl * NS, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+          cudaFree(d_cls);
+          return fail(CELLO_ECUDA, cudaGetErrorString(e));
+        }
+        for (int l = 0; l < nl; ++l) {
+          M->slow_start[b + l] = (int)slow.size();
+          for (int r = 0; r < NS; ++r)
+            if (cls[(size_t)l * NS + r]) slow.push_back((long long)(b + l) * NS + r);
+        }
+        b += nl - 1;
+        ci = cj;
+      }
+    }
+    M->slow_start[B] = (int)slow.size();
+    if (d_cls) cudaFree(d_cls);
+    CELLO_TRY(upload(&M->d_slow, slow));
+  }
   CELLO_CUDA(cudaMalloc((void**)&M->d_work, sizeof(unsigned)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_zero, sizeof(double)));
   CELLO_CUDA(cudaMemset(M->d_zero, 0, sizeof(double)));
@@ -396,8 +445,10 @@ cello_status finish_build(cello_mesh* M) {
 }
 
 void launch_refresh(const cello_mesh* M, const DevMesh& dm, void* U, int leaf0, int nleaf, cudaStream_t s) {
-  if (M->desc.precision == 4) launch_refresh_f32(dm, static_cast<float*>(U), leaf0, nleaf, s);
-  else launch_refresh_f64(dm, static_cast<double*>(U), leaf0, nleaf, s);
+  const int s0 = M->slow_start[leaf0], s1 = M->slow_start[leaf0 + nleaf];
+  const long long* slow = M->d_slow ? M->d_slow + s0 : nullptr;
+  if (M->desc.precision == 4) launch_refresh_f32(dm, static_cast<float*>(U), leaf0, nleaf, slow, s1 - s0, s);
+  else launch_refresh_f64(dm, static_cast<double*>(U), leaf0, nleaf, slow, s1 - s0, s);
 }
 
 // Transverse pencil ranges of a sweep along `axis`: a transverse axis already

@@ -138,7 +138,7 @@ def test_sweep_variants_identical_and_autotune(blob_amr, precision):
     state unchanged and picks one of them."""
     od, om, flags, U0, Uo, dts = blob_amr
     gm = H.gpu_mesh_from_flags(od, flags, precision)
-    nv = 8 if precision == 4 else 2
+    nv = 10 if precision == 4 else 2
     outs = []
     for v in range(nv):
         gm.set_sweep_variant(v)
