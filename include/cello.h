@@ -105,6 +105,19 @@ cello_status cello_neighbour_table(const cello_mesh* mesh, int8_t* kind_host, in
 cello_status cello_refine_flags(cello_mesh* mesh, const void* U, int field, double tau,
                                 double tau_coarsen, int8_t* flags_dev, void* stream);
 
+/* Remap field data onto a mesh rebuilt from `old` by one cello_octree_build
+ * (Sec. II.B: Refine, with Prolong and Restrict moving data between levels).
+ * U_old (old's pool, ghosts already refreshed) is read; the interior cells
+ * of every leaf of U_new (neu's pool) are written, ghosts are not (refresh
+ * before use).  Per new leaf: copy if the leaf existed; if an old leaf k
+ * levels coarser contains it, the old cell's minmod-limited linear
+ * reconstruction evaluated at the new cell centre, U_C + ((xi_x D_x + xi_y
+ * D_y) + xi_z D_z), xi the offset in old-cell widths (conservative); if its
+ * 8 children were old leaves, their mean (restriction).  Blocks until done.
+ * CELLO_EINVAL if the meshes are not related by one adaptation. */
+cello_status cello_remap(const cello_mesh* old, const void* U_old, const cello_mesh* neu, void* U_new,
+                         void* stream);
+
 /* Ghost refresh (Sec. II.B, Fig. 4; Restrict and Prolong): every ghost cell
  * of every leaf takes the value of the cell at its own level and position
  * after the physical boundary rule (periodic wrap, outflow clamp to the

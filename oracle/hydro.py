@@ -651,3 +651,80 @@ def refine_flags(U, mesh: Mesh, field: int, tau: float, tau_c: float):
     flags[(~hit_c) & (L > 0)] = -1
     flags[hit & (L < d.max_level)] = 1
     return flags
+
+
+# ------------------------------------------------------------------- remap
+def remap(U_old, old: Mesh, new: Mesh):
+    """Field data of a rebuilt mesh (Sec. II.B: Refine with Prolong and
+    Restrict move data between levels).  U_old must have refreshed ghosts.
+    Per new leaf, interior cells only (ghosts are left zero):
+      * the same leaf existed: copy;
+      * an old leaf k levels coarser contains it: conservative minmod-limited
+        linear reconstruction of the old cell C evaluated at the new cell
+        centre, U = U_C + ((xi_x D_x + xi_y D_y) + xi_z D_z), xi the centre
+        offset in units of the old cell width (+-1/4 for k = 1; +-1/8, +-3/8
+        for k = 2), D_d = minmod(U_C - U_C-e_d, U_C+e_d - U_C) from the old
+        leaf's padded block;
+      * its 8 children were old leaves: restriction, mean of the 8 old cells
+        in (dz, dy, dx) order times 0.125."""
+    d = new.desc
+    n, g = d.n, d.ghosts
+    N = n + 2 * g
+    out = torch.zeros((new.n_leaves, 5, N, N, N), dtype=U_old.dtype)
+    r = torch.arange(n)
+    for b, (L, i, j, k) in enumerate(new.leaves):
+        L, i, j, k = int(L), int(i), int(j), int(k)
+        t = (L, i, j, k)
+        if t in old.index:
+            src = old.index[t]
+            out[b, :, g:g + n, g:g + n, g:g + n] = U_old[src, :, g:g + n, g:g + n, g:g + n]
+            continue
+        anc = None
+        for kk in range(1, L + 1):
+            a = (L - kk, i >> kk, j >> kk, k >> kk)
+            if a in old.index:
+                anc = (old.index[a], kk, a)
+                break
+        if anc is not None:
+            src, kk, a = anc
+            A = U_old[src]
+            cell = [((c0 * n + r) >> kk) - a[1 + ax] * n + g for ax, c0 in enumerate((i, j, k))]
+            xi = [(((c0 * n + r) % (1 << kk)).to(torch.float64) + 0.5) / (1 << kk) - 0.5 for c0 in (i, j, k)]
+            cz, cy, cx = cell[2].view(-1, 1, 1), cell[1].view(1, -1, 1), cell[0].view(1, 1, -1)
+            Uc = A[:, cz, cy, cx]
+            D = []
+            for ax, (oz, oy, ox) in enumerate(((0, 0, 1), (0, 1, 0), (1, 0, 0))):
+                Um = A[:, cz - oz, cy - oy, cx - ox]
+                Up = A[:, cz + oz, cy + oy, cx + ox]
+                D.append(minmod(Uc - Um, Up - Uc))
+            xz, xy, xx = xi[2].view(1, -1, 1, 1), xi[1].view(1, 1, -1, 1), xi[0].view(1, 1, 1, -1)
+            out[b, :, g:g + n, g:g + n, g:g + n] = Uc + ((xx * D[0] + xy * D[1]) + xz * D[2])
+            continue
+        h = n // 2
+        for o in range(8):
+            ox, oy, oz = o & 1, (o >> 1) & 1, o >> 2
+            c = (L + 1, 2 * i + ox, 2 * j + oy, 2 * k + oz)
+            assert c in old.index, "meshes are not one adaptation apart"
+            C = U_old[old.index[c]]
+            v = None
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        blk = C[:, g + dz:g + n:2, g + dy:g + n:2, g + dx:g + n:2]
+                        v = blk if v is None else v + blk
+            out[b, :, g + oz * h:g + (oz + 1) * h, g + oy * h:g + (oy + 1) * h, g + ox * h:g + (ox + 1) * h] = v * 0.125
+    return out
+
+
+def adapt(U, mesh: Mesh, field: int = 0, tau: float = 0.3, tau_c: float | None = None):
+    """Refresh, flag, rebuild and remap (the oracle's adaptation step)."""
+    from .mesh import build
+    tau_c = tau / 4 if tau_c is None else tau_c
+    U = ghost_refresh(U, mesh)
+    flags = refine_flags(U, mesh, field, tau, tau_c).numpy()
+    if not flags.any():
+        return mesh, U, flags
+    new = build(mesh.desc, mesh, flags)
+    if np.array_equal(new.leaves, mesh.leaves):
+        return mesh, U, flags
+    return new, remap(U, mesh, new), flags

@@ -106,6 +106,17 @@ class Mesh:
         self._check_state(U)
         _lib.check(_lib.lib().cello_ghost_refresh(self.handle, _ptr(U), _stream(stream)), "cello_ghost_refresh")
 
+    def remap_from(self, old: "Mesh", U_old, U_new=None, stream=None):
+        """Interior data of this mesh from `old` (ghosts of U_old refreshed);
+        returns U_new (allocated if not given; its ghosts are not written)."""
+        old._check_state(U_old)
+        if U_new is None:
+            U_new = torch.zeros((self.n_leaves, 5, self.N, self.N, self.N), dtype=self.dtype, device=U_old.device)
+        self._check_state(U_new)
+        _lib.check(_lib.lib().cello_remap(old.handle, _ptr(U_old), self.handle, _ptr(U_new), _stream(stream)),
+                   "cello_remap")
+        return U_new
+
     def hydro_step(self, U, dt, cycle, cfl=0.4, dt_next=None, totals=None, stream=None):
         """dt, dt_next: float64 CUDA tensors of one element; totals: five."""
         self._check_state(U)

@@ -85,6 +85,17 @@ struct AdjSweepParams {
   int n_items;
 };
 
+// Remap of one new leaf from the old mesh: copy (src[0]), prolongation from
+// the old leaf src[0] that is k levels coarser, or restriction from the 8 old
+// children src[octant].
+struct RemapEntry {
+  int kind;   // 0 copy, 1 prolong, 2 restrict
+  int k;
+  int src[8];
+};
+void launch_remap(const DevMesh& neu, const DevMesh& old, const void* Uold, void* Unew, const RemapEntry* map,
+                  int precision, cudaStream_t s);
+
 // Accessors for translation units that see cello_mesh only as an opaque type.
 DevMesh mesh_dev(const cello_mesh* mesh);
 int mesh_precision(const cello_mesh* mesh);

@@ -200,6 +200,24 @@ void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t
 #undef CELLO_ZG
 }
 
+void launch_remap(const DevMesh& neu, const DevMesh& old, const void* Uold, void* Unew, const RemapEntry* map,
+                  int precision, cudaStream_t s) {
+  const long threads = (long)neu.B * neu.n * neu.n * neu.n;
+  if (threads <= 0) return;
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+#define CELLO_RM(T, NB) \
+  remap_kernel<T, NB><<<grid, 256, 0, s>>>(neu, old, static_cast<const T*>(Uold), static_cast<T*>(Unew), map)
+#define CELLO_RM_T(T)                       \
+  switch (neu.n) {                          \
+    case 8: CELLO_RM(T, 8); break;          \
+    case 16: CELLO_RM(T, 16); break;        \
+    case 32: CELLO_RM(T, 32); break;        \
+  }
+  if (precision == 4) { CELLO_RM_T(float) } else { CELLO_RM_T(double) }
+#undef CELLO_RM_T
+#undef CELLO_RM
+}
+
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s) {
   if (m.B <= 0) return;

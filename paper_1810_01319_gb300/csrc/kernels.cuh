@@ -438,6 +438,61 @@ __global__ void __launch_bounds__(256) classify_runs_kernel(DevMesh m, int leaf0
 }
 
 // =====================================================================
+// Remap onto a rebuilt mesh: one thread per interior cell of a new leaf.
+// =====================================================================
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) remap_kernel(DevMesh neu, DevMesh old, const T* Uold, T* Unew,
+                                                    const RemapEntry* map) {
+  constexpr int G = kGhosts, N = NB + 2 * G, H = NB / 2;
+  constexpr long SLAB = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)neu.B * NB * NB * NB) return;
+  const int leaf = (int)(gid / (NB * NB * NB));
+  const int i = (int)(gid % (NB * NB * NB));
+  const int r[3] = {i % NB, (i / NB) % NB, i / (NB * NB)};
+  const RemapEntry e = map[leaf];
+  T v[5];
+  if (e.kind == 0) {
+    load5<T, NB>(Uold, e.src[0], r[0] + G, r[1] + G, r[2] + G, v);
+  } else if (e.kind == 2) {
+    const int o[3] = {r[0] / H, r[1] / H, r[2] / H};
+    restrict8<T, NB>(Uold, e.src[o[2] * 4 + o[1] * 2 + o[0]], 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G,
+                     2 * r[2] - o[2] * NB + G, v);
+  } else {
+    const int4 nl = neu.leaf[leaf];
+    const int4 al = old.leaf[e.src[0]];
+    const int k = e.k;
+    const int nij[3] = {nl.y, nl.z, nl.w}, aij[3] = {al.y, al.z, al.w};
+    int c[3];
+    T xi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int gf = nij[a] * NB + r[a];
+      c[a] = (gf >> k) - aij[a] * NB + G;
+      xi[a] = T((double((gf & ((1 << k) - 1))) + 0.5) / double(1 << k) - 0.5);
+    }
+    T Uc[5], D[3][5];
+    load5<T, NB>(Uold, e.src[0], c[0], c[1], c[2], Uc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+      cm[a] -= 1;
+      cp[a] += 1;
+      T Um[5], Up[5];
+      load5<T, NB>(Uold, e.src[0], cm[0], cm[1], cm[2], Um);
+      load5<T, NB>(Uold, e.src[0], cp[0], cp[1], cp[2], Up);
+#pragma unroll
+      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+    }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) v[f] = Uc[f] + ((xi[0] * D[0][f] + xi[1] * D[1][f]) + xi[2] * D[2][f]);
+  }
+  const long dst = (long)leaf * 5 * SLAB + ((long)(r[2] + G) * N + (r[1] + G)) * N + (r[0] + G);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) Unew[dst + f * SLAB] = v[f];
+}
+
+// =====================================================================
 // CFL dt candidates and conserved sums, one CTA per leaf (partials), then a
 // single-CTA fixed-order finish.  Deterministic for a fixed launch shape.
 // =====================================================================

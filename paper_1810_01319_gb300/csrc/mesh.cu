@@ -720,6 +720,61 @@ cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycl
   return CELLO_OK;
 }
 
+cello_status cello_remap(const cello_mesh* old, const void* U_old, const cello_mesh* neu, void* U_new,
+                         void* stream) {
+  if (!old || !neu || !U_old || !U_new) return fail(CELLO_EINVAL, "NULL argument");
+  if (std::memcmp(&old->desc, &neu->desc, sizeof(cello_mesh_desc)) != 0)
+    return fail(CELLO_EINVAL, "meshes built from different descriptions");
+  std::unordered_map<unsigned long long, int> where;
+  for (int b = 0; b < old->B; ++b) {
+    const int4 l = old->leaves[b];
+    where[pack(Node{l.x, l.y, l.z, l.w})] = b;
+  }
+  std::vector<RemapEntry> map(neu->B);
+  for (int b = 0; b < neu->B; ++b) {
+    const int4 l = neu->leaves[b];
+    const Node t{l.x, l.y, l.z, l.w};
+    RemapEntry e{};
+    auto it = where.find(pack(t));
+    if (it != where.end()) {
+      e.kind = 0;
+      e.src[0] = it->second;
+    } else {
+      bool found = false;
+      for (int k = 1; k <= t.L && !found; ++k) {
+        auto a = where.find(pack(Node{t.L - k, t.i >> k, t.j >> k, t.k >> k}));
+        if (a != where.end()) {
+          e.kind = 1;
+          e.k = k;
+          e.src[0] = a->second;
+          found = true;
+        }
+      }
+      if (!found) {
+        e.kind = 2;
+        for (int o = 0; o < 8; ++o) {
+          auto c = where.find(pack(child(t, o)));
+          if (c == where.end()) return fail(CELLO_EINVAL, "meshes are not one adaptation apart");
+          e.src[o] = c->second;
+        }
+      }
+    }
+    map[b] = e;
+  }
+  RemapEntry* d_map = nullptr;
+  CELLO_CUDA(cudaMalloc((void**)&d_map, map.size() * sizeof(RemapEntry)));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(RemapEntry), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    launch_remap(neu->dev(), old->dev(), U_old, U_new, d_map, neu->desc.precision, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the map is freed below
+  cudaFree(d_map);
+  CELLO_CUDA(e);
+  return CELLO_OK;
+}
+
 cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, const double* dt, int cycle,
                                       void* stream) {
   if (!M || !Un || !lam || !dt) return fail(CELLO_EINVAL, "NULL argument");

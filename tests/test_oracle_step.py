@@ -227,3 +227,38 @@ def test_prolong_restrict_identities():
     for k in kids[1:]:
         s = s + k
     assert ((s * 0.125) - Uc[0]).abs().max() < 1e-15
+
+
+def test_remap_conserves_and_reproduces_linear_fields():
+    d = M.Desc(root=(2, 2, 2), n=8, ghosts=4, max_level=3, bc=(M.PERIODIC,) * 3, gamma=1.4)
+    rng = np.random.default_rng(3)
+    old = M.root_mesh(d)
+    for _ in range(2):
+        old = M.build(d, old, rng.choice([0, 1], size=old.n_leaves, p=[0.5, 0.5]))
+    lv = old.leaves[:, 0]
+    flags = np.where(lv == lv.max(), -1, rng.choice([0, 1], size=old.n_leaves, p=[0.6, 0.4])).astype(np.int8)
+    new = M.build(d, old, flags)
+    kinds = set()
+    for t in map(tuple, new.leaves.tolist()):
+        kinds.add("copy" if t in old.index else ("restrict" if all(
+            (t[0] + 1, 2 * t[1] + (o & 1), 2 * t[2] + ((o >> 1) & 1), 2 * t[3] + (o >> 2)) in old.index
+            for o in range(8)) else "prolong"))
+    assert kinds == {"copy", "restrict", "prolong"}
+    U = ics.blobs(old.leaves, d.root, d.n, d.ghosts, d.lo, d.hi, d.gamma, count=8, seed=2)
+    U = H.ghost_refresh(U, old)
+    V = H.remap(U, old, new)
+    scale = _totals(old, U.abs())
+    assert ((_totals(new, V) - _totals(old, U)).abs() / scale).max() < 1e-14
+    # a linear field (away from the periodic seam) is reproduced exactly
+    x, y, z = ics.cell_centres(old.leaves, d.root, d.n, d.ghosts, d.lo, d.hi)
+    lin = lambda x, y, z: 1.0 + 0.5 * x - 0.25 * y + 0.125 * z
+    Ul = torch.stack([lin(x, y, z)] * 5, 1).contiguous()
+    Ul = H.ghost_refresh(Ul, old)
+    Vl = H.remap(Ul, old, new)
+    xn, yn, zn = ics.cell_centres(new.leaves, d.root, d.n, d.ghosts, d.lo, d.hi)
+    g, n = d.ghosts, d.n
+    want = lin(xn, yn, zn)[:, g:g + n, g:g + n, g:g + n]
+    got = Vl[:, 0, g:g + n, g:g + n, g:g + n]
+    inner = ((xn > 0.2) & (xn < 0.8) & (yn > 0.2) & (yn < 0.8) & (zn > 0.2) & (zn < 0.8))[:, g:g + n, g:g + n, g:g + n]
+    assert inner.sum() > 1000
+    assert (got - want)[inner].abs().max() < 1e-14
