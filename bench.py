@@ -43,6 +43,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# ------------------------------------------------------------- multi-rank
+def combine_ranks(ms: float, cells: int, steps: int):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (max over ranks) and the cells of all ranks.  Returns (value, ms_max).
+    Runs on any initialised process group (nccl on GPUs, gloo on CPU)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return cells * steps / (ms / 1e3), ms
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(c) * steps / (float(t) / 1e3), float(t)
+
+
 # ------------------------------------------------------------------ mesh
 def build_workload(cfg, precision, device="cuda", chunk=1024, log=print):
     """Refine on the initial blob field to a fixpoint with the library's own
@@ -251,12 +267,9 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    value, ms = combine_ranks(ms, cells, args.steps)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t)
         torch.distributed.barrier()
-    value = cells * args.steps * world / (ms / 1e3)
     launches_per_step = 4 + 3 + (1 if mesh.n_coarse_fine else 0)
 
     # per-phase times of one batched step (events between the library's launches)

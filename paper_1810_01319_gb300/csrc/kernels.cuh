@@ -140,7 +140,7 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         L[k] = sC[k * A + j * S + p];
         R[k] = sA[k * A + (j + 1) * S + p];
       }
-      riemann_flux(L, R, gs, F);
+      riemann_flux_bulk(L, R, gs, F);
 #pragma unroll
       for (int k = 0; k < 5; ++k) sB[k * A + j * S + p] = F[k];
       if (prm.reg && (j == G - 1 || j == G + NB - 1)) {

@@ -228,4 +228,90 @@ CELLO_HD void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5])
   F[4] = u * (E + p);
 }
 
+// Float32 form of the same solver for the bulk path: the shock-curve
+// quantities are rewritten with shared reciprocals, algebraically identical
+// to riemann_flux (x = 1 + g1 (p*/p - 1) = (g1/p) p* + (1 - g1),
+// W = C sqrt(x), (p* - p)/W = (p* - p) rsqrt(x)/C, Z = 2W^3/(W^2 + C^2) =
+// 2 W x/(x + 1)); the float64 path keeps the literal formulas.
+CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<float>& gs, float F[5]) {
+  const float rL = L[0], uL = L[1], pL = L[4];
+  const float rR = R[0], uR = R[1], pR = R[4];
+  const float qL = (gs.gamma * pL) * rL, qR = (gs.gamma * pR) * rR;
+#ifdef __CUDA_ARCH__
+  const float iCL = rsqrtf(qL), iCR = rsqrtf(qR);
+#else
+  const float iCL = 1.0f / sqrtf(qL), iCR = 1.0f / sqrtf(qR);
+#endif
+  const float CL = qL * iCL, CR = qR * iCR;
+  float ps = ((CR * pL + CL * pR) + (CL * CR) * (uL - uR)) / (CL + CR);
+  ps = vmax(ps, float(kPFloor));
+  const float aL = gs.g1 / pL, aR = gs.g1 / pR, b = 1.0f - gs.g1;
+  float WLs, WRs, uLs, uRs, ZL, ZR;
+#pragma unroll 1
+  for (int it = 0; it <= kRiemannIters; ++it) {
+    const float xL = aL * ps + b, xR = aR * ps + b;
+#ifdef __CUDA_ARCH__
+    const float rxL = rsqrtf(xL), rxR = rsqrtf(xR);
+#else
+    const float rxL = 1.0f / sqrtf(xL), rxR = 1.0f / sqrtf(xR);
+#endif
+    WLs = CL * (xL * rxL);
+    WRs = CR * (xR * rxR);
+    uLs = uL - (ps - pL) * (iCL * rxL);
+    uRs = uR + (ps - pR) * (iCR * rxR);
+    ZL = (2.0f * WLs) * xL / (xL + 1.0f);
+    ZR = (2.0f * WRs) * xR / (xR + 1.0f);
+    if (it == kRiemannIters) break;
+    ps = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), float(kPFloor));
+  }
+  const float us = (ZL * uLs + ZR * uRs) / (ZL + ZR);
+  const bool left = us >= 0.0f;
+  const float rs = left ? rL : rR;
+  const float u_s = left ? uL : uR;
+  const float p_s = left ? pL : pR;
+  const float W_s = left ? WLs : WRs;
+  const float t1 = left ? L[2] : R[2];
+  const float t2 = left ? L[3] : R[3];
+  const float v_s = left ? -uL : uR;
+  const float v_star = left ? -us : us;
+  const float irs = 1.0f / rs;
+  const float tau = irs - (ps - p_s) / (W_s * W_s);
+  float rstar = (tau > 0.0f) ? 1.0f / tau : float(kRhoFloor);
+  rstar = vmax(rstar, float(kRhoFloor));
+  const float c_s = vsqrt((gs.gamma * p_s) * irs);
+  const float c_star = vsqrt((gs.gamma * ps) / rstar);
+  const bool shock = ps > p_s;
+  const float head = shock ? v_s + W_s * irs : v_s + c_s;
+  const float tail = shock ? head : v_star + c_star;
+  const bool orig = head <= 0.0f;
+  const bool star = !orig && (tail > 0.0f);
+  float r, u, p;
+  if (orig) {
+    r = rs; u = u_s; p = p_s;
+  } else if (star) {
+    r = rstar; u = us; p = ps;
+  } else {
+    const float w = head / (head - tail);
+    r = rs + w * (rstar - rs);
+    u = u_s + w * (us - u_s);
+    p = p_s + w * (ps - p_s);
+  }
+  const float f0 = r * u;
+  F[0] = f0;
+  F[1] = f0 * u + p;
+  F[2] = f0 * t1;
+  F[3] = f0 * t2;
+  const float E = p * gs.inv_gm1 + (0.5f * r) * (u * u + (t1 * t1 + t2 * t2));
+  F[4] = u * (E + p);
+}
+
+template <typename T>
+CELLO_HD void riemann_flux_bulk(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+  riemann_flux(L, R, gs, F);
+}
+template <>
+CELLO_HD void riemann_flux_bulk<float>(const float L[5], const float R[5], const Gas<float>& gs, float F[5]) {
+  riemann_flux_fast(L, R, gs, F);
+}
+
 }  // namespace cello
