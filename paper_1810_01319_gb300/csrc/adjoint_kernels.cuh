@@ -42,11 +42,14 @@ adjoint_sweep_kernel(DevMesh m, AdjSweepParams prm) {
   const int t = threadIdx.x;
   const int lc = axis == 0 ? t % N : t / P;
   const int lp = axis == 0 ? t / N : t % P;
+  __shared__ T s_dtdx[16];
+  if (t <= m.max_level) s_dtdx[t] = T(*prm.dt / ldexp(m.dx0, -t));
+  __syncthreads();
 
   for (int item = blockIdx.x; item < prm.n_items; item += gridDim.x) {
     const int leaf = prm.leaf0 + item / prm.tiles_per_leaf;
     const int tile = item % prm.tiles_per_leaf;
-    const T dtdx = T(*prm.dt / ldexp(m.dx0, -m.leaf[leaf].x));
+    const T dtdx = s_dtdx[m.leaf[leaf].x];
     const int q = tile * P + lp;
     const bool valid = q < cA * cB;
     const int pa = prm.a0 + (valid ? q / cB : 0), pb = prm.b0 + (valid ? q % cB : 0);

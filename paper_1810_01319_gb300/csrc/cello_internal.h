@@ -61,6 +61,21 @@ struct CoarseFace {
   int fslot[4];   // register slots of the fine fluxes, index o2*2 + o1
 };
 
+// Unsigned division by a launch-time constant as a multiply-high and shift
+// (Granlund & Montgomery): valid for dividends below 2^31.
+struct FastDiv {
+  unsigned d, m, s;
+  __host__ __device__ static FastDiv make(unsigned d) {
+    FastDiv f;
+    f.d = d;
+    f.s = 0;
+    while ((1u << f.s) < d) ++f.s;
+    f.m = (unsigned)((((unsigned long long)1 << 32) * ((1ull << f.s) - d)) / d + 1);
+    return f;
+  }
+  __device__ __forceinline__ unsigned div(unsigned x) const { return (__umulhi(x, m) + x) >> s; }
+};
+
 struct SweepParams {
   void* U;
   int leaf0, nleaf;        // leaves [leaf0, leaf0 + nleaf)
@@ -72,6 +87,7 @@ struct SweepParams {
   unsigned* work;          // work counter for persistent variants (device, 4 bytes)
   int n_items;             // set by the launcher
   int variant;             // index into the sweep variants of the precision
+  FastDiv div_tiles, div_cb;   // set by the launcher: by tiles_per_leaf and by the B-range length
 };
 
 struct AdjSweepParams {
@@ -117,7 +133,7 @@ void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const 
 void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const long long* slow, int nslow,
                         cudaStream_t s);
 int ghost_run_count(int n);
-void launch_classify_runs(const DevMesh& m, int leaf0, int nleaf, unsigned char* out, cudaStream_t s);
+void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsigned char* out, cudaStream_t s);
 void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces,

@@ -37,6 +37,8 @@ static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, 
   p.tiles_per_leaf = (pencils + P - 1) / P;
   p.n_items = p.nleaf * p.tiles_per_leaf;
   if (p.n_items <= 0) return;
+  p.div_tiles = FastDiv::make((unsigned)p.tiles_per_leaf);
+  p.div_cb = FastDiv::make((unsigned)(p.b1 - p.b0));
   int grid = p.n_items;
   if (kVariants[v].persistent && p.work) {
     cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);

@@ -37,6 +37,8 @@ static void launch_nb64(const DevMesh& m, SweepParams p, int pencils, cudaStream
   p.tiles_per_leaf = (pencils + 7) / 8;
   p.n_items = p.nleaf * p.tiles_per_leaf;
   if (p.n_items <= 0) return;
+  p.div_tiles = FastDiv::make((unsigned)p.tiles_per_leaf);
+  p.div_cb = FastDiv::make((unsigned)(p.b1 - p.b0));
   int grid = p.n_items;
   if (kVariants64[v].persistent && p.work) {
     cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
@@ -102,7 +104,7 @@ static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, const long l
                       cudaStream_t s) {
   const long threads = (long)ghost_runs<NB>() * nleaf;
   if (threads > 0) refresh_kernel<T, NB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, U, leaf0, nleaf);
-  if (nslow > 0) refresh_slow_kernel<T, NB><<<(nslow * 4 + 127) / 128, 128, 0, s>>>(m, U, slow, nslow);
+  if (nslow > 0) refresh_slow_kernel<T, NB><<<(nslow + 127) / 128, 128, 0, s>>>(m, U, slow, nslow);
 }
 
 template <typename T>
@@ -126,14 +128,14 @@ void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const
 
 int ghost_run_count(int n) { return n == 8 ? ghost_runs<8>() : (n == 16 ? ghost_runs<16>() : ghost_runs<32>()); }
 
-void launch_classify_runs(const DevMesh& m, int leaf0, int nleaf, unsigned char* out, cudaStream_t s) {
+void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsigned char* out, cudaStream_t s) {
   const long threads = (long)ghost_run_count(m.n) * nleaf;
   if (threads <= 0) return;
   const unsigned grid = (unsigned)((threads + 255) / 256);
   switch (m.n) {
-    case 8: classify_runs_kernel<8><<<grid, 256, 0, s>>>(m, leaf0, nleaf, out); break;
-    case 16: classify_runs_kernel<16><<<grid, 256, 0, s>>>(m, leaf0, nleaf, out); break;
-    case 32: classify_runs_kernel<32><<<grid, 256, 0, s>>>(m, leaf0, nleaf, out); break;
+    case 8: classify_runs_kernel<8><<<grid, 256, 0, s>>>(m, leaves, nleaf, out); break;
+    case 16: classify_runs_kernel<16><<<grid, 256, 0, s>>>(m, leaves, nleaf, out); break;
+    case 32: classify_runs_kernel<32><<<grid, 256, 0, s>>>(m, leaves, nleaf, out); break;
   }
 }
 

@@ -54,6 +54,11 @@ sweep_kernel(DevMesh m, SweepParams prm) {
   const int lc = t / P, lp = t % P;           // this thread's cell and pencil
   const int cp = lp, cj = lc;
   __shared__ int s_item;
+  __shared__ T s_dtdx[16];
+  // dt/dx per level, once per CTA (a float64 division per thread and item
+  // would occupy the GPU's slow float64 pipe)
+  if (t <= m.max_level) s_dtdx[t] = T(*prm.dt / ldexp(m.dx0, -t));
+  __syncthreads();
 
   int item = blockIdx.x;
   if (prm.work) {
@@ -62,16 +67,17 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     item = s_item;
   }
   while (item < prm.n_items) {
-    const int leaf = prm.leaf0 + item / prm.tiles_per_leaf;
-    const int tile = item % prm.tiles_per_leaf;
+    const int lrel = (int)prm.div_tiles.div((unsigned)item);
+    const int leaf = prm.leaf0 + lrel;
+    const int tile = item - lrel * prm.tiles_per_leaf;
     const int4 lf = m.leaf[leaf];
-    const double dtdx_d = *prm.dt / ldexp(m.dx0, -lf.x);
-    const T dtdx = T(dtdx_d);
+    const T dtdx = s_dtdx[lf.x];
 
     // ---- phase 1
     const int q = tile * P + lp;
     const bool valid = q < cA * cB;
-    const int pa = prm.a0 + (valid ? q / cB : 0), pb = prm.b0 + (valid ? q % cB : 0);
+    const int qa = (int)prm.div_cb.div((unsigned)q);
+    const int pa = prm.a0 + (valid ? qa : 0), pb = prm.b0 + (valid ? q - qa * cB : 0);
     T* base = U + (long)leaf * 5 * SLAB + pa * sTA + pb * sTB + lc * sAx;
     T Uc[5];
     if (valid) {
@@ -146,7 +152,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
       if (prm.reg && (j == G - 1 || j == G + NB - 1)) {
         const int qq = tile * P + p;
         if (qq < cA * cB) {
-          const int ca = prm.a0 + qq / cB, cb = prm.b0 + qq % cB;
+          const int qqa = (int)prm.div_cb.div((unsigned)qq);
+          const int ca = prm.a0 + qqa, cb = prm.b0 + qq - qqa * cB;
           if (ca >= G && ca < G + NB && cb >= G && cb < G + NB) {
             const int face = 2 * axis + (j == G - 1 ? 0 : 1);
             const int slot = m.face_slot[leaf * 6 + face];
@@ -404,34 +411,107 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0
   for (int f = 0; f < 5; ++f) v[f].store(U + dst + f * SLAB);
 }
 
-// The remaining runs (listed per mesh as leaf * runs + run), cell by cell:
-// restriction, prolongation, or clamped copies at outflow boundaries.
+// The remaining runs (listed per mesh as leaf * runs + run), one run of four
+// cells per thread: a run clamped along x repeats one value; a run inside a
+// finer neighbour restricts cell by cell; a run inside a coarser neighbour
+// covers two parent cells, each prolonged once for its two children.
 template <typename T, int NB>
 __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, const long long* runs, int nruns) {
   constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
   constexpr long SLAB = (long)N * N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nruns * 4) return;
-  const long long r = runs[i >> 2];
+  if (i >= nruns) return;
+  const long long r = runs[i];
   const int leaf = (int)(r / NS);
   int x0, y, z;
   ghost_coord<NB>((int)(r % NS) * 4, x0, y, z);
-  int cc[3] = {x0 + (i & 3), y, z};
-  const long dst = (long)leaf * 5 * SLAB + ((long)z * N + y) * N + cc[0];
-  T v[5];
-  ghost_value<T, NB>(m, U, leaf, cc, v);
+  const long dst = (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x0;
+  int d[3] = {x0 < G ? -1 : (x0 >= G + NB ? 1 : 0), y < G ? -1 : (y >= G + NB ? 1 : 0),
+              z < G ? -1 : (z >= G + NB ? 1 : 0)};
+  int c[3] = {x0, y, z};
+  bool xclamp = false;
 #pragma unroll
-  for (int f = 0; f < 5; ++f) U[dst + f * SLAB] = v[f];
+  for (int a = 0; a < 3; ++a)
+    if (d[a] != 0 && m.kind[leaf * 27 + face_dir(a, d[a])] == kBoundary) {
+      c[a] = d[a] < 0 ? G : G + NB - 1;
+      d[a] = 0;
+      if (a == 0) xclamp = true;
+    }
+  const int e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
+  const int8_t k = m.kind[e];
+  if (xclamp) {   // every cell of the run reads the same boundary cell
+    int cc[3] = {c[0], c[1], c[2]};
+    T v[5];
+    ghost_value<T, NB>(m, U, leaf, cc, v);
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int f = 0; f < 5; ++f) U[dst + q + f * SLAB] = v[f];
+    return;
+  }
+  if (k != kCoarse) {
+    for (int q = 0; q < 4; ++q) {
+      int cc[3] = {x0 + q, y, z};
+      T v[5];
+      ghost_value<T, NB>(m, U, leaf, cc, v);
+#pragma unroll
+      for (int f = 0; f < 5; ++f) U[dst + q + f * SLAB] = v[f];
+    }
+    return;
+  }
+  // coarser neighbour: parents of cells (x0, x0+1) and (x0+2, x0+3)
+  const int4 lf = m.leaf[leaf];
+  const int C = m.idx[e];
+  const int4 cl = m.leaf[C];
+  const int L = lf.x;
+  const int lij[3] = {lf.y, lf.z, lf.w}, cij[3] = {cl.y, cl.z, cl.w};
+  int rcyz[3];
+  T sgn[3];
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    const int ncell = (m.root[a] << L) * NB;
+    const int gl = wrap_mod(lij[a] * NB + (c[a] - G), ncell);
+    rcyz[a] = (gl >> 1) - cij[a] * NB;
+    sgn[a] = (gl & 1) ? T(1) : T(-1);
+  }
+  const int ncx = (m.root[0] << L) * NB;
+  for (int h = 0; h < 2; ++h) {
+    const int gl = wrap_mod(lij[0] * NB + (x0 + 2 * h - G), ncx);   // even: the lower child
+    int rc[3] = {(gl >> 1) - cij[0] * NB, rcyz[1], rcyz[2]};
+    T Uc[5], D[3][5];
+    load5<T, NB>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T Um[5], Up[5];
+      int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
+      rm[a] -= 1;
+      rp[a] += 1;
+      if (rm[a] >= 0) load5<T, NB>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, 1, Uc, Up);
+#pragma unroll
+      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const T sx = q ? T(1) : T(-1);
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        U[dst + 2 * h + q + f * SLAB] = Uc[f] + T(0.25) * ((sx * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
+    }
+  }
 }
 
-// Classification of every run of some leaves, for the host's slow-run list:
-// out[(leaf - leaf0) * runs + run] = 1 if the run is not a plain copy.
+// Classification of every run of the listed leaves, for the host's slow-run
+// list: out[k * runs + run] = 1 if that run of leaf leaves[k] is not a plain
+// copy.
 template <int NB>
-__global__ void __launch_bounds__(256) classify_runs_kernel(DevMesh m, int leaf0, int nleaf, unsigned char* out) {
+__global__ void __launch_bounds__(256) classify_runs_kernel(DevMesh m, const int* leaves, int nleaf,
+                                                            unsigned char* out) {
   constexpr int NS = ghost_runs<NB>();
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)nleaf * NS) return;
-  const int leaf = leaf0 + (int)(gid / NS);
+  const int leaf = leaves[gid / NS];
   int x0, y, z, c[3], d[3], e;
   ghost_coord<NB>((int)(gid % NS) * 4, x0, y, z);
   out[gid] = run_is_copy<NB>(m, leaf, x0, y, z, c, d, e) ? 0 : 1;

@@ -392,49 +392,45 @@ cello_status finish_build(cello_mesh* M) {
   CELLO_TRY(upload(&M->d_group_start, M->group_start));
   if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * 5 * d.n * d.n * sizeof(double)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_partials, (size_t)std::max(B, 1) * 6 * sizeof(double)));
-  // ghost runs the vector-copy refresh leaves to the per-cell kernel
+  // ghost runs the vector-copy refresh leaves to the per-cell kernel: only
+  // leaves with a neighbour that is not a same-level leaf can have any
   {
     const int NS = ghost_run_count(d.n);
-    std::vector<long long> slow;
-    M->slow_start.assign((size_t)B + 1, 0);
     std::vector<int> cand;
     for (int b = 0; b < B; ++b) {
       bool all_same = true;
       for (int e = 0; e < 27 && all_same; ++e) all_same = M->kind[(size_t)b * 27 + e] == kSame;
       if (!all_same) cand.push_back(b);
     }
-    const int chunk = 4096;
-    unsigned char* d_cls = nullptr;
-    std::vector<unsigned char> cls;
+    std::vector<long long> slow;
+    std::vector<int> count((size_t)B, 0);
     if (!cand.empty()) {
-      CELLO_CUDA(cudaMalloc((void**)&d_cls, (size_t)chunk * NS));
-      cls.resize((size_t)chunk * NS);
-    }
-    size_t ci = 0;
-    for (int b = 0; b < B; ++b) {
-      M->slow_start[b] = (int)slow.size();
-      if (ci < cand.size() && cand[ci] == b) {
-        // classify a run of consecutive candidate leaves in one launch
-        size_t cj = ci;
-        while (cj < cand.size() && cand[cj] == b + (int)(cj - ci) && (int)(cj - ci) < chunk) ++cj;
-        const int nl = (int)(cj - ci);
-        launch_classify_runs(dm, b, nl, d_cls, 0);
-        cudaError_t e = cudaMemcpy(cls.data(), d_cls, (size_t)nl * NS, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) {
-          cudaFree(d_cls);
-          return fail(CELLO_ECUDA, cudaGetErrorString(e));
-        }
-        for (int l = 0; l < nl; ++l) {
-          M->slow_start[b + l] = (int)slow.size();
+      const int chunk = 8192;
+      int* d_cand = nullptr;
+      unsigned char* d_cls = nullptr;
+      std::vector<unsigned char> cls((size_t)std::min<size_t>(chunk, cand.size()) * NS);
+      cudaError_t e = cudaMalloc((void**)&d_cand, cand.size() * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemcpy(d_cand, cand.data(), cand.size() * sizeof(int), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&d_cls, cls.size());
+      for (size_t c0 = 0; c0 < cand.size() && e == cudaSuccess; c0 += chunk) {
+        const int nl = (int)std::min<size_t>(chunk, cand.size() - c0);
+        launch_classify_runs(dm, d_cand + c0, nl, d_cls, 0);
+        e = cudaMemcpy(cls.data(), d_cls, (size_t)nl * NS, cudaMemcpyDeviceToHost);
+        for (int l = 0; l < nl && e == cudaSuccess; ++l) {
+          const int b = cand[c0 + l];
           for (int r = 0; r < NS; ++r)
-            if (cls[(size_t)l * NS + r]) slow.push_back((long long)(b + l) * NS + r);
+            if (cls[(size_t)l * NS + r]) {
+              slow.push_back((long long)b * NS + r);
+              count[b]++;
+            }
         }
-        b += nl - 1;
-        ci = cj;
       }
+      if (d_cand) cudaFree(d_cand);
+      if (d_cls) cudaFree(d_cls);
+      if (e != cudaSuccess) return fail(CELLO_ECUDA, cudaGetErrorString(e));
     }
-    M->slow_start[B] = (int)slow.size();
-    if (d_cls) cudaFree(d_cls);
+    M->slow_start.assign((size_t)B + 1, 0);
+    for (int b = 0; b < B; ++b) M->slow_start[b + 1] = M->slow_start[b] + count[b];
     CELLO_TRY(upload(&M->d_slow, slow));
   }
   CELLO_CUDA(cudaMalloc((void**)&M->d_work, sizeof(unsigned)));
