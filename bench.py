@@ -34,6 +34,11 @@ WORKLOAD = dict(workload="blob-amr-large", root=[16, 16, 16], n=32, max_level=2,
                 exec="graph", l2="inputs larger than L2 (state tens of GB)")
 
 
+# FP32 lane operations per second of the whole GPU at the maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2.07 GHz (one operation per lane per clock)
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -74,7 +79,8 @@ def build_workload(cfg, precision, device="cuda", chunk=1024, log=print):
         leaves = mesh.leaves.astype(np.int64)
         for s in range(0, mesh.n_leaves, chunk):
             part = ics.blobs(leaves[s:s + chunk], root, n, 4, (0, 0, 0), hi, cfg["gamma"],
-                             count=cfg["blobs"], seed=cfg["seed"], device=device, chunk=256)
+                             count=cfg["blobs"], seed=cfg["seed"], device=device, chunk=256,
+                             abc=cfg.get("abc", 0.0))
             U[s:s + chunk] = part.to(U.dtype)
             del part
         return U
@@ -162,7 +168,8 @@ def oracle_sample(cfg, seconds=15.0):
     count = max(1, int(round(cfg["blobs"] * (r / cfg["root"][0]) ** 3)))
 
     def st(mesh):
-        return ics.blobs(mesh.leaves, od.root, od.n, 4, od.lo, od.hi, od.gamma, count=count, seed=cfg["seed"])
+        return ics.blobs(mesh.leaves, od.root, od.n, 4, od.lo, od.hi, od.gamma, count=count, seed=cfg["seed"],
+                         abc=cfg.get("abc", 0.0))
     mesh = OM.root_mesh(od)
     for _ in range(od.max_level):
         f = OH.refine_flags(OH.ghost_refresh(st(mesh), mesh), mesh, 0, cfg["tau"], cfg["tau"] / 4).numpy()
@@ -187,6 +194,165 @@ def oracle_sample(cfg, seconds=15.0):
     return cells * steps / el, torch.get_num_threads(), text
 
 
+# ------------------------------------------------------------ Sedov, deep
+SEDOV = dict(workload="sedov-deep", root=[4, 4, 4], n=16, max_level=5, E=1.0, rho0=1.0, p0=1e-5, gamma=1.4,
+             tau=0.3, cfl=0.4, t_end=0.05, adapt_every=4, bc="periodic")
+
+
+def sedov_run(cfg, precision, log=print, max_wall=300.0):
+    """The deep-AMR Sedov-Taylor blast toward t_end with pressure-slope
+    adaptation every few steps; stops at t_end or after max_wall seconds of
+    wall time (the hot, rarefied centre keeps the CFL step small), and
+    returns the measurements at the time reached.  Step time is timed with
+    CUDA events around each hydro step only; adaptation is timed apart."""
+    from paper_1810_01319_gb300 import Mesh, PERIODIC, make_desc
+    from paper_1810_01319_gb300.drivers import adapt
+    from workloads import ics
+    root, n, lmax = cfg["root"], cfg["n"], cfg["max_level"]
+    desc = make_desc(root, n, lmax, (0, 0, 0), (1, 1, 1), (PERIODIC,) * 3, precision, cfg["gamma"])
+
+    def sample(mesh):
+        return ics.sedov(mesh.leaves.astype(np.int64), root, n, 4, (0, 0, 0), (1, 1, 1), cfg["gamma"],
+                         E=cfg["E"], rho0=cfg["rho0"], p0=cfg["p0"], max_level=lmax,
+                         device="cuda").to(mesh.dtype).contiguous()
+    mesh = Mesh(desc)
+    U = sample(mesh)
+    for _ in range(lmax):                       # refine on the initial condition to a fixpoint
+        mesh.ghost_refresh(U)
+        f = np.where(mesh.refine_flags(U, 4, cfg["tau"]).cpu().numpy() > 0, 1, 0).astype(np.int8)
+        if not f.any():
+            break
+        mesh = Mesh(desc, mesh, f)
+        U = sample(mesh)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t, steps, step_ms, cell_updates, max_leaves = 0.0, 0, 0.0, 0, mesh.n_leaves
+    adapt_s = 0.0
+    wall = time.time()
+    while t < cfg["t_end"] - 1e-15 and time.time() - wall < max_wall:
+        if steps % cfg["adapt_every"] == 0:
+            ta = time.time()
+            mesh, U = adapt(mesh, U, 4, cfg["tau"])
+            torch.cuda.synchronize()
+            adapt_s += time.time() - ta
+            mesh.autotune(U) if steps == 0 else None
+            max_leaves = max(max_leaves, mesh.n_leaves)
+        mesh.reduce(U, cfg["cfl"], dt_next=dt)
+        d = float(dt)
+        if t + d > cfg["t_end"]:
+            d = cfg["t_end"] - t
+            dt.fill_(d)
+        ev0.record()
+        mesh.hydro_step(U, dt, steps, cfg["cfl"])
+        ev1.record()
+        ev1.synchronize()
+        step_ms += ev0.elapsed_time(ev1)
+        cell_updates += mesh.n_leaves * n ** 3
+        t += d
+        steps += 1
+        if steps % 200 == 0:
+            log(f"[sedov] step {steps} t={t:.3e} dt={d:.2e} leaves={mesh.n_leaves} "
+                f"step_ms={step_ms:.0f} adapt_s={adapt_s:.1f} wall={time.time() - wall:.0f}s")
+    wall = time.time() - wall
+    # shock radius: density-weighted mean radius of cells within 10 % of the peak density
+    x, y, z = ics.cell_centres(mesh.leaves.astype(np.int64), root, n, 4, (0, 0, 0), (1, 1, 1), device="cuda")
+    sl = (slice(None), slice(4, 4 + n), slice(4, 4 + n), slice(4, 4 + n))
+    rho = U[:, 0].double()[sl]
+    r = torch.sqrt((x[sl] - 0.5) ** 2 + (y[sl] - 0.5) ** 2 + (z[sl] - 0.5) ** 2)
+    m = rho > 0.9 * rho.max()
+    R = float((r[m] * rho[m]).sum() / rho[m].sum())
+    return {"steps": steps, "t": t, "reached_t_end": t >= cfg["t_end"] - 1e-15, "leaves_final": mesh.n_leaves,
+            "leaves_max": max_leaves, "cell_updates": cell_updates, "step_ms_total": step_ms,
+            "adapt_s_total": adapt_s, "wall_s": wall, "value": cell_updates / (step_ms / 1e3),
+            "shock_radius": R, "peak_density": float(rho.max())}
+
+
+# ------------------------------------------------------- end to end, host
+def host_bytes_available():
+    """Bytes this process may still allocate on the host: the smaller of
+    MemAvailable and the cgroup's limit minus its usage."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    for lim_f, use_f in (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                         ("/sys/fs/cgroup/memory/memory.limit_in_bytes", "/sys/fs/cgroup/memory/memory.usage_in_bytes")):
+        try:
+            lim = open(lim_f).read().strip()
+            use = int(open(use_f).read().strip())
+            if lim != "max" and int(lim) < (1 << 60):
+                room = int(lim) - use
+                avail = room if avail is None else min(avail, room)
+            break
+        except OSError:
+            continue
+    return avail or 0
+
+
+def e2e_host_buffers(mesh, U, cfg, dt, steps, stream, log):
+    from paper_1810_01319_gb300 import EXEC_GRAPH
+    state_bytes = U.numel() * U.element_size()
+    room = host_bytes_available()
+    workload = cfg["workload"]
+    m2 = None
+    if room < 2 * state_bytes + (32 << 30):
+        sub = dict(cfg, root=[8, 8, 8], blobs=max(1, cfg["blobs"] // 8))
+        m2, U2 = build_workload(sub, 4, log=lambda *a: None)
+        if room < 2 * U2.numel() * U2.element_size() + (16 << 30):
+            log(f"[bench] e2e skipped: {room / 2**30:.0f} GiB of host memory available")
+            return {"value": None, "unit": UNIT, "skipped": f"host memory ({room / 2**30:.0f} GiB available)"}
+        m2.autotune(U2)
+        m2.set_exec(EXEC_GRAPH)
+        mesh, U, workload = m2, U2, "blob-amr 8^3 roots of 32^3, 64 blobs, level 2"
+    cells = mesh.n_leaves * cfg["n"] ** 3
+    state_bytes = U.numel() * U.element_size()
+    # page-locked in place (the caching pinned allocator would round the
+    # size up to a power of two)
+    host = torch.empty(U.shape, dtype=U.dtype)
+    cudart = torch.cuda.cudart()
+    if int(cudart.cudaHostRegister(host.data_ptr(), state_bytes, 0)) != 0:
+        return {"value": None, "unit": UNIT, "skipped": "cudaHostRegister failed"}
+    host.copy_(U)
+    dt_h = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    out_h = torch.empty(6, dtype=torch.float64, pin_memory=True)
+    dt_next = torch.zeros(1, dtype=torch.float64, device="cuda")
+    totals = torch.zeros(5, dtype=torch.float64, device="cuda")
+    mesh.reduce(U, cfg["cfl"], dt_next=dt_next)
+    dt_host = float(dt_next.item())
+
+    def step(c):
+        nonlocal dt_host
+        dt_h[0] = dt_host
+        U.copy_(host, non_blocking=True)
+        dt.copy_(dt_h, non_blocking=True)
+        mesh.hydro_step(U, dt, c, cfg["cfl"], dt_next=dt_next, totals=totals)
+        host.copy_(U, non_blocking=True)
+        out_h[:1].copy_(dt_next, non_blocking=True)
+        out_h[1:].copy_(totals, non_blocking=True)
+        stream.synchronize()
+        dt_host = float(out_h[0])
+    for c in range(2):
+        step(c)
+    t0 = time.perf_counter()
+    for c in range(steps):
+        step(2 + c)
+    el = time.perf_counter() - t0
+    res = {"value": cells * steps / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes + 8,
+           "d2h_bytes_per_step": state_bytes + 48, "workload": workload, "leaves": mesh.n_leaves,
+           "timer": "host wall clock; state copied host->device and back every step, stream synchronised"}
+    torch.cuda.synchronize()
+    cudart.cudaHostUnregister(host.data_ptr())
+    del host
+    if m2 is not None:
+        del U, m2
+        torch.cuda.empty_cache()
+    return res
+
+
 # ------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -198,13 +364,33 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="blob-amr-large", choices=["blob-amr-large", "sedov-deep"])
+    ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
+    ap.add_argument("--abc", type=float, default=0.0,
+                    help="amplitude of an ABC flow added to every cell (0: blobs in a medium at rest)")
     args = ap.parse_args()
+
+    if args.workload == "sedov-deep":
+        from paper_1810_01319_gb300 import build
+        build.build()
+        cfg = dict(SEDOV)
+        res = sedov_run(cfg, 4, log=lambda *a: print(*a, file=sys.stderr, flush=True), max_wall=args.max_wall)
+        # similarity radius at the time reached, with the published energy constant for
+        # gamma = 1.4 in 3-D (Kamm & Timmes 2007: E = alpha rho R^5 / t^2, alpha = 0.851072)
+        R_exact = (cfg["E"] * res["t"] ** 2 / (0.851072 * cfg["rho0"])) ** 0.2
+        print(json.dumps({"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": 1, "dtype": "f32",
+                          "data": "synthetic", "config": cfg, "higher_is_better": True,
+                          "shock_radius": res["shock_radius"], "shock_radius_similarity": R_exact,
+                          "shock_radius_rel_err": res["shock_radius"] / R_exact - 1, **res}))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = dict(WORKLOAD)
     cfg["root"] = [args.root] * 3
+    if args.abc > 0.0:
+        cfg["abc"] = args.abc
 
     if args.impl == "reference":
         if rank != 0:
@@ -272,7 +458,16 @@ def main():
         torch.distributed.barrier()
     launches_per_step = 4 + 3 + (1 if mesh.n_coarse_fine else 0)
 
-    # per-phase times of one batched step (events between the library's launches)
+    # algorithmic operations of the step's sweeps, counted by the library on a
+    # sample of leaves (their slabs copied to the host, ghosts refreshed) and
+    # scaled to the launch; then per-phase times of one batched step on the
+    # same state and cycle (events between the library's launches)
+    sample_ids = np.unique(np.linspace(0, mesh.n_leaves - 1, 32).round().astype(np.int64))
+    mesh.ghost_refresh(U)
+    t_ops = time.time()
+    ops, pencils, swept_cells, _ = mesh.sweep_opcount(U, sample_ids, float(dt.item()), cycle)
+    log(f"[bench] operation count on {len(sample_ids)} leaves in {time.time() - t_ops:.1f}s")
+    scale = mesh.n_leaves / len(sample_ids)
     prof = mesh.profile_step(U, dt, cycle, cfg["cfl"])
     names = ["ghost_refresh", "sweep_1", "sweep_2", "sweep_3", "flux_correct", "reduce"]
     top = max(range(len(prof)), key=lambda i: prof[i])
@@ -286,43 +481,46 @@ def main():
     alg_bytes = {"ghost_refresh": ghost_cells * 2 * 5 * elem, "sweep_1": cells * 2 * 5 * elem,
                  "sweep_2": cells * 2 * 5 * elem, "sweep_3": cells * 2 * 5 * elem,
                  "flux_correct": 0, "reduce": cells * 5 * elem}
-    traffic_alg = alg_bytes[names[top]]
-    achieved = traffic_alg / (prof[top] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": names[top], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": src, "traffic": None,
-                "algorithmic_bytes_per_launch": traffic_alg, "phase_ms": dict(zip(names, prof))}
+    phase_names = ["primitives", "slopes_and_shock_detector", "interface_values", "flatten_and_trace",
+                   "riemann_flux", "update"]
+    sweeps = {}
+    for k in range(3):
+        ops_launch = float(ops[k].sum()) * scale
+        t = prof[1 + k] / 1e3
+        sweeps[f"sweep_{k + 1}"] = {
+            "ops_per_launch": ops_launch, "ops_per_updated_cell": float(ops[k].sum() / swept_cells[k]),
+            "ops_by_phase_per_updated_cell": {p: float(ops[k][i] / swept_cells[k]) for i, p in enumerate(phase_names)},
+            "achieved_tops": ops_launch / t / 1e12,
+            "hbm_gbs_algorithmic": alg_bytes[f"sweep_{k + 1}"] / t / 1e9}
+    kname = names[top]
+    if kname.startswith("sweep"):
+        sw = sweeps[kname]
+        roofline = {"bound": "alu", "kernel": kname, "achieved": sw["achieved_tops"], "peak": ALU_PEAK_TOPS,
+                    "unit": "T FP32 lane-op/s", "frac": sw["achieved_tops"] / ALU_PEAK_TOPS,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per lane per clock",
+                    "traffic": None, "algorithmic_ops_per_launch": sw["ops_per_launch"],
+                    "ops_sample": f"{len(sample_ids)} leaves evenly spaced in Morton order, scaled by "
+                                  f"{mesh.n_leaves}/{len(sample_ids)}",
+                    "hbm": {"achieved": sw["hbm_gbs_algorithmic"], "peak": hbm, "unit": "GB/s",
+                            "frac": sw["hbm_gbs_algorithmic"] / hbm, "peak_source": src,
+                            "algorithmic_bytes_per_launch": alg_bytes[kname]},
+                    "sweeps": sweeps, "phase_ms": dict(zip(names, prof))}
+    else:
+        achieved = alg_bytes[kname] / (prof[top] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "peak_source": src, "traffic": None,
+                    "algorithmic_bytes_per_launch": alg_bytes[kname], "sweeps": sweeps,
+                    "phase_ms": dict(zip(names, prof))}
 
-    # end to end through the public API: every step the host writes that
-    # step's dt into pinned memory, it is copied to the device, the step runs,
-    # and the step's result (dt_next and the five totals) is copied back to
-    # pinned host memory and read by the host before the next step.  The
-    # state itself stays resident in HBM across steps, as in a simulation.
+    # end to end through the public API with the state in host memory: every
+    # step copies the whole state from pinned host memory to the device, runs
+    # the step (dt in, dt_next and totals out), and copies the state and the
+    # step's result back to pinned host memory, read by the host before the
+    # next step.  At full size when the host has room for a pinned copy of
+    # the state (with a wide margin), else on the 8^3-root blob box.
     e2e = None
     if not args.no_e2e:
-        dt_h = torch.empty(1, dtype=torch.float64, pin_memory=True)
-        out_h = torch.empty(6, dtype=torch.float64, pin_memory=True)
-        dt_host = float(dt.item())
-
-        def e2e_step(c):
-            nonlocal dt_host
-            dt_h[0] = dt_host
-            dt.copy_(dt_h, non_blocking=True)
-            mesh.hydro_step(U, dt, c, cfg["cfl"], dt_next=dt_next, totals=totals)
-            out_h[:1].copy_(dt_next, non_blocking=True)
-            out_h[1:].copy_(totals, non_blocking=True)
-            stream.synchronize()
-            dt_host = float(out_h[0])
-        for _ in range(2):
-            e2e_step(cycle)
-            cycle += 1
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step(cycle)
-            cycle += 1
-        el = time.perf_counter() - t0
-        e2e = {"value": cells * args.steps * world / el, "unit": UNIT, "h2d_bytes_per_step": 8,
-               "d2h_bytes_per_step": 48, "timer": "host wall clock, stream synchronised every step",
-               "state_resident": True}
+        e2e = e2e_host_buffers(mesh, U, cfg, dt, args.steps, stream, log)
 
     # FP64 plain per-block path against FP32 batched on the 8^3-root blob box
     # (64 blobs, same blob density): the metric's comparison

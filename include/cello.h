@@ -39,7 +39,7 @@ typedef enum {
     CELLO_EINVAL = 1,     /* bad argument or unsupported size */
     CELLO_ENOMEM = 2,     /* device or host allocation failed */
     CELLO_ECUDA = 3,      /* a CUDA runtime call failed */
-    CELLO_ENONFINITE = 4, /* reserved: non-finite state detected */
+    CELLO_ENONFINITE = 4, /* cello_check: a bad state was seen */
     CELLO_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
     CELLO_EINTERNAL = 6   /* broken invariant (e.g. 2:1 balance) */
 } cello_status;
@@ -78,6 +78,21 @@ cello_status cello_octree_build(const cello_mesh_desc* desc, const cello_mesh* p
                                 const int8_t* flags_host, cello_mesh** out);
 
 void cello_mesh_free(cello_mesh* mesh);
+
+/* Rebuild a mesh from an explicit leaf list (host int32, count x (level, i,
+ * j, k), any order), e.g. from a checkpoint: the leaves must lie inside the
+ * root array, not repeat or overlap, and tile the domain, and the mesh must
+ * be 2:1 balanced; CELLO_EINVAL / CELLO_EINTERNAL otherwise.  The result is
+ * the same mesh (same Morton order, same table) as the one saved. */
+cello_status cello_mesh_from_leaves(const cello_mesh_desc* desc, const int32_t* leaves_host, int64_t count,
+                                   cello_mesh** out);
+
+/* Failure detection: every reduction (cello_reduce, or a step asked for dt
+ * or totals) sets bit 0 of the mesh's device error word when a leaf interior
+ * holds a non-finite value or a non-positive density or pressure (before
+ * the floors).  This call waits for the device, returns the word in *word
+ * (nullable), clears it, and returns CELLO_ENONFINITE if bit 0 was set. */
+cello_status cello_check(cello_mesh* mesh, uint32_t* word);
 
 /* Sizes: leaves, elements per leaf (5 * N^3), coarse-fine faces. */
 cello_status cello_mesh_info(const cello_mesh* mesh, int64_t* n_leaves, int64_t* leaf_elems,
@@ -143,10 +158,14 @@ cello_status cello_hydro_step(cello_mesh* mesh, void* U, const double* dt_dev, i
  * ghost entries are ignored) and receives the adjoint of the state U_n at
  * the start of the step (ghost entries zero).  U_n is read only; cycle and
  * dt_dev must be those of the forward step.  At a kink (min, max, branch)
- * the derivative of the branch taken in the forward pass is used.  Needs a
- * single-level, fully periodic mesh (no coarse-fine faces); the library
- * keeps three states of device scratch per mesh for the recomputed forward
- * sweeps. */
+ * the derivative of the branch taken in the forward pass is used.  Any
+ * mesh: on a single-level periodic mesh the ghost copy is transposed by a
+ * deterministic gather; otherwise the transposes of copy, restriction and
+ * limited prolongation scatter with atomic adds (summation order, hence the
+ * last bits, may vary between runs), and the coarse-fine flux correction is
+ * transposed into the face fluxes of the adjoint sweeps.  The library keeps
+ * three states of device scratch per mesh (plus the flux-register adjoints)
+ * for the recomputed forward sweeps. */
 cello_status cello_hydro_adjoint_step(cello_mesh* mesh, const void* U_n, void* lam_inout,
                                       const double* dt_dev, int cycle, void* stream);
 
@@ -164,7 +183,7 @@ cello_status cello_set_exec(cello_mesh* mesh, int mode);
 /* Launch variant of the PPM sweep kernel used by cello_hydro_step and the
  * adjoint: pencils per CTA, register bound (minimum resident CTAs per SM)
  * and schedule (one CTA per work item, or one resident wave pulling items
- * from a device counter).  Float32 has 10 variants, float64 2; every variant
+ * from a device counter).  Float32 has 12 variants, float64 2; every variant
  * computes the same values.  Cached graphs are dropped. */
 cello_status cello_set_sweep_variant(cello_mesh* mesh, int variant);
 
@@ -176,6 +195,22 @@ cello_status cello_set_sweep_variant(cello_mesh* mesh, int variant);
  * done; call it outside any stream capture. */
 cello_status cello_autotune(cello_mesh* mesh, void* U, int* variant_out, float* ms_out, int ms_len,
                             void* stream);
+
+/* Algorithmic operation count of the three PPM sweeps of one step (Sec.
+ * II.C), the numerator of the sweep kernel's ALU roofline.  Host only, no
+ * device work: the sweep's formulas run in float32 through a counting
+ * scalar (one operation per add, subtract, multiply, divide, square root,
+ * comparison, absolute value or copysign) over the pencils the sweep kernel
+ * covers, on `count` leaves whose slabs the caller copied (ghosts refreshed)
+ * into U_host (float32, [count][5][(n+2g)^3], overwritten with the swept
+ * state); leaf_ids are those leaves' indices in the mesh; dt and cycle as in
+ * cello_hydro_step.  out[24]: for the k-th sweep of the step, out[8k+0..5]
+ * are the operations of its six phases (primitives, slopes and shock
+ * detector, interface values, flattening and tracing, Riemann flux, update),
+ * out[8k+6] the pencils and out[8k+7] the cells updated.  Float32 meshes
+ * only; CELLO_EINVAL otherwise or on a bad leaf id. */
+cello_status cello_sweep_opcount(const cello_mesh* mesh, float* U_host, const int32_t* leaf_ids, int64_t count,
+                                 double dt, int cycle, double* out);
 
 /* One batched step (as cello_hydro_step, without dt_next/totals) with CUDA
  * events recorded between its phases; blocks until it completes and writes

@@ -44,17 +44,22 @@ def _stream(stream):
 class Mesh:
     """A leaf table built by cello_octree_build; owns the C handle."""
 
-    def __init__(self, desc: _lib.MeshDesc, prev: "Mesh | None" = None, flags=None):
+    def __init__(self, desc: _lib.MeshDesc, prev: "Mesh | None" = None, flags=None, leaves=None):
         L = _lib.lib()
         self.desc = desc
         out = ctypes.c_void_p()
-        fl = None
-        if flags is not None:
-            fl = np.ascontiguousarray(np.asarray(flags, dtype=np.int8))
-            assert prev is not None and len(fl) == prev.n_leaves
-        _lib.check(L.cello_octree_build(ctypes.byref(desc), prev.handle if prev else None,
-                                        fl.ctypes.data_as(ctypes.c_void_p) if fl is not None else None,
-                                        ctypes.byref(out)), "cello_octree_build")
+        if leaves is not None:
+            lv = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 4))
+            _lib.check(L.cello_mesh_from_leaves(ctypes.byref(desc), lv.ctypes.data_as(ctypes.c_void_p), len(lv),
+                                                ctypes.byref(out)), "cello_mesh_from_leaves")
+        else:
+            fl = None
+            if flags is not None:
+                fl = np.ascontiguousarray(np.asarray(flags, dtype=np.int8))
+                assert prev is not None and len(fl) == prev.n_leaves
+            _lib.check(L.cello_octree_build(ctypes.byref(desc), prev.handle if prev else None,
+                                            fl.ctypes.data_as(ctypes.c_void_p) if fl is not None else None,
+                                            ctypes.byref(out)), "cello_octree_build")
         self.handle = out
         nl, le, ncf = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _lib.check(L.cello_mesh_info(out, ctypes.byref(nl), ctypes.byref(le), ctypes.byref(ncf)), "cello_mesh_info")
@@ -152,6 +157,28 @@ class Mesh:
                                                  ctypes.cast(out, ctypes.c_void_p), _stream(stream)),
                    "cello_profile_step")
         return list(out)
+
+    def sweep_opcount(self, U, leaf_ids, dt: float, cycle: int = 0):
+        """Counted operations of the step's three sweeps on the given leaves
+        (their slabs are copied to the host; the ghosts must be refreshed).
+        Returns (ops [3, 6] per sweep and phase, pencils [3], cells [3], swept
+        host copy [count, 5, N, N, N])."""
+        ids = np.ascontiguousarray(np.asarray(leaf_ids, dtype=np.int32))
+        host = U[torch.as_tensor(ids, dtype=torch.int64, device=U.device)].detach().to("cpu").contiguous()
+        out = np.zeros(24, dtype=np.float64)
+        _lib.check(_lib.lib().cello_sweep_opcount(self.handle, ctypes.c_void_p(host.data_ptr()),
+                                                  ids.ctypes.data_as(ctypes.c_void_p), len(ids), float(dt),
+                                                  int(cycle), out.ctypes.data_as(ctypes.c_void_p)),
+                   "cello_sweep_opcount")
+        o = out.reshape(3, 8)
+        return o[:, :6].copy(), o[:, 6].copy(), o[:, 7].copy(), host
+
+    def check(self) -> int:
+        """Read and clear the device error word (waits for the device); raises
+        CelloError with CELLO_ENONFINITE if a reduction saw a bad state."""
+        w = ctypes.c_uint32()
+        _lib.check(_lib.lib().cello_check(self.handle, ctypes.byref(w)), "cello_check")
+        return w.value
 
     def set_sweep_variant(self, variant: int):
         _lib.check(_lib.lib().cello_set_sweep_variant(self.handle, int(variant)), "cello_set_sweep_variant")

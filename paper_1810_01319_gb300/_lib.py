@@ -34,6 +34,9 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "cello_octree_build": (ctypes.c_int, [ctypes.POINTER(MeshDesc), _vp, _vp, ctypes.POINTER(_vp)]),
     "cello_mesh_free": (None, [_vp]),
+    "cello_mesh_from_leaves": (ctypes.c_int, [ctypes.POINTER(MeshDesc), _vp, ctypes.c_int64, ctypes.POINTER(_vp)]),
+    "cello_check": (ctypes.c_int, [_vp, _vp]),
+    "cello_sweep_opcount": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, _vp]),
     "cello_mesh_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p]),
     "cello_mesh_leaves": (ctypes.c_int, [_vp, _vp]),
     "cello_neighbour_table": (ctypes.c_int, [_vp, _vp, _vp, _vp]),

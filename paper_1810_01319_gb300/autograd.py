@@ -8,7 +8,8 @@ import torch
 
 
 class HydroRollout(torch.autograd.Function):
-    """U_final = step_{n-1} o ... o step_0 (U0) on a single-level periodic mesh."""
+    """U_final = step_{n-1} o ... o step_0 (U0) on a fixed mesh (any levels and
+    boundaries; the mesh is not adapted inside the rollout)."""
 
     @staticmethod
     def forward(ctx, U0, mesh, dts, cycle0, every):

@@ -29,6 +29,7 @@ UNITS = {
     "table.cu": [],
     "mesh.cu": [],
     "noalloc.cu": [],
+    "opcount.cu": [],
 }
 
 

@@ -44,6 +44,7 @@ struct DevMesh {
   const int* idx;         // [B][27]
   const int* fine8;       // [B][27][8]
   const int* face_slot;   // [B][6] flux-register slot of each face or -1
+  unsigned* err;          // error word: bit 0 set by the reduction on a non-finite or non-positive state
 };
 
 // Face order used by registers and corrections: -x, +x, -y, +y, -z, +z.
@@ -93,6 +94,7 @@ struct SweepParams {
 struct AdjSweepParams {
   const void* U;           // state entering the forward sweep (ghosts refreshed)
   void* lam;               // adjoint, updated in place
+  const double* regb;      // adjoints of the face fluxes kept for flux correction (may be null)
   int leaf0, nleaf;
   int axis;
   int a0, a1, b0, b1;
@@ -144,9 +146,18 @@ void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, d
 void launch_adjoint_sweep_f32(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStream_t s);
+// AMR form: scatter each ghost cell's adjoint onto its sources (copies,
+// restrictions, limited prolongations evaluated at the refreshed state U),
+// then clear the ghost adjoints.
+void launch_adjoint_refresh_scatter(const DevMesh& m, const void* U, void* lam, int precision, cudaStream_t s);
+void launch_fluxcorr_adjoint(const DevMesh& m, const void* lam, int precision, const CoarseFace* faces, int nfaces,
+                             double* regb, const double* dt, cudaStream_t s);
 void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s);
 void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);
+// Host: counted operations of one leaf's sweep (opcount.cu), update applied.
+void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
+                  unsigned long long counts[6]);
 
 }  // namespace cello

@@ -6,10 +6,10 @@ namespace cello {
 
 // Float32 sweep variants: {pencils per CTA, min resident CTAs per SM, persistent}.
 static const SweepVariant kVariants[] = {
-    {8, 3, false}, {8, 4, false}, {4, 6, false}, {16, 1, false}, {4, 8, false},
-    {8, 3, true},  {8, 4, true},  {4, 6, true},  {16, 1, true},  {4, 8, true},
+    {8, 3, false}, {8, 4, false}, {4, 6, false}, {16, 1, false}, {4, 8, false}, {16, 2, false},
+    {8, 3, true},  {8, 4, true},  {4, 6, true},  {16, 1, true},  {4, 8, true},  {16, 2, true},
 };
-constexpr int kNT = 5;   // distinct kernel instantiations; variant v uses template v % kNT
+constexpr int kNT = 6;   // distinct kernel instantiations; variant v uses template v % kNT
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
 static int g_resident[3][kNV];   // resident CTAs per GPU by [n index][variant], from the occupancy API
 
@@ -56,6 +56,7 @@ static void prepare_nb(int sms) {
   prepare_variant<NB, 4, 6>(2, sms);
   prepare_variant<NB, 16, 1>(3, sms);
   prepare_variant<NB, 4, 8>(4, sms);
+  prepare_variant<NB, 16, 2>(5, sms);
   for (int v = kNT; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - kNT];
 }
 
@@ -68,6 +69,7 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
     case 2: launch_variant<NB, 4, 6>(m, p, pencils, v, s); break;
     case 3: launch_variant<NB, 16, 1>(m, p, pencils, v, s); break;
     case 4: launch_variant<NB, 4, 8>(m, p, pencils, v, s); break;
+    case 5: launch_variant<NB, 16, 2>(m, p, pencils, v, s); break;
   }
 }
 

@@ -190,6 +190,44 @@ void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStre
 #undef CELLO_AR
 }
 
+template <typename T, int NB>
+static void adj_scatter_n(const DevMesh& m, const T* U, T* lam, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  const long ng = (long)m.B * ((long)N * N * N - (long)NB * NB * NB);
+  adjoint_refresh_scatter_kernel<T, NB><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(m, U, lam);
+  zero_ghosts_kernel<T, NB><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(lam, m.B);
+}
+
+void launch_adjoint_refresh_scatter(const DevMesh& m, const void* U, void* lam, int precision, cudaStream_t s) {
+  if (m.B <= 0) return;
+#define CELLO_AS(T)                                                                                        \
+  switch (m.n) {                                                                                           \
+    case 8: adj_scatter_n<T, 8>(m, static_cast<const T*>(U), static_cast<T*>(lam), s); break;             \
+    case 16: adj_scatter_n<T, 16>(m, static_cast<const T*>(U), static_cast<T*>(lam), s); break;           \
+    case 32: adj_scatter_n<T, 32>(m, static_cast<const T*>(U), static_cast<T*>(lam), s); break;           \
+  }
+  if (precision == 4) { CELLO_AS(float) } else { CELLO_AS(double) }
+#undef CELLO_AS
+}
+
+void launch_fluxcorr_adjoint(const DevMesh& m, const void* lam, int precision, const CoarseFace* faces, int nfaces,
+                             double* regb, const double* dt, cudaStream_t s) {
+  if (nfaces <= 0) return;
+  const long threads = (long)nfaces * m.n * m.n;
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+#define CELLO_FA(T, NB) \
+  fluxcorr_adjoint_kernel<T, NB><<<grid, 256, 0, s>>>(m, static_cast<const T*>(lam), faces, nfaces, regb, dt)
+#define CELLO_FA_T(T)                       \
+  switch (m.n) {                            \
+    case 8: CELLO_FA(T, 8); break;          \
+    case 16: CELLO_FA(T, 16); break;        \
+    case 32: CELLO_FA(T, 32); break;        \
+  }
+  if (precision == 4) { CELLO_FA_T(float) } else { CELLO_FA_T(double) }
+#undef CELLO_FA_T
+#undef CELLO_FA
+}
+
 void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s) {
   if (m.B <= 0) return;
 #define CELLO_ZG(T)                                           \

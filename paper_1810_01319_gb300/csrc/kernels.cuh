@@ -93,8 +93,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     __syncthreads();
 
     const int j = cj, p = cp;
-    // ---- phase 2
-    if (j >= 1 && j <= N - 2) {
+    // ---- phase 2 (slopes of cells 2..N-3: the interfaces used below are 2..N-4)
+    if (j >= 2 && j <= N - 3) {
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
         const T* a = sW + k * A + p;
@@ -108,8 +108,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
                                      un[(j - 1) * S], un[(j + 1) * S]);
     }
     __syncthreads();
-    // ---- phase 3
-    if (j >= 1 && j <= N - 3) {
+    // ---- phase 3 (interfaces j+1/2 read by cells 3..N-4)
+    if (j >= 2 && j <= N - 4) {
 #pragma unroll
       for (int k = 0; k < 5; ++k)
         sB[k * A + j * S + p] = interface_value(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
@@ -614,6 +614,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh
   const T gamma = T(m.gamma), gm1 = T(m.gamma - 1.0);
   const T* b = U + (long)leaf * 5 * SLAB;
   double v[6] = {INFINITY, 0, 0, 0, 0, 0};
+  int bad = 0;
   for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
     const int x = i % NB + G, y = (i / NB) % NB + G, z = i / (NB * NB) + G;
     const long o = ((long)z * N + y) * N + x;
@@ -621,18 +622,22 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh
     const T rho = vmax(r0, T(kRhoFloor));
     const T u = m1 / rho, vv = m2 / rho, w = m3 / rho;
     const T ke = (T(0.5) * rho) * (u * u + (vv * vv + w * w));
-    const T p = vmax(gm1 * (E - ke), T(kPFloor));
+    const T praw = gm1 * (E - ke);
+    bad |= !(r0 > T(0)) || !(praw > T(0)) || !isfinite(praw + (m1 + m2 + m3));
+    const T p = vmax(praw, T(kPFloor));
     const T c = vsqrt((gamma * p) / rho);
     const T s = vmax(vabs(u), vmax(vabs(vv), vabs(w))) + c;
     v[0] = fmin(v[0], double(dx / s));
     v[1] += double(r0); v[2] += double(m1); v[3] += double(m2); v[4] += double(m3); v[5] += double(E);
   }
+  bad = __syncthreads_or(bad);
   block_reduce6(v, sh);
   if (threadIdx.x == 0) {
     const double dxd = ldexp(m.dx0, -lf.x);
     const double vol = dxd * dxd * dxd;
     partials[leaf * 6 + 0] = v[0];
     for (int k = 1; k < 6; ++k) partials[leaf * 6 + k] = v[k] * vol;
+    if (bad && m.err) atomicOr(m.err, 1u);
   }
 }
 
@@ -660,6 +665,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
   const float gamma = float(m.gamma), gm1 = float(m.gamma - 1.0);
   const float* b = U + (long)leaf * 5 * SLAB;
   float mn = INFINITY, hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
+  int bad = 0;
   for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
     const int x = i % NB + G, y = (i / NB) % NB + G, z = i / (NB * NB) + G;
     const long o = ((long)z * N + y) * N + x;
@@ -667,7 +673,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
     const float rho = vmax(r0, float(kRhoFloor));
     const float u = m1 / rho, vv = m2 / rho, w = m3 / rho;
     const float ke = (0.5f * rho) * (u * u + (vv * vv + w * w));
-    const float p = vmax(gm1 * (E - ke), float(kPFloor));
+    const float praw = gm1 * (E - ke);
+    bad |= !(r0 > 0.0f) || !(praw > 0.0f) || !isfinite(praw + (m1 + m2 + m3));
+    const float p = vmax(praw, float(kPFloor));
     const float c = sqrtf((gamma * p) / rho);
     const float s = vmax(fabsf(u), vmax(fabsf(vv), fabsf(w))) + c;
     mn = fminf(mn, dx / s);
@@ -681,12 +689,14 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
   v[0] = double(mn);
 #pragma unroll
   for (int k = 0; k < 5; ++k) v[k + 1] = double(hi[k]) + double(lo[k]);
+  bad = __syncthreads_or(bad);
   block_reduce6(v, sh);
   if (threadIdx.x == 0) {
     const double dxd = ldexp(m.dx0, -lf.x);
     const double vol = dxd * dxd * dxd;
     partials[leaf * 6 + 0] = v[0];
     for (int k = 1; k < 6; ++k) partials[leaf * 6 + k] = v[k] * vol;
+    if (bad && m.err) atomicOr(m.err, 1u);
   }
 }
 

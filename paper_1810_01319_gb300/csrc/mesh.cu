@@ -153,6 +153,7 @@ struct cello_mesh {
   int exec_mode = CELLO_EXEC_BATCHED;
   int sweep_variant = 0;           // chosen by cello_autotune or cello_set_sweep_variant
   unsigned* d_work = nullptr;      // work counter of the persistent sweep variants
+  unsigned* d_err = nullptr;       // error word set by the reduction
   double* d_zero = nullptr;        // dt = 0, for timing sweeps without changing the state
   void* adj_scratch = nullptr;   // three states for the adjoint's forward recomputation
   size_t adj_bytes = 0;
@@ -177,6 +178,7 @@ struct cello_mesh {
     m.idx = d_idx;
     m.fine8 = d_fine8;
     m.face_slot = d_face_slot;
+    m.err = d_err;
     return m;
   }
 
@@ -189,6 +191,8 @@ struct cello_mesh {
     adj_scratch = nullptr;
     if (d_work) cudaFree(d_work);
     if (d_zero) cudaFree(d_zero);
+    if (d_err) cudaFree(d_err);
+    d_err = nullptr;
     d_work = nullptr;
     d_zero = nullptr;
     if (d_slow) cudaFree(d_slow);
@@ -434,6 +438,8 @@ cello_status finish_build(cello_mesh* M) {
     CELLO_TRY(upload(&M->d_slow, slow));
   }
   CELLO_CUDA(cudaMalloc((void**)&M->d_work, sizeof(unsigned)));
+  CELLO_CUDA(cudaMalloc((void**)&M->d_err, sizeof(unsigned)));
+  CELLO_CUDA(cudaMemset(M->d_err, 0, sizeof(unsigned)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_zero, sizeof(double)));
   CELLO_CUDA(cudaMemset(M->d_zero, 0, sizeof(double)));
   CELLO_CUDA(cudaDeviceSynchronize());
@@ -511,17 +517,17 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
 
 cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double* dt, int cycle, cudaStream_t s) {
   const cello_mesh_desc& d = M->desc;
-  for (int a = 0; a < 3; ++a)
-    if (d.bc[a] != CELLO_PERIODIC) return fail(CELLO_EINVAL, "the adjoint step needs periodic boundaries");
-  for (int b = 1; b < M->B; ++b)
-    if (M->leaves[b].x != M->leaves[0].x) return fail(CELLO_EINVAL, "the adjoint step needs a single-level mesh");
+  bool uniform_periodic = true;   // then the ghost copy's transpose is a deterministic gather
+  for (int a = 0; a < 3; ++a) uniform_periodic = uniform_periodic && d.bc[a] == CELLO_PERIODIC;
+  for (int b = 1; b < M->B && uniform_periodic; ++b) uniform_periodic = M->leaves[b].x == M->leaves[0].x;
   const size_t state = (size_t)M->B * 5 * M->N * M->N * M->N * d.precision;
-  if (M->adj_bytes < 3 * state) {
+  const size_t regs = (size_t)M->nslots * 5 * d.n * d.n * sizeof(double);
+  if (M->adj_bytes < 3 * state + regs) {
     if (M->adj_scratch) cudaFree(M->adj_scratch);
     M->adj_scratch = nullptr;
     M->adj_bytes = 0;
-    CELLO_CUDA(cudaMalloc(&M->adj_scratch, 3 * state));
-    M->adj_bytes = 3 * state;
+    CELLO_CUDA(cudaMalloc(&M->adj_scratch, 3 * state + regs));
+    M->adj_bytes = 3 * state + regs;
   }
   char* S0 = static_cast<char*>(M->adj_scratch);
   char* S1 = S0 + state;
@@ -557,12 +563,19 @@ cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double
     }
     swept[axis] = true;
   }
-  // reverse: the adjoint of U_{n+1} lives on interior cells only
+  // reverse: the adjoint of U_{n+1} lives on interior cells only; the
+  // coarse-fine flux correction's adjoint gives the face-flux adjoints
   launch_zero_ghosts(dm, lam, d.precision, s);
+  double* regb = nullptr;
+  if (!M->cfaces.empty()) {
+    regb = reinterpret_cast<double*>(S2 + state);
+    launch_fluxcorr_adjoint(dm, lam, d.precision, M->d_cfaces, (int)M->cfaces.size(), regb, dt, s);
+  }
   for (int oi = 2; oi >= 0; --oi) {
     AdjSweepParams p{};
     p.U = entry[oi];
     p.lam = lam;
+    p.regb = regb;
     p.axis = order[oi];
     p.a0 = rng[oi][0]; p.a1 = rng[oi][1]; p.b0 = rng[oi][2]; p.b1 = rng[oi][3];
     const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
@@ -574,7 +587,8 @@ cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double
     if (d.precision == 4) launch_adjoint_sweep_f32(dm, p, s);
     else launch_adjoint_sweep_f64(dm, p, s);
   }
-  launch_adjoint_refresh(dm, lam, d.precision, s);
+  if (uniform_periodic) launch_adjoint_refresh(dm, lam, d.precision, s);
+  else launch_adjoint_refresh_scatter(dm, S0, lam, d.precision, s);
   CELLO_CUDA(cudaGetLastError());
   return CELLO_OK;
 }
@@ -620,6 +634,65 @@ cello_status cello_octree_build(const cello_mesh_desc* desc, const cello_mesh* p
     return st;
   }
   *out = M;
+  return CELLO_OK;
+}
+
+cello_status cello_mesh_from_leaves(const cello_mesh_desc* desc, const int32_t* leaves_host, int64_t count,
+                                   cello_mesh** out) {
+  if (!out || !leaves_host || count <= 0) return fail(CELLO_EINVAL, "NULL argument or empty leaf list");
+  *out = nullptr;
+  CELLO_TRY(check_desc(desc));
+  std::vector<Node> ls((size_t)count);
+  std::unordered_set<unsigned long long> seen;
+  double volume = 0.0;
+  for (int64_t b = 0; b < count; ++b) {
+    const Node t{leaves_host[4 * b], leaves_host[4 * b + 1], leaves_host[4 * b + 2], leaves_host[4 * b + 3]};
+    if (t.L < 0 || t.L > desc->max_level) return fail(CELLO_EINVAL, "leaf level out of range");
+    const int p[3] = {t.i, t.j, t.k};
+    for (int a = 0; a < 3; ++a)
+      if (p[a] < 0 || p[a] >= (desc->root[a] << t.L)) return fail(CELLO_EINVAL, "leaf index out of range");
+    if (!seen.insert(pack(t)).second) return fail(CELLO_EINVAL, "duplicate leaf");
+    ls[(size_t)b] = t;
+    volume += std::ldexp(1.0, -3 * t.L);
+  }
+  for (const Node& t : ls) {   // no leaf may contain another
+    Node q = t;
+    while (q.L > 0) {
+      q = Node{q.L - 1, q.i >> 1, q.j >> 1, q.k >> 1};
+      if (seen.count(pack(q))) return fail(CELLO_EINVAL, "leaves overlap");
+    }
+  }
+  if (volume != (double)desc->root[0] * desc->root[1] * desc->root[2])
+    return fail(CELLO_EINVAL, "leaves do not tile the domain");
+  prepare_kernels();
+  auto* M = new (std::nothrow) cello_mesh();
+  if (!M) return fail(CELLO_ENOMEM, "host allocation failed");
+  M->desc = *desc;
+  M->N = desc->n + 2 * desc->ghosts;
+  std::vector<std::pair<unsigned long long, Node>> keyed;
+  for (const Node& t : ls) keyed.emplace_back(leaf_key(*desc, t), t);
+  std::sort(keyed.begin(), keyed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  M->B = (int)keyed.size();
+  for (const auto& kv : keyed) {
+    M->keys.push_back(kv.first);
+    M->leaves.push_back(make_int4(kv.second.L, kv.second.i, kv.second.j, kv.second.k));
+  }
+  cello_status st = finish_build(M);
+  if (st != CELLO_OK) {
+    delete M;
+    return st;
+  }
+  *out = M;
+  return CELLO_OK;
+}
+
+cello_status cello_check(cello_mesh* M, uint32_t* word) {
+  if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
+  unsigned w = 0;
+  CELLO_CUDA(cudaMemcpy(&w, M->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CELLO_CUDA(cudaMemset(M->d_err, 0, sizeof(unsigned)));
+  if (word) *word = w;
+  if (w & 1u) return fail(CELLO_ENONFINITE, "a reduction saw a non-finite value or a non-positive density or pressure");
   return CELLO_OK;
 }
 
@@ -838,6 +911,35 @@ cello_status cello_autotune(cello_mesh* M, void* U, int* variant_out, float* ms_
   CELLO_CUDA(cudaGetLastError());
   if (variant_out) *variant_out = best;
   return cello_set_sweep_variant(M, best);
+}
+
+cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32_t* leaf_ids, int64_t count,
+                                 double dt, int cycle, double* out) {
+  if (!M || !U_host || !leaf_ids || !out || count <= 0) return fail(CELLO_EINVAL, "NULL argument or empty sample");
+  if (M->desc.precision != 4) return fail(CELLO_EINVAL, "operation counts are taken on float32 meshes");
+  for (int64_t i = 0; i < count; ++i)
+    if (leaf_ids[i] < 0 || leaf_ids[i] >= M->B) return fail(CELLO_EINVAL, "leaf id out of range");
+  const cello_mesh_desc& d = M->desc;
+  const long slab = 5L * M->N * M->N * M->N;
+  const double dx0 = (d.hi[0] - d.lo[0]) / (d.root[0] * d.n);
+  for (int k = 0; k < 3 * 8; ++k) out[k] = 0.0;
+  const int order[3] = {cycle % 2 == 0 ? 0 : 2, 1, cycle % 2 == 0 ? 2 : 0};
+  bool swept[3] = {false, false, false};
+  for (int oi = 0; oi < 3; ++oi) {
+    const int axis = order[oi];
+    int a0, a1, b0, b1;
+    sweep_ranges(M, axis, swept, a0, a1, b0, b1);
+    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = 0; i < count; ++i) {
+      const double dtdx = dt / std::ldexp(dx0, -M->leaves[leaf_ids[i]].x);
+      opcount_leaf(U_host + i * slab, d.n, d.ghosts, axis, a0, a1, b0, b1, dtdx, d.gamma, c);
+    }
+    for (int k = 0; k < 6; ++k) out[oi * 8 + k] = (double)c[k];
+    out[oi * 8 + 6] = (double)count * (a1 - a0) * (b1 - b0);
+    out[oi * 8 + 7] = out[oi * 8 + 6] * d.n;
+    swept[axis] = true;
+  }
+  return CELLO_OK;
 }
 
 cello_status cello_profile_step(cello_mesh* M, void* U, const double* dt, int cycle, double cfl, float* phase_ms,

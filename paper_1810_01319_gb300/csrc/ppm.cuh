@@ -20,7 +20,7 @@ constexpr double kPFloor = 1e-20;
 constexpr double kEpsShock = 0.33;   // shock detector: relative pressure jump
 constexpr double kOmega1 = 0.75;     // flattening ratio offset
 constexpr double kOmega2 = 10.0;     // flattening ratio slope
-constexpr int kRiemannIters = 5;     // fixed Newton steps, no early exit
+constexpr int kRiemannIters = 5;     // Newton steps (a lane stops early only at an exact fixed point)
 
 template <typename T> CELLO_HD T vmax(T a, T b) { return a > b ? a : b; }
 template <typename T> CELLO_HD T vmin(T a, T b) { return a < b ? a : b; }
@@ -164,7 +164,8 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
 }
 
 // Two-shock approximate Riemann solver (Colella & Woodward 1984): fixed
-// Newton steps on p* along shock curves on both sides, u* the Z-weighted
+// Newton steps on p* along shock curves on both sides (a lane whose p* stops
+// changing leaves the loop early, which gives bit-identical results), u* the Z-weighted
 // mean, sampled at x/t = 0 (u* >= 0 takes the left side), linear in a
 // rarefaction fan between head and tail.  Fluxes (rho, m_n, m_t1, m_t2, E).
 template <typename T>
@@ -185,7 +186,9 @@ CELLO_HD void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5])
     ZL = ((T(2) * WLs) * WLs) * WLs / (WLs * WLs + CL * CL);
     ZR = ((T(2) * WRs) * WRs) * WRs / (WRs * WRs + CR * CR);
     if (it == kRiemannIters) break;
-    ps = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), T(kPFloor));
+    const T pn = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), T(kPFloor));
+    if (pn == ps) break;   // fixed point: every remaining step would repeat this one exactly
+    ps = pn;
   }
   const T us = (ZL * uLs + ZR * uRs) / (ZL + ZR);
 
@@ -262,7 +265,9 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
     ZL = (2.0f * WLs) * xL / (xL + 1.0f);
     ZR = (2.0f * WRs) * xR / (xR + 1.0f);
     if (it == kRiemannIters) break;
-    ps = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), float(kPFloor));
+    const float pn = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), float(kPFloor));
+    if (pn == ps) break;   // fixed point (see riemann_flux)
+    ps = pn;
   }
   const float us = (ZL * uLs + ZR * uRs) / (ZL + ZR);
   const bool left = us >= 0.0f;

@@ -136,3 +136,41 @@ def test_float32_adjoint_close_to_float64():
         out[prec] = lam.double().cpu()
     err = float((out[4] - out[8]).abs().max() / out[8].abs().max())
     assert err < 1e-3, err
+
+
+@pytest.mark.parametrize("bc,steps", [((OM.PERIODIC,) * 3, 2), ((OM.OUTFLOW, OM.PERIODIC, OM.OUTFLOW), 2)])
+def test_amr_adjoint_matches_oracle_autograd(bc, steps):
+    """AMR adjoint (restriction, limited prolongation, coarse-fine flux
+    correction, outflow clamps transposed) against torch autograd through the
+    oracle on a 2^3-root, level-2 blob mesh."""
+    od = H.oracle_desc(root=(2, 2, 2), n=8, lmax=2, bc=bc)
+    om, flags = H.ic_refined(od, "blobs", count=16, seed=2)
+    assert om.leaves[:, 0].max() == 2 and len(OH.coarse_fine_faces(om)) > 0
+    U0 = _moving_state(od, om, 4)
+    _, dts = OH.run(U0, om, steps, 0.4)
+    n, g4 = od.n, od.ghosts
+    w = torch.randn(U0.shape, generator=torch.Generator().manual_seed(8), dtype=torch.float64)
+    wi = torch.zeros_like(w)
+    wi[:, :, g4:g4 + n, g4:g4 + n, g4:g4 + n] = w[:, :, g4:g4 + n, g4:g4 + n, g4:g4 + n]
+    Ut = U0.clone().requires_grad_(True)
+    plan = OH.RefreshPlan(om)
+    cf = OH.coarse_fine_faces(om)
+    V = Ut
+    for s, dt in enumerate(dts):
+        V = OH.step(V, om, dt, s, plan, cf=cf)
+    (go,) = torch.autograd.grad((V * wi).sum(), Ut)
+    gm = H.gpu_mesh_from_flags(od, flags, 8)
+    U = U0.cuda().contiguous()
+    states = []
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for s, v in enumerate(dts):
+        states.append(U.clone())
+        dt.fill_(v)
+        gm.hydro_step(U, dt, s)
+    lam = wi.cuda().contiguous()
+    for s in range(steps - 1, -1, -1):
+        dt.fill_(dts[s])
+        gm.hydro_adjoint_step(states[s], lam, dt, s)
+    torch.cuda.synchronize()
+    err = float((lam.cpu() - go).abs().max() / go.abs().max())
+    assert err < 1e-10, err

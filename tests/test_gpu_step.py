@@ -138,7 +138,7 @@ def test_sweep_variants_identical_and_autotune(blob_amr, precision):
     state unchanged and picks one of them."""
     od, om, flags, U0, Uo, dts = blob_amr
     gm = H.gpu_mesh_from_flags(od, flags, precision)
-    nv = 10 if precision == 4 else 2
+    nv = 12 if precision == 4 else 2
     outs = []
     for v in range(nv):
         gm.set_sweep_variant(v)
@@ -151,3 +151,28 @@ def test_sweep_variants_identical_and_autotune(blob_amr, precision):
     best, ms = gm.autotune(U)
     assert torch.equal(U, before)
     assert 0 <= best < nv and len(ms) == nv and min(ms) > 0
+
+
+def test_sweep_opcount_mirrors_the_kernel():
+    """The host operation count runs the sweep's formulas over the kernel's
+    pencil ranges: its swept copy of the leaves matches a GPU step (no
+    coarse-fine faces) to float32 tolerance, and its pencil counts are those
+    of the three launches."""
+    od = H.oracle_desc(root=(2, 2, 2), n=16, lmax=0)
+    om = OM.root_mesh(od)
+    gm = H.gpu_mesh_from_flags(od, [], 4)
+    U0 = H.state(od, om.leaves, "blobs", count=12, seed=3).to(torch.float32).cuda().contiguous()
+    gm.ghost_refresh(U0)
+    dt = 2e-3
+    for cycle in (0, 1):
+        ops, pencils, cells, host = gm.sweep_opcount(U0, np.arange(gm.n_leaves), dt, cycle)
+        U = U0.clone()
+        gm.hydro_step(U, torch.full((1,), dt, dtype=torch.float64, device="cuda"), cycle)
+        errs = H.l1_rel_per_field(H.interior(host, 16), H.interior(U.cpu(), 16))
+        assert max(errs) < 2e-5, errs
+        N, n, B = 24, 16, gm.n_leaves
+        assert list(pencils) == [B * N * N, B * N * n, B * n * n]
+        assert list(cells) == [p * n for p in pencils]
+        per_cell = ops.sum(1) / cells
+        assert np.all(per_cell > 300) and np.all(per_cell < 3000), per_cell
+        assert np.all(ops > 0)

@@ -71,10 +71,13 @@ def blob_params(count, seed):
 
 
 def blobs(leaves, root, n, ghosts, lo, hi, gamma, count=64, seed=0, contrast=10.0, p0=1.0,
-          device="cpu", chunk=64):
+          device="cpu", chunk=64, abc=0.0):
     """Blob field in a periodic unit box: ambient rho=1 at rest; inside a blob
     (periodic minimum-image distance below its radius) rho=contrast and the
-    blob's velocity; overlaps go to the lowest blob index; p = p0."""
+    blob's velocity; overlaps go to the lowest blob index; p = p0.  With
+    abc > 0 an Arnold-Beltrami-Childress flow of amplitude abc (A = B = C,
+    wavenumber 2 pi) is added to every cell's velocity, so that no region is
+    at rest."""
     centres, radii, vel = blob_params(count, seed)
     leaves_np = np.asarray(leaves, dtype=np.int64)
     B = leaves_np.shape[0]
@@ -117,7 +120,14 @@ def blobs(leaves, root, n, ghosts, lo, hi, gamma, count=64, seed=0, contrast=10.
     one = torch.ones(inside.shape, dtype=torch.float64, device=inside.device)
     rho = torch.where(inside, contrast * one, one)
     p = torch.full_like(rho, p0)
-    return conserved(rho, v[..., 0], v[..., 1], v[..., 2], p, gamma)
+    vx, vy, vz = v[..., 0], v[..., 1], v[..., 2]
+    if abc > 0.0:
+        x, y, z = cell_centres(leaves_np, root, n, ghosts, lo, hi, device)
+        k = 2.0 * np.pi
+        vx = vx + abc * (torch.sin(k * z) + torch.cos(k * y))
+        vy = vy + abc * (torch.sin(k * x) + torch.cos(k * z))
+        vz = vz + abc * (torch.sin(k * y) + torch.cos(k * x))
+    return conserved(rho, vx, vy, vz, p, gamma)
 
 
 def sedov(leaves, root, n, ghosts, lo, hi, gamma, E=1.0, rho0=1.0, p0=1e-5, half_width=None,
