@@ -181,19 +181,30 @@ enum { CELLO_EXEC_PLAIN = 0, CELLO_EXEC_BATCHED = 1, CELLO_EXEC_GRAPH = 2 };
 cello_status cello_set_exec(cello_mesh* mesh, int mode);
 
 /* Launch variant of the PPM sweep kernel used by cello_hydro_step and the
- * adjoint: pencils per CTA, register bound (minimum resident CTAs per SM)
- * and schedule (one CTA per work item, or one resident wave pulling items
- * from a device counter).  Float32 has 12 variants, float64 2; every variant
- * computes the same values.  Cached graphs are dropped. */
+ * adjoint, for all three sweep axes: the form (shared-memory phases with
+ * one thread per cell, or register streaming with one thread per pencil),
+ * pencils per CTA, register bound (minimum resident CTAs per SM) and
+ * schedule (one CTA per work item, or one resident wave pulling items from
+ * a device counter).  Float32 has 24 variants (12 shared-memory, 12
+ * streaming, of which 4 read x pencils as 16-byte vectors), float64 2.  The variants of one form compute the same values;
+ * the two float32 forms agree to float32 rounding (a multiply and an add
+ * may be fused across what is a register in one form and shared memory in
+ * the other).  Cached graphs are dropped. */
 cello_status cello_set_sweep_variant(cello_mesh* mesh, int variant);
 
+/* The same with one variant per sweep axis: variants[3] for the x, y and z
+ * sweeps (host array). */
+cello_status cello_set_sweep_variants(cello_mesh* mesh, const int* variants);
+
 /* Autotuner (Sec. IV: agglomerated work units on accelerators): times the
- * three sweeps of a step for every sweep variant on up to 4096 leaves of U
- * with dt = 0 (U is left bit-for-bit unchanged), keeps the fastest for this
- * mesh and returns it in *variant_out (nullable); ms_out (host, nullable,
- * ms_len entries) receives the best time of each variant.  Blocks until
- * done; call it outside any stream capture. */
-cello_status cello_autotune(cello_mesh* mesh, void* U, int* variant_out, float* ms_out, int ms_len,
+ * sweeps of an even and an odd step (each axis in both of its positions)
+ * for every sweep variant on up to 4096 leaves of U with dt = 0 (U is left
+ * bit-for-bit unchanged), keeps the fastest variant of each axis for this
+ * mesh and returns them in variants_out[3] (nullable); ms_out (host,
+ * nullable, ms_len entries) receives at [3 v + axis] the best time of
+ * variant v on that axis.  Blocks until done; call it outside any stream
+ * capture. */
+cello_status cello_autotune(cello_mesh* mesh, void* U, int* variants_out, float* ms_out, int ms_len,
                             void* stream);
 
 /* Algorithmic operation count of the three PPM sweeps of one step (Sec.
@@ -211,6 +222,17 @@ cello_status cello_autotune(cello_mesh* mesh, void* U, int* variant_out, float* 
  * only; CELLO_EINVAL otherwise or on a bad leaf id. */
 cello_status cello_sweep_opcount(const cello_mesh* mesh, float* U_host, const int32_t* leaf_ids, int64_t count,
                                  double dt, int cycle, double* out);
+
+/* One step with the state in HOST memory: copies the state (host ->
+ * device, into the caller's device buffer U_dev of the same size) and dt,
+ * runs cello_hydro_step, copies the state back into U_host and dt_next and
+ * the five totals into out_host[6], and waits for the stream.  U_host should
+ * be page-locked (cudaHostAlloc or cudaHostRegister) for full copy speed;
+ * pageable memory works, slower.  dt_host: the step's dt; dt_dev: a device
+ * double the call writes it to; scratch_dev: 6 device doubles.  Errors as
+ * cello_hydro_step. */
+cello_status cello_hydro_step_host(cello_mesh* mesh, void* U_host, void* U_dev, double dt_host, double* dt_dev,
+                                   int cycle, double cfl, double* scratch_dev, double* out_host, void* stream);
 
 /* One batched step (as cello_hydro_step, without dt_next/totals) with CUDA
  * events recorded between its phases; blocks until it completes and writes

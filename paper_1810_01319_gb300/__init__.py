@@ -173,6 +173,24 @@ class Mesh:
         o = out.reshape(3, 8)
         return o[:, :6].copy(), o[:, 6].copy(), o[:, 7].copy(), host
 
+    def hydro_step_host(self, U_host, U_dev, dt: float, cycle: int, cfl: float = 0.4, stream=None):
+        """One step with the state in host memory (copied in and out by the
+        library; page-locked U_host copies at full speed).  Returns
+        (dt_next, totals[5]) as Python floats."""
+        self._check_state(U_dev)
+        if U_host.device.type != "cpu" or U_host.dtype != U_dev.dtype or U_host.shape != U_dev.shape \
+                or not U_host.is_contiguous():
+            raise CelloError("U_host must be a contiguous CPU tensor shaped like the device state")
+        if not hasattr(self, "_host_scratch"):
+            self._host_scratch = torch.zeros(7, dtype=torch.float64, device=U_dev.device)
+            self._host_out = np.zeros(6, dtype=np.float64)
+        sc = self._host_scratch
+        _lib.check(_lib.lib().cello_hydro_step_host(self.handle, ctypes.c_void_p(U_host.data_ptr()), _ptr(U_dev),
+                                                    float(dt), _ptr(sc[6:]), int(cycle), float(cfl), _ptr(sc),
+                                                    self._host_out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+                   "cello_hydro_step_host")
+        return float(self._host_out[0]), [float(x) for x in self._host_out[1:]]
+
     def check(self) -> int:
         """Read and clear the device error word (waits for the device); raises
         CelloError with CELLO_ENONFINITE if a reduction saw a bad state."""
@@ -184,14 +202,23 @@ class Mesh:
         _lib.check(_lib.lib().cello_set_sweep_variant(self.handle, int(variant)), "cello_set_sweep_variant")
 
     def autotune(self, U, stream=None):
-        """Pick the fastest sweep variant for this mesh (U is not changed).
-        Returns (chosen variant, best milliseconds of each variant)."""
+        """Pick the fastest sweep variant of each axis for this mesh (U is not
+        changed).  Returns (chosen variants [x, y, z], best milliseconds of
+        each variant as [[x, y, z], ...])."""
         self._check_state(U)
-        v = ctypes.c_int()
-        ms = (ctypes.c_float * 16)()
-        _lib.check(_lib.lib().cello_autotune(self.handle, _ptr(U), ctypes.byref(v), ctypes.cast(ms, ctypes.c_void_p),
-                                             16, _stream(stream)), "cello_autotune")
-        return v.value, [t for t in ms if t > 0]
+        v = (ctypes.c_int * 3)()
+        ms = (ctypes.c_float * 192)()
+        _lib.check(_lib.lib().cello_autotune(self.handle, _ptr(U), ctypes.cast(v, ctypes.c_void_p),
+                                             ctypes.cast(ms, ctypes.c_void_p), 192, _stream(stream)),
+                   "cello_autotune")
+        t = [ms[3 * i:3 * i + 3] for i in range(64)]
+        return list(v), [list(x) for x in t if min(x) > 0]
+
+    def set_sweep_variants(self, variants):
+        """One sweep variant per axis (x, y, z)."""
+        arr = (ctypes.c_int * 3)(*[int(x) for x in variants])
+        _lib.check(_lib.lib().cello_set_sweep_variants(self.handle, ctypes.cast(arr, ctypes.c_void_p)),
+                   "cello_set_sweep_variants")
 
     def set_exec(self, mode: int):
         _lib.check(_lib.lib().cello_set_exec(self.handle, int(mode)), "cello_set_exec")

@@ -36,6 +36,8 @@ SIGNATURES = {
     "cello_mesh_free": (None, [_vp]),
     "cello_mesh_from_leaves": (ctypes.c_int, [ctypes.POINTER(MeshDesc), _vp, ctypes.c_int64, ctypes.POINTER(_vp)]),
     "cello_check": (ctypes.c_int, [_vp, _vp]),
+    "cello_hydro_step_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_int, ctypes.c_double,
+                                             _vp, _vp, _vp]),
     "cello_sweep_opcount": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, _vp]),
     "cello_mesh_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p]),
     "cello_mesh_leaves": (ctypes.c_int, [_vp, _vp]),
@@ -48,6 +50,7 @@ SIGNATURES = {
     "cello_reduce_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_set_exec": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cello_set_sweep_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "cello_set_sweep_variants": (ctypes.c_int, [_vp, _vp]),
     "cello_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "cello_hydro_adjoint_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "cello_profile_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp]),

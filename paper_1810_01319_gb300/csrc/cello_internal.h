@@ -18,9 +18,11 @@ constexpr int kAdjPencils = 4;       // pencils per adjoint-sweep CTA
 // schedule (static: one CTA per item; persistent: one resident wave of CTAs
 // pulling items from a device counter).  The autotuner times them.
 struct SweepVariant {
-  int pencils;
-  int min_blocks;
-  bool persistent;
+  int pencils;       // pencils per CTA (the CTA size of the streaming form)
+  int min_blocks;    // resident CTAs per SM the register bound is set for
+  bool persistent;   // work-counter schedule over a resident grid
+  bool stream;       // register-streaming form (sweep_stream_kernel)
+  bool vec4;         // streaming form reading x pencils four cells at a time
 };
 int sweep_variant_count_f32();
 int sweep_variant_count_f64();

@@ -4,12 +4,19 @@
 
 namespace cello {
 
-// Float32 sweep variants: {pencils per CTA, min resident CTAs per SM, persistent}.
+// Float32 sweep variants.  Shared-memory form: {pencils per CTA, min
+// resident CTAs per SM}; register-streaming form: {CTA size = pencils per
+// CTA, min resident CTAs per SM}; each without and with the persistent
+// work-counter schedule.
 static const SweepVariant kVariants[] = {
-    {8, 3, false}, {8, 4, false}, {4, 6, false}, {16, 1, false}, {4, 8, false}, {16, 2, false},
-    {8, 3, true},  {8, 4, true},  {4, 6, true},  {16, 1, true},  {4, 8, true},  {16, 2, true},
+    {8, 3, false, false},  {8, 4, false, false},  {4, 6, false, false}, {16, 1, false, false},
+    {4, 8, false, false},  {16, 2, false, false}, {64, 8, false, true}, {128, 4, false, true},
+    {64, 6, false, true},  {32, 16, false, true}, {64, 4, false, true, true}, {64, 6, false, true, true},
+    {8, 3, true, false},   {8, 4, true, false},   {4, 6, true, false},  {16, 1, true, false},
+    {4, 8, true, false},   {16, 2, true, false},  {64, 8, true, true},  {128, 4, true, true},
+    {64, 6, true, true},   {32, 16, true, true},  {64, 4, true, true, true},  {64, 6, true, true, true},
 };
-constexpr int kNT = 6;   // distinct kernel instantiations; variant v uses template v % kNT
+constexpr int kNT = 12;  // distinct kernel instantiations; variant v uses template v % kNT
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
 static int g_resident[3][kNV];   // resident CTAs per GPU by [n index][variant], from the occupancy API
 
@@ -31,22 +38,43 @@ static void prepare_variant(int v, int sms) {
   g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
 }
 
-template <int NB, int P, int MINB>
-static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, cudaStream_t s) {
-  constexpr int N = NB + 2 * kGhosts;
-  p.tiles_per_leaf = (pencils + P - 1) / P;
+template <int NB, int CT, int MINB, bool VEC4>
+static void prepare_stream_variant(int v, int sms) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_stream_kernel<float, NB, CT, MINB, VEC4>, CT, 0);
+  g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
+}
+
+// Work items, grid and schedule of one launch; false if there is no work.
+static bool plan_launch(SweepParams& p, int pencils, int per_cta, int v, int nbi, int& grid, cudaStream_t s) {
+  p.tiles_per_leaf = (pencils + per_cta - 1) / per_cta;
   p.n_items = p.nleaf * p.tiles_per_leaf;
-  if (p.n_items <= 0) return;
+  if (p.n_items <= 0) return false;
   p.div_tiles = FastDiv::make((unsigned)p.tiles_per_leaf);
   p.div_cb = FastDiv::make((unsigned)(p.b1 - p.b0));
-  int grid = p.n_items;
+  grid = p.n_items;
   if (kVariants[v].persistent && p.work) {
     cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
-    grid = g_resident[nb_index(NB)][v] < grid ? g_resident[nb_index(NB)][v] : grid;
+    grid = g_resident[nbi][v] < grid ? g_resident[nbi][v] : grid;
   } else {
     p.work = nullptr;
   }
+  return true;
+}
+
+template <int NB, int P, int MINB>
+static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, cudaStream_t s) {
+  constexpr int N = NB + 2 * kGhosts;
+  int grid = 0;
+  if (!plan_launch(p, pencils, P, v, nb_index(NB), grid, s)) return;
   sweep_kernel<float, NB, P, MINB><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
+}
+
+template <int NB, int CT, int MINB, bool VEC4>
+static void launch_stream_variant(const DevMesh& m, SweepParams p, int pencils, int v, cudaStream_t s) {
+  int grid = 0;
+  if (!plan_launch(p, pencils, CT, v, nb_index(NB), grid, s)) return;
+  sweep_stream_kernel<float, NB, CT, MINB, VEC4><<<grid, CT, 0, s>>>(m, p);
 }
 
 template <int NB>
@@ -57,6 +85,12 @@ static void prepare_nb(int sms) {
   prepare_variant<NB, 16, 1>(3, sms);
   prepare_variant<NB, 4, 8>(4, sms);
   prepare_variant<NB, 16, 2>(5, sms);
+  prepare_stream_variant<NB, 64, 8, false>(6, sms);
+  prepare_stream_variant<NB, 128, 4, false>(7, sms);
+  prepare_stream_variant<NB, 64, 6, false>(8, sms);
+  prepare_stream_variant<NB, 32, 16, false>(9, sms);
+  prepare_stream_variant<NB, 64, 4, true>(10, sms);
+  prepare_stream_variant<NB, 64, 6, true>(11, sms);
   for (int v = kNT; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - kNT];
 }
 
@@ -70,6 +104,12 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
     case 3: launch_variant<NB, 16, 1>(m, p, pencils, v, s); break;
     case 4: launch_variant<NB, 4, 8>(m, p, pencils, v, s); break;
     case 5: launch_variant<NB, 16, 2>(m, p, pencils, v, s); break;
+    case 6: launch_stream_variant<NB, 64, 8, false>(m, p, pencils, v, s); break;
+    case 7: launch_stream_variant<NB, 128, 4, false>(m, p, pencils, v, s); break;
+    case 8: launch_stream_variant<NB, 64, 6, false>(m, p, pencils, v, s); break;
+    case 9: launch_stream_variant<NB, 32, 16, false>(m, p, pencils, v, s); break;
+    case 10: launch_stream_variant<NB, 64, 4, true>(m, p, pencils, v, s); break;
+    case 11: launch_stream_variant<NB, 64, 6, true>(m, p, pencils, v, s); break;
   }
 }
 

@@ -172,11 +172,236 @@ sweep_kernel(DevMesh m, SweepParams prm) {
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
         const T Fp = sB[k * A + lc * S + lp], Fm = sB[k * A + (lc - 1) * S + lp];
-        base[comp[k] * SLAB] = Uc[comp[k]] - dtdx * (Fp - Fm);
+        base[comp[k] * SLAB] = Uc[comp[k]] - dtdx * sub_rn(Fp, Fm);
       }
     }
     __syncthreads();
     if (prm.work) {
+      if (t == 0) s_item = (int)atomicAdd(prm.work, 1u);
+      __syncthreads();
+      item = s_item;
+    } else {
+      item += gridDim.x;
+    }
+  }
+}
+
+// =====================================================================
+// Register-streaming form of the same sweep: one thread per pencil walks
+// its cells once, keeping a sliding window of the pencil in registers
+// (primitives of 5 cells, 2 slopes, 3 shock detectors, 3 interface values,
+// the last right-edge state and the last flux), so that no value passes
+// through shared memory and no phase waits at a barrier.  At step k the
+// thread reads cell k and produces: the slope of cell k-1, the shock
+// detector of cell k-2, the interface value k-2+1/2, the traced edge states
+// of cell k-3, the flux at interface k-4+1/2 and the updated cell k-4.  The
+// index ranges of every quantity are those of sweep_kernel, so the two
+// forms evaluate the same expressions on the same values.
+// =====================================================================
+// The sliding window of one pencil.
+template <typename T>
+struct PencilWindow {
+  T w[5][5];    // primitives of cells k-4 .. k (sweep-local components)
+  T dm[2][5];   // slopes of cells k-2, k-1
+  T ft[3];      // shock detectors of cells k-4 .. k-2
+  T ai[3][5];   // interface values k-4+1/2 .. k-2+1/2
+  T wp[5];      // right-edge state of cell k-4 (left state of interface k-4+1/2)
+  T fl[5];      // flux at interface k-5+1/2
+};
+
+// One step of the walk: cell k enters as conserved values Us (sweep-local
+// components); old holds cell k-4 as stored (component order), read
+// before it is overwritten here.
+// DEFER: the updated cell is returned in upd[5] (component order) instead
+// of being stored.
+template <typename T, int NB, bool DEFER = false>
+__device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T Us[5], const T old[5], T* base,
+                                            long sAx, const int comp[5], T dtdx, const Gas<T>& gs,
+                                            const DevMesh& m, const SweepParams& prm, int leaf, int axis,
+                                            bool face_row, int pa, int pb, T* upd = nullptr) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
+  to_primitive(Us, gs, S.w[4]);
+  if (k >= 3 && k <= N - 2) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.dm[1][c] = limited_slope(S.w[2][c], S.w[3][c], S.w[4][c]);
+  }
+  if (k >= 4) {
+    S.ft[2] = flatten_tilde(S.w[0][4], S.w[1][4], S.w[3][4], S.w[4][4], S.w[1][1], S.w[3][1]);
+    if (k <= N - 2) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        S.ai[2][c] = interface_value(S.w[2][c], S.w[3][c], S.dm[0][c], S.dm[1][c]);
+    }
+  }
+  if (k >= 6) {
+    // cell j = k-3: W = w[1], aL = ai[0], aR = ai[1], shock detectors ft[0..2]
+    const T s = S.w[2][4] - S.w[0][4];
+    const T f = (s > T(0)) ? vmax(S.ft[1], S.ft[0]) : ((s < T(0)) ? vmax(S.ft[1], S.ft[2]) : S.ft[1]);
+    T aL[5], aR[5], Wm[5], Wp[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      aL[c] = S.ai[0][c];
+      aR[c] = S.ai[1][c];
+      flatten_monotone(S.w[1][c], f, aL[c], aR[c]);
+    }
+    trace(S.w[1], aL, aR, dtdx, gs, Wm, Wp);
+    if (k >= 7) {
+      // interface j = k-4 (+1/2): left state wp (cell k-4), right state Wm (cell k-3)
+      T F[5];
+      riemann_flux_bulk(S.wp, Wm, gs, F);
+      const int j = k - 4;
+      if (face_row && (j == G - 1 || j == G + NB - 1)) {
+        const int face = 2 * axis + (j == G - 1 ? 0 : 1);
+        const int slot = m.face_slot[leaf * 6 + face];
+        if (slot >= 0) {
+          double* r = prm.reg + (long)slot * 5 * NB * NB + (pa - G) * NB + (pb - G);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) r[(long)comp[c] * NB * NB] = double(F[c]);
+        }
+      }
+      if (k >= 8) {
+        // cell j = k-4 between interfaces j-1/2 (fl) and j+1/2 (F)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const T v = old[c] - dtdx * sub_rn(F[c], S.fl[c]);
+          if (DEFER) upd[c] = v;
+          else base[comp[c] * SLAB + (long)j * sAx] = v;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) S.fl[c] = F[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.wp[c] = Wp[c];
+  }
+  // slide the windows
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    S.w[0][c] = S.w[1][c]; S.w[1][c] = S.w[2][c]; S.w[2][c] = S.w[3][c]; S.w[3][c] = S.w[4][c];
+    S.dm[0][c] = S.dm[1][c];
+    S.ai[0][c] = S.ai[1][c]; S.ai[1][c] = S.ai[2][c];
+  }
+  S.ft[0] = S.ft[1]; S.ft[1] = S.ft[2];
+}
+
+__device__ __forceinline__ float lane4(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void set_lane4(float4& v, int i, float x) {
+  if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+
+// VEC4 (float32, used on the x sweep, whose pencils run along the
+// contiguous axis): cells are read and written four at a time as 16-byte
+// vectors (a group is read one group ahead; the group updated during group
+// g is g-1, written back at its end) instead of 4-byte accesses 160 bytes
+// apart across the warp; other axes take the one-cell path.
+template <typename T, int NB, int CT, int MINB, bool VEC4>
+__global__ void __launch_bounds__(CT, MINB)
+sweep_stream_kernel(DevMesh m, SweepParams prm) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
+  const Gas<T> gs = Gas<T>::make(m.gamma);
+  T* U = static_cast<T*>(prm.U);
+  const int axis = prm.axis;
+  const int cA = prm.a1 - prm.a0, cB = prm.b1 - prm.b0;
+  const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
+  const long sTA = axis == 2 ? N : (long)N * N;
+  const long sTB = axis == 0 ? N : 1;
+  int comp[5];
+  comp[0] = 0; comp[1] = 1 + axis; comp[4] = 4;
+  comp[2] = axis == 0 ? 2 : 1;
+  comp[3] = axis == 2 ? 2 : 3;
+
+  const int t = threadIdx.x;
+  __shared__ int s_item;
+  __shared__ T s_dtdx[16];
+  if (t <= m.max_level) s_dtdx[t] = T(*prm.dt / ldexp(m.dx0, -t));
+  __syncthreads();
+
+  int item = blockIdx.x;
+  if (prm.work) {
+    if (t == 0) s_item = (int)atomicAdd(prm.work, 1u);
+    __syncthreads();
+    item = s_item;
+  }
+  while (item < prm.n_items) {
+    const int lrel = (int)prm.div_tiles.div((unsigned)item);
+    const int leaf = prm.leaf0 + lrel;
+    const int tile = item - lrel * prm.tiles_per_leaf;
+    const int4 lf = m.leaf[leaf];
+    const T dtdx = s_dtdx[lf.x];
+    const int q = tile * CT + t;
+    if (q < cA * cB) {
+      const int qa = (int)prm.div_cb.div((unsigned)q);
+      const int pa = prm.a0 + qa, pb = prm.b0 + q - qa * cB;
+      T* base = U + (long)leaf * 5 * SLAB + pa * sTA + pb * sTB;
+      const bool face_row = prm.reg && pa >= G && pa < G + NB && pb >= G && pb < G + NB;
+      PencilWindow<T> S;
+      T old[5];
+      if (VEC4 && axis == 0) {
+        // rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
+        float4* b4 = reinterpret_cast<float4*>(base);
+        float4 nx4[5];   // the next group of four cells
+#pragma unroll
+        for (int c = 0; c < 5; ++c) nx4[c] = b4[comp[c] * (SLAB / 4)];
+#pragma unroll 1
+        for (int g = 0; g < N / 4; ++g) {
+          float4 cur4[5], old4[5], out4[5];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) cur4[c] = nx4[c];
+          if (g + 1 < N / 4) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) nx4[c] = b4[comp[c] * (SLAB / 4) + g + 1];
+          }
+          if (g >= 2) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) old4[c] = b4[comp[c] * (SLAB / 4) + g - 1];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = 4 * g + i;
+            T Us[5], up[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+              Us[c] = lane4(cur4[c], i);
+              old[c] = lane4(old4[c], i);
+            }
+            stream_step<T, NB, true>(S, k, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb,
+                                     up);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) set_lane4(out4[c], i, up[c]);
+          }
+          if (g >= 2 && g - 1 <= N / 4 - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
+#pragma unroll
+            for (int c = 0; c < 5; ++c) b4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
+          }
+        }
+      } else {
+        T nx[5];   // cell k+1, loaded one step ahead
+#pragma unroll
+        for (int c = 0; c < 5; ++c) nx[c] = base[comp[c] * SLAB];
+#pragma unroll 1
+        for (int k = 0; k < N; ++k) {
+          T Us[5];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) Us[c] = nx[c];
+          if (k + 1 < N) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) nx[c] = base[comp[c] * SLAB + (k + 1) * sAx];
+          }
+          if (k >= 8) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) old[c] = base[comp[c] * SLAB + (k - 4) * sAx];
+          }
+          stream_step<T, NB>(S, k, Us, old, base, sAx, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb);
+        }
+      }
+    }
+    if (prm.work) {
+      __syncthreads();
       if (t == 0) s_item = (int)atomicAdd(prm.work, 1u);
       __syncthreads();
       item = s_item;

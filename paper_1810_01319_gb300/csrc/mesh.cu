@@ -151,7 +151,7 @@ struct cello_mesh {
   long long* d_slow = nullptr;     // ghost runs that are not same-level copies (leaf * runs + run)
   std::vector<int> slow_start;     // per-leaf offsets into d_slow, B + 1 entries
   int exec_mode = CELLO_EXEC_BATCHED;
-  int sweep_variant = 0;           // chosen by cello_autotune or cello_set_sweep_variant
+  int sweep_variant[3] = {0, 0, 0};   // per sweep axis; chosen by cello_autotune or set by the caller
   unsigned* d_work = nullptr;      // work counter of the persistent sweep variants
   unsigned* d_err = nullptr;       // error word set by the reduction
   double* d_zero = nullptr;        // dt = 0, for timing sweeps without changing the state
@@ -490,7 +490,7 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
     p.dt = dt;
     p.reg = M->d_reg;
     p.work = M->d_work;
-    p.variant = M->sweep_variant;
+    p.variant = M->sweep_variant[axis];
     if (plain) {
       for (int b = 0; b < B; ++b) {
         p.leaf0 = b;
@@ -555,7 +555,7 @@ cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double
       p.dt = dt;
       p.reg = nullptr;
       p.work = M->d_work;
-      p.variant = M->sweep_variant;
+      p.variant = M->sweep_variant[axis];
       p.leaf0 = 0;
       p.nleaf = B;
       if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
@@ -851,66 +851,100 @@ cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, 
   return adjoint_step(M, Un, lam, dt, cycle, (cudaStream_t)stream);
 }
 
-cello_status cello_set_sweep_variant(cello_mesh* M, int variant) {
-  if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
+cello_status cello_set_sweep_variants(cello_mesh* M, const int* variants) {
+  if (!M || !variants) return fail(CELLO_EINVAL, "NULL argument");
   const int nv = M->desc.precision == 4 ? sweep_variant_count_f32() : sweep_variant_count_f64();
-  if (variant < 0 || variant >= nv) return fail(CELLO_EINVAL, "sweep variant out of range");
-  M->sweep_variant = variant;
+  for (int a = 0; a < 3; ++a)
+    if (variants[a] < 0 || variants[a] >= nv) return fail(CELLO_EINVAL, "sweep variant out of range");
+  for (int a = 0; a < 3; ++a) M->sweep_variant[a] = variants[a];
   for (auto& g : M->graphs) cudaGraphExecDestroy(g.exec);
   M->graphs.clear();
   return CELLO_OK;
 }
 
-cello_status cello_autotune(cello_mesh* M, void* U, int* variant_out, float* ms_out, int ms_len, void* stream) {
+cello_status cello_set_sweep_variant(cello_mesh* M, int variant) {
+  const int v[3] = {variant, variant, variant};
+  return cello_set_sweep_variants(M, v);
+}
+
+cello_status cello_autotune(cello_mesh* M, void* U, int* variants_out, float* ms_out, int ms_len, void* stream) {
   if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   const cello_mesh_desc& d = M->desc;
   const DevMesh dm = M->dev();
   const int nv = d.precision == 4 ? sweep_variant_count_f32() : sweep_variant_count_f64();
   const int nleaf = std::min(M->B, 4096);   // per-leaf cost is uniform: a sample of leaves suffices
-  cudaEvent_t e0, e1;
-  CELLO_CUDA(cudaEventCreate(&e0));
-  CELLO_CUDA(cudaEventCreate(&e1));
-  int best = 0;
-  float best_ms = 1e30f;
-  for (int v = 0; v < nv; ++v) {
-    float vbest = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
-      cudaEventRecord(e0, s);
-      bool swept[3] = {false, false, false};
-      for (int axis = 0; axis < 3; ++axis) {   // the three sweeps of an even cycle, dt = 0 (state unchanged)
-        SweepParams p{};
-        p.U = U;
-        p.axis = axis;
-        sweep_ranges(M, axis, swept, p.a0, p.a1, p.b0, p.b1);
-        const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
-        p.dt = M->d_zero;
-        p.reg = nullptr;
-        p.work = M->d_work;
-        p.variant = v;
-        p.leaf0 = 0;
-        p.nleaf = nleaf;
-        if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
-        else launch_sweep_f64(dm, p, pencils, s);
-        swept[axis] = true;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) CELLO_CUDA(cudaEventCreate(&ev[i]));
+  int best[3] = {0, 0, 0};
+  float best_ms[3] = {1e30f, 1e30f, 1e30f};
+  cudaError_t err = cudaSuccess;
+  for (int v = 0; v < nv && err == cudaSuccess; ++v) {
+    float vbest[3] = {1e30f, 1e30f, 1e30f};
+    for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+      float axis_ms[3] = {0, 0, 0};
+      // the sweeps of an even (x, y, z) and an odd (z, y, x) cycle, dt = 0 (state unchanged):
+      // each axis is timed in both of its positions
+      for (int parity = 0; parity < 2 && err == cudaSuccess; ++parity) {
+        const int order[3] = {parity == 0 ? 0 : 2, 1, parity == 0 ? 2 : 0};
+        bool swept[3] = {false, false, false};
+        cudaEventRecord(ev[0], s);
+        for (int oi = 0; oi < 3; ++oi) {
+          const int axis = order[oi];
+          SweepParams p{};
+          p.U = U;
+          p.axis = axis;
+          sweep_ranges(M, axis, swept, p.a0, p.a1, p.b0, p.b1);
+          const int pencils = (p.a1 - p.a0) * (p.b1 - p.b0);
+          p.dt = M->d_zero;
+          p.reg = nullptr;
+          p.work = M->d_work;
+          p.variant = v;
+          p.leaf0 = 0;
+          p.nleaf = nleaf;
+          if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
+          else launch_sweep_f64(dm, p, pencils, s);
+          swept[axis] = true;
+          cudaEventRecord(ev[oi + 1], s);
+        }
+        err = cudaEventSynchronize(ev[3]);
+        for (int oi = 0; oi < 3 && err == cudaSuccess; ++oi) {
+          float ms = 0;
+          err = cudaEventElapsedTime(&ms, ev[oi], ev[oi + 1]);
+          axis_ms[order[oi]] += ms;
+        }
       }
-      cudaEventRecord(e1, s);
-      CELLO_CUDA(cudaEventSynchronize(e1));
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0 && ms < vbest) vbest = ms;   // the first repetition warms up
+      if (rep > 0)   // the first repetition warms up
+        for (int a = 0; a < 3; ++a) vbest[a] = std::min(vbest[a], axis_ms[a]);
     }
-    if (ms_out && v < ms_len) ms_out[v] = vbest;
-    if (vbest < best_ms) {
-      best_ms = vbest;
-      best = v;
+    for (int a = 0; a < 3; ++a) {
+      if (ms_out && 3 * v + a < ms_len) ms_out[3 * v + a] = vbest[a];
+      if (vbest[a] < best_ms[a]) {
+        best_ms[a] = vbest[a];
+        best[a] = v;
+      }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  CELLO_CUDA(err);
   CELLO_CUDA(cudaGetLastError());
-  if (variant_out) *variant_out = best;
-  return cello_set_sweep_variant(M, best);
+  if (variants_out)
+    for (int a = 0; a < 3; ++a) variants_out[a] = best[a];
+  return cello_set_sweep_variants(M, best);
+}
+
+cello_status cello_hydro_step_host(cello_mesh* M, void* U_host, void* U_dev, double dt_host, double* dt_dev,
+                                   int cycle, double cfl, double* scratch_dev, double* out_host, void* stream) {
+  if (!M || !U_host || !U_dev || !dt_dev || !scratch_dev || !out_host) return fail(CELLO_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)M->B * 5 * M->N * M->N * M->N * (size_t)M->desc.precision;
+  CELLO_CUDA(cudaMemcpyAsync(U_dev, U_host, bytes, cudaMemcpyHostToDevice, s));
+  CELLO_CUDA(cudaMemcpyAsync(dt_dev, &dt_host, sizeof(double), cudaMemcpyHostToDevice, s));
+  CELLO_TRY(cello_hydro_step(M, U_dev, dt_dev, cycle, cfl, scratch_dev, scratch_dev + 1, stream));
+  CELLO_CUDA(cudaMemcpyAsync(U_host, U_dev, bytes, cudaMemcpyDeviceToHost, s));
+  CELLO_CUDA(cudaMemcpyAsync(out_host, scratch_dev, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CELLO_CUDA(cudaStreamSynchronize(s));
+  return CELLO_OK;
 }
 
 cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32_t* leaf_ids, int64_t count,

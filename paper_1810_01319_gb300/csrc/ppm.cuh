@@ -31,6 +31,23 @@ CELLO_HD double vsqrt(double a) { return sqrt(a); }
 CELLO_HD float vcopysign(float a, float b) { return copysignf(a, b); }
 CELLO_HD double vcopysign(double a, double b) { return copysign(a, b); }
 
+// Subtraction that is never fused with the multiply producing an operand
+// (a flux difference must round each flux first, wherever the fluxes live).
+CELLO_HD float sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+CELLO_HD double sub_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+
 // Gas constants in the working precision, derived once in float64.
 template <typename T> struct Gas {
   T gamma, gm1, g1, inv_gm1;
@@ -53,6 +70,22 @@ CELLO_HD void to_primitive(const T U[5], const Gas<T>& gs, T W[5]) {
   T ut2 = U[3] / rho;
   T ke = (T(0.5) * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
   T p = vmax(gs.gm1 * (U[4] - ke), T(kPFloor));
+  W[0] = rho; W[1] = un; W[2] = ut1; W[3] = ut2; W[4] = p;
+}
+
+// Float32 form: one reciprocal of rho and three multiplies rounded on their
+// own (never fused into a neighbouring add), so that a velocity is the same
+// rounded value whether it is kept in a register or passes through memory.
+CELLO_HD void to_primitive(const float U[5], const Gas<float>& gs, float W[5]) {
+  const float rho = vmax(U[0], float(kRhoFloor));
+  const float ir = 1.0f / rho;
+#ifdef __CUDA_ARCH__
+  const float un = __fmul_rn(U[1], ir), ut1 = __fmul_rn(U[2], ir), ut2 = __fmul_rn(U[3], ir);
+#else
+  const float un = U[1] * ir, ut1 = U[2] * ir, ut2 = U[3] * ir;
+#endif
+  const float ke = (0.5f * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
+  const float p = vmax(gs.gm1 * (U[4] - ke), float(kPFloor));
   W[0] = rho; W[1] = un; W[2] = ut1; W[3] = ut2; W[4] = p;
 }
 

@@ -131,26 +131,53 @@ def test_exec_modes_bit_identical(blob_amr, precision):
         assert torch.equal(U, outs[0][0]) and torch.equal(tot, outs[0][1])
 
 
+# float32 sweep variants by form: shared-memory phases, register streaming
+F32_SMEM = [0, 1, 2, 3, 4, 5, 12, 13, 14, 15, 16, 17]
+F32_STREAM = [6, 7, 8, 9, 10, 11, 18, 19, 20, 21, 22, 23]
+
+
 @pytest.mark.parametrize("precision", [4, 8])
 def test_sweep_variants_identical_and_autotune(blob_amr, precision):
-    """Every launch variant of the sweep (tile shape, register bound,
-    persistent schedule) computes the same values; the autotuner leaves the
-    state unchanged and picks one of them."""
+    """Within each form of the sweep (shared-memory phases; register
+    streaming), every launch variant (tile shape, register bound, persistent
+    schedule) computes the same values.  The two float32 forms evaluate the
+    same expressions but the compiler may fuse a multiply and an add across
+    what is a shared-memory boundary in one form and a register in the other,
+    so they agree to float32 rounding, far inside the parity bar.  The
+    autotuner leaves the state unchanged and picks one variant per axis."""
     od, om, flags, U0, Uo, dts = blob_amr
     gm = H.gpu_mesh_from_flags(od, flags, precision)
-    nv = 12 if precision == 4 else 2
-    outs = []
+    forms = [F32_SMEM, F32_STREAM] if precision == 4 else [[0, 1]]
+    nv = sum(len(f) for f in forms)
+    outs = {}
     for v in range(nv):
         gm.set_sweep_variant(v)
-        U, _, tot = _run_gpu(gm, U0, 3, dts=dts)
-        outs.append(U.cpu())
-    for v in range(1, nv):
-        assert torch.equal(outs[v], outs[0]), v
+        U, _, tot = _run_gpu(gm, U0, 6, dts=dts)
+        outs[v] = U.cpu()
+    for form in forms:
+        for v in form[1:]:
+            assert torch.equal(outs[v], outs[form[0]]), v
+    if precision == 4:
+        a, b = H.interior(outs[F32_SMEM[0]], 16), H.interior(outs[F32_STREAM[0]], 16)
+        assert max(H.l1_rel_per_field(a, b)) <= 1e-6
+        for v in (F32_SMEM[0], F32_STREAM[0]):   # each form against the float64 oracle
+            l1 = H.l1_rel_per_field(H.interior(outs[v], 16), H.interior(Uo, 16))
+            assert max(l1) <= 2e-5, (v, l1)
     U = U0.to(gm.dtype).cuda().contiguous()
     before = U.clone()
     best, ms = gm.autotune(U)
     assert torch.equal(U, before)
-    assert 0 <= best < nv and len(ms) == nv and min(ms) > 0
+    assert len(best) == 3 and all(0 <= b < nv for b in best)
+    assert len(ms) == nv and all(len(t) == 3 and min(t) > 0 for t in ms)
+    # a mixed per-axis choice
+    mixed = [F32_SMEM[0], F32_STREAM[-1], F32_STREAM[0]] if precision == 4 else [1, 0, 1]
+    gm.set_sweep_variants(mixed)
+    U, _, _ = _run_gpu(gm, U0, 6, dts=dts)
+    if precision == 8:
+        assert torch.equal(U.cpu(), outs[0])
+    else:
+        l1 = H.l1_rel_per_field(H.interior(U.cpu(), 16), H.interior(Uo, 16))
+        assert max(l1) <= 2e-5, l1
 
 
 def test_sweep_opcount_mirrors_the_kernel():
@@ -176,3 +203,22 @@ def test_sweep_opcount_mirrors_the_kernel():
         per_cell = ops.sum(1) / cells
         assert np.all(per_cell > 300) and np.all(per_cell < 3000), per_cell
         assert np.all(ops > 0)
+
+
+def test_hydro_step_host_buffers_match_device_step(blob_amr):
+    """The host-buffer entry point copies in, steps and copies out: the same
+    state, dt_next and totals as the device call."""
+    od, om, flags, U0, Uo, dts = blob_amr
+    gm = H.gpu_mesh_from_flags(od, flags, 4)
+    Ud = U0.to(torch.float32).cuda().contiguous()
+    host = U0.to(torch.float32).contiguous().clone()
+    scratch = torch.empty_like(Ud)
+    dtn = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(5, dtype=torch.float64, device="cuda")
+    for c in range(3):
+        dt = float(dts[c])
+        gm.hydro_step(Ud, torch.full((1,), dt, dtype=torch.float64, device="cuda"), c, dt_next=dtn, totals=tot)
+        dn, th = gm.hydro_step_host(host, scratch, dt, c)
+        assert dn == float(dtn.item())
+        assert th == [float(x) for x in tot.cpu()]
+    assert torch.equal(host, Ud.cpu())
