@@ -240,10 +240,70 @@ def riemann_flux(WL, WR, gamma):
     return f0, f1, f2, f3, f4
 
 
-def pencil_fluxes(Uc, dtdx, gamma):
+def hllc_waves(WL, WR, gamma):
+    """The HLLC wave fan (Toro, Spruce & Speares 1994; Toro, "Riemann Solvers
+    and Numerical Methods for Fluid Dynamics", 3rd ed., Sec. 10.4) of left
+    and right primitive states (rho, u_n, u_t1, u_t2, p): wave-speed bounds
+    of Davis, S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R +
+    c_R); contact speed S* = (p_R - p_L + m_L u_L - m_R u_R) / (m_L - m_R)
+    with m_K = rho_K (S_K - u_K) (Toro eq. 10.37); star states U*_K = m_K /
+    (S_K - S*) (1, S*, v_K, w_K, E_K / rho_K + (S* - u_K)(S* + p_K / m_K))
+    (eq. 10.39) and star fluxes F*_K = F_K + S_K (U*_K - U_K) (eq. 10.38).
+    Returns a dict of the speeds, the side states U, fluxes F and the star
+    states and fluxes."""
+    inv_gm1 = 1.0 / (gamma - 1.0)
+
+    def side(W):
+        r, u, v, w, p = W
+        c = ieee_sqrt((gamma * p) / r)
+        E = p * inv_gm1 + (0.5 * r) * (u * u + (v * v + w * w))
+        f0 = r * u
+        F = (f0, f0 * u + p, f0 * v, f0 * w, u * (E + p))
+        Uc = (r, r * u, r * v, r * w, E)
+        return c, E, F, Uc
+
+    rL, uL, vL, wL, pL = WL
+    rR, uR, vR, wR, pR = WR
+    cL, EL, FL, UL = side(WL)
+    cR, ER, FR, UR = side(WR)
+    SL = torch.minimum(uL - cL, uR - cR)
+    SR = torch.maximum(uL + cL, uR + cR)
+    mL = rL * (SL - uL)
+    mR = rR * (SR - uR)
+    Ss = ((pR - pL) + (mL * uL - mR * uR)) / (mL - mR)
+
+    def star(S, m, r, u, v, w, p, E, F, Uc):
+        fac = m / (S - Ss)
+        Us = (fac, fac * Ss, fac * v, fac * w, fac * (E / r + (Ss - u) * (Ss + p / m)))
+        return Us, tuple(Fk + S * (Usk - Uk) for Fk, Usk, Uk in zip(F, Us, Uc))
+
+    UsL, FsL = star(SL, mL, rL, uL, vL, wL, pL, EL, FL, UL)
+    UsR, FsR = star(SR, mR, rR, uR, vR, wR, pR, ER, FR, UR)
+    return dict(SL=SL, SR=SR, Ss=Ss, UL=UL, UR=UR, FL=FL, FR=FR, UsL=UsL, UsR=UsR, FsL=FsL, FsR=FsR)
+
+
+def hllc_flux(WL, WR, gamma):
+    """HLLC interface flux, an alternative to the two-shock flux of the PPM
+    sweep: the flux of the region of the fan (hllc_waves) holding x/t = 0,
+    F_L if S_L >= 0, F*_L if S* >= 0, F*_R if S_R > 0, else F_R.  Returns
+    the five fluxes (rho, m_n, m_t1, m_t2, E)."""
+    h = hllc_waves(WL, WR, gamma)
+    SL, Ss, SR = h["SL"], h["Ss"], h["SR"]
+    out = []
+    for k in range(5):
+        out.append(torch.where(SL >= 0.0, h["FL"][k],
+                               torch.where(Ss >= 0.0, h["FsL"][k],
+                                           torch.where(SR > 0.0, h["FsR"][k], h["FR"][k]))))
+    return tuple(out)
+
+
+RIEMANN = {"two-shock": riemann_flux, "hllc": hllc_flux}
+
+
+def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock"):
     """Fluxes at the n+1 interfaces between cells c and c+1, c = 3 .. N-5, of
     pencils of length N = n + 8 (last tensor dim).  Uc = (rho, m_n, m_t1,
-    m_t2, E) tensors."""
+    m_t2, E) tensors; riemann names the interface solver."""
     N = Uc[0].shape[-1]
     W = primitives(*Uc, gamma)
     p, un = W[4], W[1]
@@ -268,7 +328,7 @@ def pencil_fluxes(Uc, dtdx, gamma):
     Wm, Wp = trace(Wc, aL, aR, dtdx, gamma)        # cells 3..N-4
     left = [x[..., 0:N - 7] for x in Wp]
     right = [x[..., 1:N - 6] for x in Wm]
-    return riemann_flux(left, right, gamma)
+    return RIEMANN[riemann](left, right, gamma)
 
 
 # ------------------------------------------------------------------ sweeps
@@ -297,7 +357,7 @@ def sweep(U, mesh: Mesh, axis: int, dt: float, rows):
     comp = AXIS_COMPONENTS[axis]
     V = U.movedim(dim, -1)
     dtdx = dtdx_of_leaves(mesh, dt).view(B, 1, 1, 1)
-    F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma)
+    F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma, mesh.desc.riemann)
     (a0, a1), (b0, b1) = rows
     V2 = V.clone()
     for q in range(5):

@@ -41,7 +41,8 @@ SAME, COARSE, FINE, BOUNDARY = 0, 1, 2, 3
 @dataclass(frozen=True)
 class Desc:
     """Mesh description: root blocks per axis, cells per block edge n, ghost
-    depth, deepest level, physical box, boundary kind per axis, gamma."""
+    depth, deepest level, physical box, boundary kind per axis, gamma, and
+    the Riemann solver of the PPM sweeps."""
     root: tuple
     n: int
     ghosts: int
@@ -50,6 +51,7 @@ class Desc:
     hi: tuple = (1.0, 1.0, 1.0)
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
     gamma: float = 1.4
+    riemann: str = "two-shock"   # interface flux: "two-shock" (CW84) or "hllc"
 
     def dx(self, level: int) -> float:
         """Cell width at a level (cells are cubes; checked in Mesh)."""

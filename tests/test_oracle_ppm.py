@@ -121,3 +121,88 @@ def test_sedov_constant():
     # Kamm & Timmes (2007), energy constants alpha = xi0^-(nu+2) for gamma = 1.4
     assert exact.sedov_xi0(1.4, nu=3) ** -5 == pytest.approx(0.851072, abs=2e-6)
     assert exact.sedov_xi0(1.4, nu=2) ** -4 == pytest.approx(0.984074, abs=2e-6)
+
+
+# ---------------------------------------------------------------- HLLC
+def _states(seed, n=200, umax=1.0):
+    g = torch.Generator().manual_seed(seed)
+    r = 0.1 + torch.rand(n, generator=g, dtype=torch.float64)
+    u = umax * torch.randn(n, generator=g, dtype=torch.float64)
+    t1 = torch.randn(n, generator=g, dtype=torch.float64)
+    t2 = torch.randn(n, generator=g, dtype=torch.float64)
+    p = 0.1 + torch.rand(n, generator=g, dtype=torch.float64)
+    return (r, u, t1, t2, p)
+
+
+def test_hllc_consistency_equal_states():
+    W = _states(3)
+    F = H.hllc_flux(W, W, 1.4)
+    for a, b in zip(F, _flux(W, 1.4)):
+        assert torch.allclose(a, b, rtol=1e-14, atol=1e-14)
+
+
+def test_hllc_resolves_a_stationary_contact_exactly():
+    """A contact at rest (equal p, zero velocity, any density jump) is an
+    exact HLLC solution: no mass or energy crosses, the momentum flux is p
+    (Toro Sec. 10.4: the middle wave is resolved)."""
+    one = torch.ones(1, dtype=torch.float64)
+    z = torch.zeros(1, dtype=torch.float64)
+    for rl, rr in ((1.0, 0.25), (4.0, 0.5), (0.125, 2.0)):
+        WL = (rl * one, z, z, z, one)
+        WR = (rr * one, z, z, z, one)
+        F = H.hllc_flux(WL, WR, 1.4)
+        assert float(F[0]) == 0.0 and float(F[1]) == 1.0 and float(F[4]) == 0.0
+        assert float(F[2]) == 0.0 and float(F[3]) == 0.0
+
+
+def test_hllc_moving_contact_is_upwinded():
+    one = torch.ones(1, dtype=torch.float64)
+    z = torch.zeros(1, dtype=torch.float64)
+    for u0 in (0.3, -0.3):
+        WL = (one, u0 * one, 0.2 * one, z, one)
+        WR = (0.25 * one, u0 * one, -0.4 * one, z, one)
+        F = H.hllc_flux(WL, WR, 1.4)
+        up = WL if u0 > 0 else WR
+        Fe = _flux(up, 1.4)
+        for a, b in zip(F, Fe):
+            assert float(a) == pytest.approx(float(b), rel=1e-13, abs=1e-14)
+
+
+def test_hllc_supersonic_takes_the_upwind_flux():
+    W = _states(4, umax=0.0)
+    WL = (W[0], W[1] + 5.0, W[2], W[3], W[4])     # u - c > 0 on both sides
+    WR = (W[4] * 0 + 0.5, W[1] + 6.0, W[3], W[2], W[0])
+    F = H.hllc_flux(WL, WR, 1.4)
+    for a, b in zip(F, _flux(WL, 1.4)):
+        assert torch.allclose(a, b, rtol=1e-14, atol=1e-14)
+
+
+def test_hllc_mirror_symmetry_bit_exact():
+    WL, WR = _states(5), _states(6)
+
+    def mirror(W):
+        return (W[0], -W[1], W[2], W[3], W[4])
+    F = H.hllc_flux(WL, WR, 1.4)
+    Fm = H.hllc_flux(mirror(WR), mirror(WL), 1.4)
+    assert torch.equal(Fm[0], -F[0]) and torch.equal(Fm[1], F[1]) and torch.equal(Fm[4], -F[4])
+    assert torch.equal(Fm[2], -F[2]) and torch.equal(Fm[3], -F[3])
+
+
+def test_hllc_fan_satisfies_the_jump_conditions():
+    """Across the contact the two star states satisfy the Rankine-Hugoniot
+    conditions, F*_R - F*_L = S* (U*_R - U*_L), in all five components
+    (equal star pressure and normal velocity S* on both sides), and the fan
+    satisfies the integral consistency condition (S* - S_L) U*_L + (S_R - S*)
+    U*_R = S_R U_R - S_L U_L - (F_R - F_L) (Toro Sec. 10.4)."""
+    for seed in (7, 8, 9):
+        h = H.hllc_waves(_states(seed), _states(seed + 10), 1.4)
+        SL, Ss, SR = h["SL"], h["Ss"], h["SR"]
+        for k in range(5):
+            lhs = h["FsR"][k] - h["FsL"][k]
+            rhs = Ss * (h["UsR"][k] - h["UsL"][k])
+            scale = h["FsR"][k].abs() + h["FsL"][k].abs() + (Ss * h["UsR"][k]).abs() + 1.0
+            assert float(((lhs - rhs).abs() / scale).max()) < 1e-12, k
+            a = (Ss - SL) * h["UsL"][k] + (SR - Ss) * h["UsR"][k]
+            b = SR * h["UR"][k] - SL * h["UL"][k] - (h["FR"][k] - h["FL"][k])
+            sc = (SR * h["UR"][k]).abs() + (SL * h["UL"][k]).abs() + h["FR"][k].abs() + h["FL"][k].abs() + 1.0
+            assert float(((a - b).abs() / sc).max()) < 1e-12, k

@@ -262,3 +262,20 @@ def test_remap_conserves_and_reproduces_linear_fields():
     inner = ((xn > 0.2) & (xn < 0.8) & (yn > 0.2) & (yn < 0.8) & (zn > 0.2) & (zn < 0.8))[:, g:g + n, g:g + n, g:g + n]
     assert inner.sum() > 1000
     assert (got - want)[inner].abs().max() < 1e-14
+
+
+def test_sod_with_hllc_against_exact_solution():
+    """The HLLC interface flux in the full PPM step: Sod converges to the
+    exact solution like the two-shock flux does."""
+    errs = []
+    for nx in (4, 8):
+        d = M.Desc(root=(nx, 1, 1), n=16, ghosts=4, max_level=0, hi=(1.0, 1.0 / nx, 1.0 / nx),
+                   bc=(M.OUTFLOW, M.PERIODIC, M.PERIODIC), gamma=1.4, riemann="hllc")
+        mesh = M.root_mesh(d)
+        U, dts = H.run(_state(mesh, "sod"), mesh, 10 * nx, 0.4)
+        T = sum(dts)
+        rho = torch.cat([_interior(mesh, U)[b, 0, 0, 0, :] for b in range(nx)]).numpy()
+        x = (np.arange(nx * 16) + 0.5) / (nx * 16)
+        re, _, _ = exact.sample((x - 0.5) / T, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+        errs.append(np.abs(rho - re).mean())
+    assert errs[0] < 0.01 and errs[1] < errs[0] / 2 ** 0.6, errs
