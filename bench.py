@@ -358,6 +358,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="blob-amr-large", choices=["blob-amr-large", "sedov-deep"])
     ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
+    ap.add_argument("--variants", default="", help="sweep variants x,y,z instead of autotuning (profiling)")
     ap.add_argument("--abc", type=float, default=0.0,
                     help="amplitude of an ABC flow added to every cell (0: blobs in a medium at rest)")
     args = ap.parse_args()
@@ -416,9 +417,14 @@ def main():
     mesh, U = build_workload(cfg, 4, log=log)
     log(f"[bench] workload ready in {time.time() - t_setup:.1f}s: {mesh.n_leaves} leaves, "
         f"{mesh.n_coarse_fine} coarse-fine faces")
-    variant, variant_ms = mesh.autotune(U)
-    log(f"[bench] autotuned sweep variants (x, y, z) {variant}: "
-        f"{[['%.2f' % t for t in axes] for axes in variant_ms]} ms")
+    if args.variants:
+        variant, variant_ms = [int(v) for v in args.variants.split(",")], None
+        mesh.set_sweep_variants(variant)
+        log(f"[bench] sweep variants (x, y, z) {variant} as given")
+    else:
+        variant, variant_ms = mesh.autotune(U)
+        log(f"[bench] autotuned sweep variants (x, y, z) {variant}: "
+            f"{[['%.2f' % t for t in axes] for axes in variant_ms]} ms")
     mesh.set_exec(EXEC_GRAPH)
     cells = mesh.n_leaves * cfg["n"] ** 3
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")

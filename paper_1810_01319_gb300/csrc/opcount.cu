@@ -48,6 +48,7 @@ CELLO_HD bool operator!=(OpF a, OpF b) { tick(); return a.v != b.v; }
 CELLO_HD OpF vabs(OpF a) { tick(); return OpF(fabsf(a.v)); }
 CELLO_HD OpF vsqrt(OpF a) { tick(); return OpF(sqrtf(a.v)); }
 CELLO_HD OpF vcopysign(OpF a, OpF b) { tick(); return OpF(copysignf(a.v, b.v)); }
+CELLO_HD OpF vdiv(OpF a, OpF b) { tick(); return OpF(a.v / b.v); }
 
 }  // namespace
 

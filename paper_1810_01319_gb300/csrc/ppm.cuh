@@ -48,6 +48,19 @@ CELLO_HD double sub_rn(double a, double b) {
 #endif
 }
 
+// Division in the bulk arithmetic: float32 on the device uses the fast
+// approximate form (reciprocal and multiply, within 2 ulp for divisors
+// below 2^126, which every divisor here is: densities, pressures, sound
+// speeds and their sums); float64 keeps the correctly rounded division.
+CELLO_HD float vdiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+CELLO_HD double vdiv(double a, double b) { return a / b; }
+
 // Gas constants in the working precision, derived once in float64.
 template <typename T> struct Gas {
   T gamma, gm1, g1, inv_gm1;
@@ -78,7 +91,7 @@ CELLO_HD void to_primitive(const T U[5], const Gas<T>& gs, T W[5]) {
 // rounded value whether it is kept in a register or passes through memory.
 CELLO_HD void to_primitive(const float U[5], const Gas<float>& gs, float W[5]) {
   const float rho = vmax(U[0], float(kRhoFloor));
-  const float ir = 1.0f / rho;
+  const float ir = vdiv(1.0f, rho);
 #ifdef __CUDA_ARCH__
   const float un = __fmul_rn(U[1], ir), ut1 = __fmul_rn(U[2], ir), ut2 = __fmul_rn(U[3], ir);
 #else
@@ -111,7 +124,7 @@ CELLO_HD T flatten_tilde(T pm2, T pm1, T pp1, T pp2, T um1, T up1) {
   T dp1 = pp1 - pm1;
   T dp2 = pp2 - pm2;
   bool shock = (vabs(dp1) > T(kEpsShock) * vmin(pp1, pm1)) && (um1 - up1 > T(0)) && (dp2 != T(0));
-  T ratio = dp1 / ((dp2 != T(0)) ? dp2 : T(1));
+  T ratio = vdiv(dp1, (dp2 != T(0)) ? dp2 : T(1));
   T ft = vmax(vmin(T(kOmega2) * (ratio - T(kOmega1)), T(1)), T(0));
   return shock ? ft : T(0);
 }
@@ -150,15 +163,15 @@ template <typename T>
 CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
                                       const Gas<T>& gs, T Wm[5], T Wp[5]) {
   const T rho = W[0], un = W[1], p = W[4];
-  const T csq = (gs.gamma * p) / rho;
+  const T csq = vdiv(gs.gamma * p, rho);
   const T c = vsqrt(csq);
   T a6[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) a6[q] = T(6) * (W[q] - T(0.5) * (aL[q] + aR[q]));
   const T lm = un - c, l0 = un, lp = un + c;
-  const T half_rho_c = (T(0.5) * rho) / c;
-  const T half_inv_csq = T(0.5) / csq;
-  const T c_rho = c / rho;
+  const T half_rho_c = vdiv(T(0.5) * rho, c);
+  const T half_inv_csq = vdiv(T(0.5), csq);
+  const T c_rho = vdiv(c, rho);
 
   {  // right edge: waves moving right
     const T sp = lp * dtdx, s0 = l0 * dtdx, sm = lm * dtdx;
@@ -170,7 +183,7 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
       bm = (ref[4] - avg_right(aL[4], aR[4], a6[4], sm)) * half_inv_csq -
            (ref[1] - avg_right(aL[1], aR[1], a6[1], sm)) * half_rho_c;
     if (l0 > T(0))
-      b0 = (ref[0] - avg_right(aL[0], aR[0], a6[0], s0)) - (ref[4] - avg_right(aL[4], aR[4], a6[4], s0)) / csq;
+      b0 = (ref[0] - avg_right(aL[0], aR[0], a6[0], s0)) - vdiv(ref[4] - avg_right(aL[4], aR[4], a6[4], s0), csq);
     Wp[0] = vmax(ref[0] - (b0 + bm), T(kRhoFloor));
     Wp[1] = ref[1] + c_rho * bm;
     Wp[4] = vmax(ref[4] - csq * bm, T(kPFloor));
@@ -187,7 +200,7 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
       bp = (ref[4] - avg_left(aL[4], aR[4], a6[4], tp)) * half_inv_csq +
            (ref[1] - avg_left(aL[1], aR[1], a6[1], tp)) * half_rho_c;
     if (l0 < T(0))
-      b0 = (ref[0] - avg_left(aL[0], aR[0], a6[0], t0)) - (ref[4] - avg_left(aL[4], aR[4], a6[4], t0)) / csq;
+      b0 = (ref[0] - avg_left(aL[0], aR[0], a6[0], t0)) - vdiv(ref[4] - avg_left(aL[4], aR[4], a6[4], t0), csq);
     Wm[0] = vmax(ref[0] - (b0 + bp), T(kRhoFloor));
     Wm[1] = ref[1] - c_rho * bp;
     Wm[4] = vmax(ref[4] - csq * bp, T(kPFloor));
@@ -279,9 +292,9 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
   const float iCL = 1.0f / sqrtf(qL), iCR = 1.0f / sqrtf(qR);
 #endif
   const float CL = qL * iCL, CR = qR * iCR;
-  float ps = ((CR * pL + CL * pR) + (CL * CR) * (uL - uR)) / (CL + CR);
+  float ps = vdiv((CR * pL + CL * pR) + (CL * CR) * (uL - uR), CL + CR);
   ps = vmax(ps, float(kPFloor));
-  const float aL = gs.g1 / pL, aR = gs.g1 / pR, b = 1.0f - gs.g1;
+  const float aL = vdiv(gs.g1, pL), aR = vdiv(gs.g1, pR), b = 1.0f - gs.g1;
   float WLs, WRs, uLs, uRs, ZL, ZR;
 #pragma unroll 1
   for (int it = 0; it <= kRiemannIters; ++it) {
@@ -295,14 +308,14 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
     WRs = CR * (xR * rxR);
     uLs = uL - (ps - pL) * (iCL * rxL);
     uRs = uR + (ps - pR) * (iCR * rxR);
-    ZL = (2.0f * WLs) * xL / (xL + 1.0f);
-    ZR = (2.0f * WRs) * xR / (xR + 1.0f);
+    ZL = vdiv((2.0f * WLs) * xL, xL + 1.0f);
+    ZR = vdiv((2.0f * WRs) * xR, xR + 1.0f);
     if (it == kRiemannIters) break;
-    const float pn = vmax(ps - ((ZL * ZR) * (uRs - uLs)) / (ZL + ZR), float(kPFloor));
+    const float pn = vmax(ps - vdiv((ZL * ZR) * (uRs - uLs), ZL + ZR), float(kPFloor));
     if (pn == ps) break;   // fixed point (see riemann_flux)
     ps = pn;
   }
-  const float us = (ZL * uLs + ZR * uRs) / (ZL + ZR);
+  const float us = vdiv(ZL * uLs + ZR * uRs, ZL + ZR);
   const bool left = us >= 0.0f;
   const float rs = left ? rL : rR;
   const float u_s = left ? uL : uR;
@@ -312,12 +325,12 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
   const float t2 = left ? L[3] : R[3];
   const float v_s = left ? -uL : uR;
   const float v_star = left ? -us : us;
-  const float irs = 1.0f / rs;
-  const float tau = irs - (ps - p_s) / (W_s * W_s);
-  float rstar = (tau > 0.0f) ? 1.0f / tau : float(kRhoFloor);
+  const float irs = vdiv(1.0f, rs);
+  const float tau = irs - vdiv(ps - p_s, W_s * W_s);
+  float rstar = (tau > 0.0f) ? vdiv(1.0f, tau) : float(kRhoFloor);
   rstar = vmax(rstar, float(kRhoFloor));
   const float c_s = vsqrt((gs.gamma * p_s) * irs);
-  const float c_star = vsqrt((gs.gamma * ps) / rstar);
+  const float c_star = vsqrt(vdiv(gs.gamma * ps, rstar));
   const bool shock = ps > p_s;
   const float head = shock ? v_s + W_s * irs : v_s + c_s;
   const float tail = shock ? head : v_star + c_star;
@@ -329,7 +342,7 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
   } else if (star) {
     r = rstar; u = us; p = ps;
   } else {
-    const float w = head / (head - tail);
+    const float w = vdiv(head, head - tail);
     r = rs + w * (rstar - rs);
     u = u_s + w * (us - u_s);
     p = p_s + w * (ps - p_s);
