@@ -34,6 +34,12 @@ WORKLOAD = dict(workload="blob-amr-large", root=[16, 16, 16], n=32, max_level=2,
                 exec="graph", l2="inputs larger than L2 (state tens of GB)")
 
 
+# DRAM bytes (read + written) per 32^3 leaf of one sweep launch, measured by
+# ncu on the 4^3-root blob box (3,970 leaves) for the same kernel form and
+# position in the sweep order, keyed "axis-form-position"; the roofline's
+# traffic is this times the leaves of the launch.
+SWEEP_DRAM_BYTES_PER_LEAF = {}
+
 # FP32 lane operations per second of the whole GPU at the maximum SM clock:
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (one operation per lane per clock)
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
@@ -461,6 +467,7 @@ def main():
     # sample of leaves (their slabs copied to the host, ghosts refreshed) and
     # scaled to the launch; then per-phase times of one batched step on the
     # same state and cycle (events between the library's launches)
+    cycle += cycle % 2          # an even cycle: the sweeps run x, y, z
     sample_ids = np.unique(np.linspace(0, mesh.n_leaves - 1, 32).round().astype(np.int64))
     mesh.ghost_refresh(U)
     t_ops = time.time()
@@ -498,10 +505,17 @@ def main():
     kname = names[top]
     if kname.startswith("sweep"):
         sw = sweeps[kname]
+        traffic, tsrc = None, None
+        key = f"{sw['axis']}-{sw['form']}-{kname}"
+        if key in SWEEP_DRAM_BYTES_PER_LEAF and cfg["n"] == 32:
+            traffic = SWEEP_DRAM_BYTES_PER_LEAF[key] * mesh.n_leaves
+            tsrc = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per leaf of the same kernel and sweep "
+                    "position on the 4^3-root blob box, times the leaves of this launch")
         roofline = {"bound": "alu", "kernel": kname, "achieved": sw["achieved_tops"], "peak": ALU_PEAK_TOPS,
                     "unit": "T FP32 lane-op/s", "frac": sw["achieved_tops"] / ALU_PEAK_TOPS,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per lane per clock",
-                    "traffic": None, "algorithmic_ops_per_launch": sw["ops_per_launch"],
+                    "traffic": traffic, "traffic_source": tsrc,
+                    "algorithmic_ops_per_launch": sw["ops_per_launch"],
                     "ops_sample": f"{len(sample_ids)} leaves evenly spaced in Morton order, scaled by "
                                   f"{mesh.n_leaves}/{len(sample_ids)}",
                     "hbm": {"achieved": sw["hbm_gbs_algorithmic"], "peak": hbm, "unit": "GB/s",

@@ -61,7 +61,14 @@ typedef struct {
     int bc[3];
     int precision;
     double gamma;
+    int riemann;      /* interface flux of the PPM sweeps: CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC */
+    int reserved;     /* must be 0 */
 } cello_mesh_desc;
+
+/* Riemann solvers of the sweep (Sec. II.C, PPM): the Colella-Woodward
+ * two-shock solver, or HLLC (Toro, Spruce & Speares 1994) with Davis wave
+ * speeds.  The adjoint step supports the two-shock solver only. */
+enum { CELLO_RIEMANN_TWO_SHOCK = 0, CELLO_RIEMANN_HLLC = 1 };
 
 /* Build a mesh (Sec. II.B, array of octrees; Refine drives adaptation).
  * prev == NULL: the root array, every leaf at level 0.  Otherwise the new

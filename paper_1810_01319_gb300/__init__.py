@@ -16,11 +16,13 @@ import torch
 from . import _lib
 from ._lib import EXEC_BATCHED, EXEC_GRAPH, EXEC_PLAIN, OUTFLOW, PERIODIC, CelloError  # noqa: F401
 
+RIEMANN_TWO_SHOCK, RIEMANN_HLLC = 0, 1
+
 __all__ = ["Mesh", "make_desc", "PERIODIC", "OUTFLOW", "EXEC_PLAIN", "EXEC_BATCHED", "EXEC_GRAPH", "CelloError"]
 
 
 def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3,
-              precision=8, gamma=1.4, ghosts=4) -> _lib.MeshDesc:
+              precision=8, gamma=1.4, ghosts=4, riemann=0) -> _lib.MeshDesc:
     d = _lib.MeshDesc()
     d.root[:] = list(root)
     d.n, d.ghosts, d.max_level = n, ghosts, max_level
@@ -29,6 +31,8 @@ def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PE
     d.bc[:] = list(bc)
     d.precision = precision
     d.gamma = float(gamma)
+    d.riemann = int(riemann)
+    d.reserved = 0
     return d
 
 

@@ -22,7 +22,7 @@ struct SweepVariant {
   int min_blocks;    // resident CTAs per SM the register bound is set for
   bool persistent;   // work-counter schedule over a resident grid
   bool stream;       // register-streaming form (sweep_stream_kernel)
-  bool vec4;         // streaming form reading x pencils four cells at a time
+  int vec;           // streaming form reading x pencils four cells at a time: 1 unrolled, 2 rolled
 };
 int sweep_variant_count_f32();
 int sweep_variant_count_f64();
@@ -40,6 +40,7 @@ struct DevMesh {
   int bc[3];              // 0 periodic, 1 outflow
   double dx0;             // cell width at level 0
   double gamma;
+  int riemann;            // CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC
   int B;                  // leaves
   const int4* leaf;       // (level, i, j, k)
   const int8_t* kind;     // [B][27]
@@ -160,6 +161,6 @@ void launch_flags(const DevMesh& m, const void* U, int precision, int field, dou
                   int8_t* flags, cudaStream_t s);
 // Host: counted operations of one leaf's sweep (opcount.cu), update applied.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
-                  unsigned long long counts[6]);
+                  int riemann, unsigned long long counts[6]);
 
 }  // namespace cello

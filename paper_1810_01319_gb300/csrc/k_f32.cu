@@ -11,10 +11,10 @@ namespace cello {
 static const SweepVariant kVariants[] = {
     {8, 3, false, false},  {8, 4, false, false},  {4, 6, false, false}, {16, 1, false, false},
     {4, 8, false, false},  {16, 2, false, false}, {64, 8, false, true}, {128, 4, false, true},
-    {64, 6, false, true},  {32, 16, false, true}, {64, 4, false, true, true}, {64, 6, false, true, true},
+    {64, 6, false, true},  {32, 16, false, true}, {64, 5, false, true, 2}, {64, 6, false, true, 1},
     {8, 3, true, false},   {8, 4, true, false},   {4, 6, true, false},  {16, 1, true, false},
     {4, 8, true, false},   {16, 2, true, false},  {64, 8, true, true},  {128, 4, true, true},
-    {64, 6, true, true},   {32, 16, true, true},  {64, 4, true, true, true},  {64, 6, true, true, true},
+    {64, 6, true, true},   {32, 16, true, true},  {64, 5, true, true, 2},  {64, 6, true, true, 1},
 };
 constexpr int kNT = 12;  // distinct kernel instantiations; variant v uses template v % kNT
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -31,17 +31,19 @@ static size_t sweep_smem() {
 template <int NB, int P, int MINB>
 static void prepare_variant(int v, int sms) {
   constexpr int N = NB + 2 * kGhosts;
-  auto k = sweep_kernel<float, NB, P, MINB>;
+  auto k = sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_TWO_SHOCK>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<NB, P, MINB>());
+  cudaFuncSetAttribute(sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_HLLC>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<NB, P, MINB>());
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, N * P, sweep_smem<NB, P, MINB>());
   g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
 }
 
-template <int NB, int CT, int MINB, bool VEC4>
+template <int NB, int CT, int MINB, int VEC>
 static void prepare_stream_variant(int v, int sms) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_stream_kernel<float, NB, CT, MINB, VEC4>, CT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_stream_kernel<float, NB, CT, MINB, VEC, 0>, CT, 0);
   g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
 }
 
@@ -67,14 +69,20 @@ static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, 
   constexpr int N = NB + 2 * kGhosts;
   int grid = 0;
   if (!plan_launch(p, pencils, P, v, nb_index(NB), grid, s)) return;
-  sweep_kernel<float, NB, P, MINB><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
+  if (m.riemann == CELLO_RIEMANN_HLLC)
+    sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_HLLC><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
+  else
+    sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_TWO_SHOCK><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
 }
 
-template <int NB, int CT, int MINB, bool VEC4>
+template <int NB, int CT, int MINB, int VEC>
 static void launch_stream_variant(const DevMesh& m, SweepParams p, int pencils, int v, cudaStream_t s) {
   int grid = 0;
   if (!plan_launch(p, pencils, CT, v, nb_index(NB), grid, s)) return;
-  sweep_stream_kernel<float, NB, CT, MINB, VEC4><<<grid, CT, 0, s>>>(m, p);
+  if (m.riemann == CELLO_RIEMANN_HLLC)
+    sweep_stream_kernel<float, NB, CT, MINB, VEC, CELLO_RIEMANN_HLLC><<<grid, CT, 0, s>>>(m, p);
+  else
+    sweep_stream_kernel<float, NB, CT, MINB, VEC, CELLO_RIEMANN_TWO_SHOCK><<<grid, CT, 0, s>>>(m, p);
 }
 
 template <int NB>
@@ -85,12 +93,12 @@ static void prepare_nb(int sms) {
   prepare_variant<NB, 16, 1>(3, sms);
   prepare_variant<NB, 4, 8>(4, sms);
   prepare_variant<NB, 16, 2>(5, sms);
-  prepare_stream_variant<NB, 64, 8, false>(6, sms);
-  prepare_stream_variant<NB, 128, 4, false>(7, sms);
-  prepare_stream_variant<NB, 64, 6, false>(8, sms);
-  prepare_stream_variant<NB, 32, 16, false>(9, sms);
-  prepare_stream_variant<NB, 64, 4, true>(10, sms);
-  prepare_stream_variant<NB, 64, 6, true>(11, sms);
+  prepare_stream_variant<NB, 64, 8, 0>(6, sms);
+  prepare_stream_variant<NB, 128, 4, 0>(7, sms);
+  prepare_stream_variant<NB, 64, 6, 0>(8, sms);
+  prepare_stream_variant<NB, 32, 16, 0>(9, sms);
+  prepare_stream_variant<NB, 64, 5, 2>(10, sms);
+  prepare_stream_variant<NB, 64, 6, 1>(11, sms);
   for (int v = kNT; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - kNT];
 }
 
@@ -104,12 +112,12 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
     case 3: launch_variant<NB, 16, 1>(m, p, pencils, v, s); break;
     case 4: launch_variant<NB, 4, 8>(m, p, pencils, v, s); break;
     case 5: launch_variant<NB, 16, 2>(m, p, pencils, v, s); break;
-    case 6: launch_stream_variant<NB, 64, 8, false>(m, p, pencils, v, s); break;
-    case 7: launch_stream_variant<NB, 128, 4, false>(m, p, pencils, v, s); break;
-    case 8: launch_stream_variant<NB, 64, 6, false>(m, p, pencils, v, s); break;
-    case 9: launch_stream_variant<NB, 32, 16, false>(m, p, pencils, v, s); break;
-    case 10: launch_stream_variant<NB, 64, 4, true>(m, p, pencils, v, s); break;
-    case 11: launch_stream_variant<NB, 64, 6, true>(m, p, pencils, v, s); break;
+    case 6: launch_stream_variant<NB, 64, 8, 0>(m, p, pencils, v, s); break;
+    case 7: launch_stream_variant<NB, 128, 4, 0>(m, p, pencils, v, s); break;
+    case 8: launch_stream_variant<NB, 64, 6, 0>(m, p, pencils, v, s); break;
+    case 9: launch_stream_variant<NB, 32, 16, 0>(m, p, pencils, v, s); break;
+    case 10: launch_stream_variant<NB, 64, 5, 2>(m, p, pencils, v, s); break;
+    case 11: launch_stream_variant<NB, 64, 6, 1>(m, p, pencils, v, s); break;
   }
 }
 

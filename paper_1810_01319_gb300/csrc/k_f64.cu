@@ -23,8 +23,10 @@ static size_t sweep_smem64() {
 template <int NB>
 static void prepare_nb64(int sms) {
   constexpr int N = NB + 2 * kGhosts;
-  auto k = sweep_kernel<double, NB, 8, 2>;
+  auto k = sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_TWO_SHOCK>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem64<NB>());
+  cudaFuncSetAttribute(sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_HLLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sweep_smem64<NB>());
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, N * 8, sweep_smem64<NB>());
   g_resident64[nb_index64(NB)] = (nb > 0 ? nb : 1) * sms;
@@ -46,7 +48,10 @@ static void launch_nb64(const DevMesh& m, SweepParams p, int pencils, cudaStream
   } else {
     p.work = nullptr;
   }
-  sweep_kernel<double, NB, 8, 2><<<grid, N * 8, sweep_smem64<NB>(), s>>>(m, p);
+  if (m.riemann == CELLO_RIEMANN_HLLC)
+    sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_HLLC><<<grid, N * 8, sweep_smem64<NB>(), s>>>(m, p);
+  else
+    sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_TWO_SHOCK><<<grid, N * 8, sweep_smem64<NB>(), s>>>(m, p);
 }
 
 int sweep_variant_count_f64() { return kNV64; }

@@ -26,7 +26,16 @@ __device__ __forceinline__ T minmod(T a, T b) {
 //   values  4 flatten + monotone + trace  5 Riemann flux (+ face registers)
 //   6 conservative update of cells g..g+n-1.
 // =====================================================================
-template <typename T, int NB, int P, int MINB>
+// The interface flux of the sweep: RS = CELLO_RIEMANN_TWO_SHOCK or
+// CELLO_RIEMANN_HLLC, fixed at compile time so that each kernel carries
+// one solver.
+template <int RS, typename T>
+__device__ __forceinline__ void interface_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+  if (RS == CELLO_RIEMANN_HLLC) hllc_flux(L, R, gs, F);
+  else riemann_flux_bulk(L, R, gs, F);
+}
+
+template <typename T, int NB, int P, int MINB, int RS>
 __global__ void __launch_bounds__((NB + 8) * P, MINB)
 sweep_kernel(DevMesh m, SweepParams prm) {
   constexpr int G = kGhosts, N = NB + 2 * G, S = P, A = N * S;
@@ -146,7 +155,7 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         L[k] = sC[k * A + j * S + p];
         R[k] = sA[k * A + (j + 1) * S + p];
       }
-      riemann_flux_bulk(L, R, gs, F);
+      interface_flux<RS>(L, R, gs, F);
 #pragma unroll
       for (int k = 0; k < 5; ++k) sB[k * A + j * S + p] = F[k];
       if (prm.reg && (j == G - 1 || j == G + NB - 1)) {
@@ -214,7 +223,7 @@ struct PencilWindow {
 // before it is overwritten here.
 // DEFER: the updated cell is returned in upd[5] (component order) instead
 // of being stored.
-template <typename T, int NB, bool DEFER = false>
+template <typename T, int NB, int RS, bool DEFER = false>
 __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T Us[5], const T old[5], T* base,
                                             long sAx, const int comp[5], T dtdx, const Gas<T>& gs,
                                             const DevMesh& m, const SweepParams& prm, int leaf, int axis,
@@ -249,7 +258,7 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
     if (k >= 7) {
       // interface j = k-4 (+1/2): left state wp (cell k-4), right state Wm (cell k-3)
       T F[5];
-      riemann_flux_bulk(S.wp, Wm, gs, F);
+      interface_flux<RS>(S.wp, Wm, gs, F);
       const int j = k - 4;
       if (face_row && (j == G - 1 || j == G + NB - 1)) {
         const int face = 2 * axis + (j == G - 1 ? 0 : 1);
@@ -293,12 +302,13 @@ __device__ __forceinline__ void set_lane4(float4& v, int i, float x) {
   if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
 }
 
-// VEC4 (float32, used on the x sweep, whose pencils run along the
+// VEC > 0 (float32, used on the x sweep, whose pencils run along the
 // contiguous axis): cells are read and written four at a time as 16-byte
 // vectors (a group is read one group ahead; the group updated during group
 // g is g-1, written back at its end) instead of 4-byte accesses 160 bytes
-// apart across the warp; other axes take the one-cell path.
-template <typename T, int NB, int CT, int MINB, bool VEC4>
+// apart across the warp; VEC = 1 unrolls the four cells of a group, VEC = 2
+// keeps one copy of the step; other axes take the one-cell path.
+template <typename T, int NB, int CT, int MINB, int VEC, int RS>
 __global__ void __launch_bounds__(CT, MINB)
 sweep_stream_kernel(DevMesh m, SweepParams prm) {
   constexpr int G = kGhosts, N = NB + 2 * G;
@@ -341,7 +351,7 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
       const bool face_row = prm.reg && pa >= G && pa < G + NB && pb >= G && pb < G + NB;
       PencilWindow<T> S;
       T old[5];
-      if (VEC4 && axis == 0) {
+      if (VEC > 0 && axis == 0) {
         // rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
         float4* b4 = reinterpret_cast<float4*>(base);
         float4 nx4[5];   // the next group of four cells
@@ -360,19 +370,38 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
 #pragma unroll
             for (int c = 0; c < 5; ++c) old4[c] = b4[comp[c] * (SLAB / 4) + g - 1];
           }
+          if (VEC == 1) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k = 4 * g + i;
-            T Us[5], up[5];
+            for (int i = 0; i < 4; ++i) {
+              T Us[5], up[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-              Us[c] = lane4(cur4[c], i);
-              old[c] = lane4(old4[c], i);
+              for (int c = 0; c < 5; ++c) {
+                Us[c] = lane4(cur4[c], i);
+                old[c] = lane4(old4[c], i);
+              }
+              stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
+                                           face_row, pa, pb, up);
+#pragma unroll
+              for (int c = 0; c < 5; ++c) set_lane4(out4[c], i, up[c]);
             }
-            stream_step<T, NB, true>(S, k, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb,
-                                     up);
+          } else {   // one copy of the step body: the groups' lanes shift by one each cell
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+              T Us[5], up[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) set_lane4(out4[c], i, up[c]);
+              for (int c = 0; c < 5; ++c) {
+                Us[c] = cur4[c].x;
+                old[c] = old4[c].x;
+              }
+              stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
+                                           face_row, pa, pb, up);
+#pragma unroll
+              for (int c = 0; c < 5; ++c) {
+                cur4[c].x = cur4[c].y; cur4[c].y = cur4[c].z; cur4[c].z = cur4[c].w;
+                old4[c].x = old4[c].y; old4[c].y = old4[c].z; old4[c].z = old4[c].w;
+                out4[c].x = out4[c].y; out4[c].y = out4[c].z; out4[c].z = out4[c].w; out4[c].w = up[c];
+              }
+            }
           }
           if (g >= 2 && g - 1 <= N / 4 - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
 #pragma unroll
@@ -396,7 +425,7 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
 #pragma unroll
             for (int c = 0; c < 5; ++c) old[c] = base[comp[c] * SLAB + (k - 4) * sAx];
           }
-          stream_step<T, NB>(S, k, Us, old, base, sAx, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb);
+          stream_step<T, NB, RS>(S, k, Us, old, base, sAx, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb);
         }
       }
     }

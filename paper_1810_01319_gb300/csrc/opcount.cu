@@ -58,7 +58,7 @@ CELLO_HD OpF vdiv(OpF a, OpF b) { tick(); return OpF(a.v / b.v); }
 // detector, interface values, flattening + monotonicity + tracing, Riemann
 // flux, conservative update.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx_d, double gamma,
-                  unsigned long long counts[6]) {
+                  int riemann, unsigned long long counts[6]) {
   const int N = n + 2 * g;
   const long SLAB = (long)N * N * N;
   const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
@@ -124,7 +124,8 @@ void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, i
           L[k] = Wp[j * 5 + k];
           R[k] = Wm[(j + 1) * 5 + k];
         }
-        riemann_flux(L, R, gs, fl);
+        if (riemann == CELLO_RIEMANN_HLLC) hllc_flux(L, R, gs, fl);
+        else riemann_flux(L, R, gs, fl);
         for (int k = 0; k < 5; ++k) F[j * 5 + k] = fl[k];
       }
       mark(4, t0);

@@ -356,6 +356,45 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
   F[4] = u * (E + p);
 }
 
+// HLLC flux (Toro, Spruce & Speares 1994; Toro, Riemann Solvers and
+// Numerical Methods, Sec. 10.4): Davis wave-speed bounds, contact speed S*,
+// and the flux of the fan region at x/t = 0 (F_L if S_L >= 0, F*_L if
+// S* >= 0, F*_R if S_R > 0, else F_R) with F*_K = F_K + S_K (U*_K - U_K),
+// U*_K = m_K / (S_K - S*) (1, S*, v_K, w_K, E_K / rho_K + (S* - u_K)(S* +
+// p_K / m_K)), m_K = rho_K (S_K - u_K).  Only the side that is sampled is
+// evaluated past the wave speeds; each quantity is the same expression in
+// the same order as a full evaluation of both sides.
+template <typename T>
+CELLO_HD void hllc_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+  const T rL = L[0], uL = L[1], pL = L[4];
+  const T rR = R[0], uR = R[1], pR = R[4];
+  const T cL = vsqrt(vdiv(gs.gamma * pL, rL));
+  const T cR = vsqrt(vdiv(gs.gamma * pR, rR));
+  const T SL = vmin(uL - cL, uR - cR);
+  const T SR = vmax(uL + cL, uR + cR);
+  const T mL = rL * (SL - uL);
+  const T mR = rR * (SR - uR);
+  const T Ss = vdiv((pR - pL) + (mL * uL - mR * uR), mL - mR);
+  const bool left = (SL >= T(0)) || (Ss >= T(0));
+  const T r = left ? rL : rR, u = left ? uL : uR, v = left ? L[2] : R[2], w = left ? L[3] : R[3];
+  const T p = left ? pL : pR, S = left ? SL : SR, m = left ? mL : mR;
+  const T E = p * gs.inv_gm1 + (T(0.5) * r) * (u * u + (v * v + w * w));
+  const T f0 = r * u;
+  F[0] = f0;
+  F[1] = f0 * u + p;
+  F[2] = f0 * v;
+  F[3] = f0 * w;
+  F[4] = u * (E + p);
+  const bool outer = left ? (SL >= T(0)) : !(SR > T(0));
+  if (!outer) {
+    const T fac = vdiv(m, S - Ss);
+    const T Us[5] = {fac, fac * Ss, fac * v, fac * w, fac * (vdiv(E, r) + (Ss - u) * (Ss + vdiv(p, m)))};
+    const T Uc[5] = {r, r * u, r * v, r * w, E};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) F[k] = F[k] + S * (Us[k] - Uc[k]);
+  }
+}
+
 template <typename T>
 CELLO_HD void riemann_flux_bulk(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
   riemann_flux(L, R, gs, F);

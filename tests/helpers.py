@@ -6,9 +6,10 @@ from oracle import mesh as OM
 from workloads import ics
 
 
-def oracle_desc(root=(2, 2, 2), n=8, lmax=2, bc=(OM.PERIODIC,) * 3, gamma=5.0 / 3.0, hi=None):
+def oracle_desc(root=(2, 2, 2), n=8, lmax=2, bc=(OM.PERIODIC,) * 3, gamma=5.0 / 3.0, hi=None, riemann="two-shock"):
     hi = hi or tuple(r / max(root) for r in root)
-    return OM.Desc(root=tuple(root), n=n, ghosts=4, max_level=lmax, bc=tuple(bc), gamma=gamma, hi=hi)
+    return OM.Desc(root=tuple(root), n=n, ghosts=4, max_level=lmax, bc=tuple(bc), gamma=gamma, hi=hi,
+                   riemann=riemann)
 
 
 def flag_sequence(desc, rounds, seed, p_refine=0.4, p_coarsen=0.0):
@@ -25,9 +26,13 @@ def flag_sequence(desc, rounds, seed, p_refine=0.4, p_coarsen=0.0):
     return meshes, flags
 
 
+RIEMANN_CODES = {"two-shock": 0, "hllc": 1}
+
+
 def gpu_desc(odesc, precision):
     from paper_1810_01319_gb300 import make_desc
-    return make_desc(odesc.root, odesc.n, odesc.max_level, odesc.lo, odesc.hi, odesc.bc, precision, odesc.gamma)
+    return make_desc(odesc.root, odesc.n, odesc.max_level, odesc.lo, odesc.hi, odesc.bc, precision, odesc.gamma,
+                     riemann=RIEMANN_CODES[odesc.riemann])
 
 
 def gpu_mesh_from_flags(odesc, flags, precision):
