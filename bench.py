@@ -38,7 +38,8 @@ WORKLOAD = dict(workload="blob-amr-large", root=[16, 16, 16], n=32, max_level=2,
 # ncu on the 4^3-root blob box (3,970 leaves) for the same kernel form and
 # position in the sweep order, keyed "axis-form-position"; the roofline's
 # traffic is this times the leaves of the launch.
-SWEEP_DRAM_BYTES_PER_LEAF = {}
+SWEEP_DRAM_BYTES_PER_LEAF = {"x-streaming-vec4-sweep_1": 2.548e6, "y-streaming-sweep_2": 2.291e6,
+                             "z-streaming-sweep_3": 1.831e6}
 
 # FP32 lane operations per second of the whole GPU at the maximum SM clock:
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (one operation per lane per clock)
@@ -299,21 +300,23 @@ def host_bytes_available():
     return avail or 0
 
 
-def e2e_host_buffers(mesh, U, cfg, dt, steps, stream, log):
+def e2e_host_buffers(cfg, steps, stream, log):
+    """End to end through the public API with the state in host memory, on
+    the 8^3-root blob box (same blob density): the 16^3-root state (138 GB)
+    cannot be held page-locked on the host next to its working copy.  Run
+    before the headline workload is built, so that the device holds only
+    this box."""
     from paper_1810_01319_gb300 import EXEC_GRAPH
-    state_bytes = U.numel() * U.element_size()
     room = host_bytes_available()
-    workload = cfg["workload"]
-    m2 = None
-    if room < 2 * state_bytes + (32 << 30):
-        sub = dict(cfg, root=[8, 8, 8], blobs=max(1, cfg["blobs"] // 8))
-        m2, U2 = build_workload(sub, 4, log=lambda *a: None)
-        if room < 2 * U2.numel() * U2.element_size() + (16 << 30):
-            log(f"[bench] e2e skipped: {room / 2**30:.0f} GiB of host memory available")
-            return {"value": None, "unit": UNIT, "skipped": f"host memory ({room / 2**30:.0f} GiB available)"}
-        m2.autotune(U2)
-        m2.set_exec(EXEC_GRAPH)
-        mesh, U, workload = m2, U2, "blob-amr 8^3 roots of 32^3, 64 blobs, level 2"
+    sub = dict(cfg, root=[8, 8, 8], blobs=max(1, cfg["blobs"] // 8))
+    mesh, U = build_workload(sub, 4, log=lambda *a: None)
+    workload = "blob-amr 8^3 roots of 32^3, 64 blobs, level 2"
+    if room < 2 * U.numel() * U.element_size() + (16 << 30):
+        log(f"[bench] e2e skipped: {room / 2**30:.0f} GiB of host memory available")
+        return {"value": None, "unit": UNIT, "skipped": f"host memory ({room / 2**30:.0f} GiB available)"}
+    mesh.autotune(U)
+    mesh.set_exec(EXEC_GRAPH)
+    m2 = mesh
     cells = mesh.n_leaves * cfg["n"] ** 3
     state_bytes = U.numel() * U.element_size()
     # page-locked in place (the caching pinned allocator would round the
@@ -419,6 +422,15 @@ def main():
     build.build()
     from paper_1810_01319_gb300 import _lib  # noqa: F401  (fails loudly if the library is missing)
 
+    # end to end through the public API with the state in host memory: every
+    # step copies the whole state from page-locked host memory to the device,
+    # runs the step (dt in, dt_next and totals out), and copies the state and
+    # the step's result back, read by the host before the next step
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_host_buffers(cfg, args.steps, torch.cuda.current_stream(), log)
+        torch.cuda.empty_cache()
+
     t_setup = time.time()
     mesh, U = build_workload(cfg, 4, log=log)
     log(f"[bench] workload ready in {time.time() - t_setup:.1f}s: {mesh.n_leaves} leaves, "
@@ -496,7 +508,8 @@ def main():
         t = prof[1 + k] / 1e3
         v = variant[order[k]]
         sweeps[f"sweep_{k + 1}"] = {
-            "axis": "xyz"[order[k]], "variant": v, "form": "streaming" if v % 12 >= 6 else "shared-memory",
+            "axis": "xyz"[order[k]], "variant": v,
+            "form": ("streaming-vec4" if v % 12 >= 10 else "streaming") if v % 12 >= 6 else "shared-memory",
             "ms": prof[1 + k],
             "ops_per_launch": ops_launch, "ops_per_updated_cell": float(ops[k].sum() / swept_cells[k]),
             "ops_by_phase_per_updated_cell": {p: float(ops[k][i] / swept_cells[k]) for i, p in enumerate(phase_names)},
@@ -529,15 +542,6 @@ def main():
                     "algorithmic_bytes_per_launch": alg_bytes[kname], "sweeps": sweeps,
                     "phase_ms": dict(zip(names, prof))}
 
-    # end to end through the public API with the state in host memory: every
-    # step copies the whole state from pinned host memory to the device, runs
-    # the step (dt in, dt_next and totals out), and copies the state and the
-    # step's result back to pinned host memory, read by the host before the
-    # next step.  At full size when the host has room for a pinned copy of
-    # the state (with a wide margin), else on the 8^3-root blob box.
-    e2e = None
-    if not args.no_e2e:
-        e2e = e2e_host_buffers(mesh, U, cfg, dt, args.steps, stream, log)
 
     # FP64 plain per-block path against FP32 batched on the 8^3-root blob box
     # (64 blobs, same blob density): the metric's comparison
