@@ -36,6 +36,9 @@ EPS_SHOCK = 0.33     # CW84 shock-detector threshold on the relative pressure ju
 OMEGA1 = 0.75        # CW84 flattening: ratio offset
 OMEGA2 = 10.0        # CW84 flattening: ratio slope
 N_RIEMANN = 5        # fixed Newton iterations of the two-shock solver, no early exit
+EPS_STEEP = 0.01     # CW84 contact steepening: least relative density jump
+ETA1, ETA2 = 20.0, 0.05   # CW84 contact steepening: eta = clamp(ETA1 (eta~ - ETA2), 0, 1)
+K0_STEEP = 0.1       # CW84 gas-dynamics condition: steepen where the density jump dominates
 SIXTH = 1.0 / 6.0
 TWO_THIRDS = 2.0 / 3.0
 GHOSTS = 4           # the PPM stencil below reaches 4 cells on each side
@@ -300,10 +303,34 @@ def hllc_flux(WL, WR, gamma):
 RIEMANN = {"two-shock": riemann_flux, "hllc": hllc_flux}
 
 
-def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock"):
+def steepening_eta(rm2, rm1, r0, rp1, rp2, pm1, pp1, gamma):
+    """Contact-steepening weight of a cell (Colella & Woodward 1984, Sec. 1,
+    eqs. 1.14-1.17 on a uniform grid, and the gas-dynamics condition of
+    Sec. 3, eq. 3.2) from the densities of cells j-2 .. j+2 and the pressures
+    of cells j-1, j+1: with D_c = rho_{c+1} - 2 rho_c + rho_{c-1},
+    eta~ = -(D_{j+1} - D_{j-1}) / (6 (rho_{j+1} - rho_{j-1})), set to 0 where
+    D_{j+1} D_{j-1} > 0, where |rho_{j+1} - rho_{j-1}| < EPS_STEEP
+    min(|rho_{j+1}|, |rho_{j-1}|), or where gamma K0 |rho_{j+1} - rho_{j-1}| /
+    min(rho_{j+1}, rho_{j-1}) < |p_{j+1} - p_{j-1}| / min(p_{j+1}, p_{j-1});
+    eta = clamp(ETA1 (eta~ - ETA2), 0, 1)."""
+    Dm = (r0 - 2.0 * rm1) + rm2
+    Dp = (rp2 - 2.0 * rp1) + r0
+    drho = rp1 - rm1
+    off = ((Dp * Dm > 0.0)
+           | (drho.abs() - EPS_STEEP * torch.minimum(rp1.abs(), rm1.abs()) < 0.0)
+           | (((gamma * K0_STEEP) * drho.abs()) / torch.minimum(rp1, rm1)
+              < (pp1 - pm1).abs() / torch.minimum(pp1, pm1)))
+    safe = torch.where(off, torch.ones_like(drho), drho)
+    eta_t = torch.where(off, torch.zeros_like(drho), -(Dp - Dm) / (6.0 * safe))
+    return torch.clamp(torch.clamp(ETA1 * (eta_t - ETA2), max=1.0), min=0.0)
+
+
+def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock", steepen=False):
     """Fluxes at the n+1 interfaces between cells c and c+1, c = 3 .. N-5, of
     pencils of length N = n + 8 (last tensor dim).  Uc = (rho, m_n, m_t1,
-    m_t2, E) tensors; riemann names the interface solver."""
+    m_t2, E) tensors; riemann names the interface solver; steepen applies
+    contact steepening to the density edge values (before flattening and the
+    monotonicity constraints, as in CW84)."""
     N = Uc[0].shape[-1]
     W = primitives(*Uc, gamma)
     p, un = W[4], W[1]
@@ -320,6 +347,13 @@ def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock"):
     for q in range(5):
         l = ai[q][..., 1:N - 5]
         r = ai[q][..., 2:N - 4]
+        if steepen and q == 0:                                                              # cells 3..N-4
+            rho = W[0]
+            eta = steepening_eta(rho[..., 1:N - 5], rho[..., 2:N - 4], rho[..., 3:N - 3], rho[..., 4:N - 2],
+                                 rho[..., 5:N - 1], p[..., 2:N - 4], p[..., 4:N - 2], gamma)
+            dmm, dmp = dm[0][..., 1:N - 5], dm[0][..., 3:N - 3]                             # slopes of j-1, j+1
+            l = l * (1.0 - eta) + (rho[..., 2:N - 4] + 0.5 * dmm) * eta
+            r = r * (1.0 - eta) + (rho[..., 4:N - 2] - 0.5 * dmp) * eta
         l = f * Wc[q] + (1.0 - f) * l
         r = f * Wc[q] + (1.0 - f) * r
         l, r = monotonize(Wc[q], l, r)
@@ -357,7 +391,8 @@ def sweep(U, mesh: Mesh, axis: int, dt: float, rows):
     comp = AXIS_COMPONENTS[axis]
     V = U.movedim(dim, -1)
     dtdx = dtdx_of_leaves(mesh, dt).view(B, 1, 1, 1)
-    F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma, mesh.desc.riemann)
+    F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma, mesh.desc.riemann,
+                      mesh.desc.steepen)
     (a0, a1), (b0, b1) = rows
     V2 = V.clone()
     for q in range(5):

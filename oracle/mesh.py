@@ -52,6 +52,7 @@ class Desc:
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
     gamma: float = 1.4
     riemann: str = "two-shock"   # interface flux: "two-shock" (CW84) or "hllc"
+    steepen: bool = False        # CW84 contact steepening of the density edge values
 
     def dx(self, level: int) -> float:
         """Cell width at a level (cells are cubes; checked in Mesh)."""

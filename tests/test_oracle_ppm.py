@@ -206,3 +206,66 @@ def test_hllc_fan_satisfies_the_jump_conditions():
             b = SR * h["UR"][k] - SL * h["UL"][k] - (h["FR"][k] - h["FL"][k])
             sc = (SR * h["UR"][k]).abs() + (SL * h["UL"][k]).abs() + h["FR"][k].abs() + h["FL"][k].abs() + 1.0
             assert float(((a - b).abs() / sc).max()) < 1e-12, k
+
+
+# ---------------------------------------------------------- contact steepening
+def _eta(rho, p, gamma=1.4):
+    N = rho.shape[-1]
+    return H.steepening_eta(rho[..., 0:N - 4], rho[..., 1:N - 3], rho[..., 2:N - 2], rho[..., 3:N - 1],
+                            rho[..., 4:N], p[..., 1:N - 3], p[..., 3:N - 1], gamma)   # cells 2..N-3
+
+
+def test_steepening_switches_on_at_a_contact_only():
+    N = 40
+    rho = torch.ones(N, dtype=torch.float64)
+    rho[20:] = 0.125
+    p = torch.ones(N, dtype=torch.float64)
+    eta = _eta(rho, p)
+    on = torch.nonzero(eta).flatten() + 2
+    assert on.tolist() == [19, 20] and torch.all(eta[on - 2] == 1.0)
+    # a pressure jump as large as the density jump (a shock): off (gas-dynamics condition)
+    p2 = p.clone()
+    p2[20:] = 0.1
+    assert torch.all(_eta(rho, p2) == 0.0)
+    # a density jump below the relative threshold: off
+    rho3 = torch.ones(N, dtype=torch.float64)
+    rho3[20:] = 1.005
+    assert torch.all(_eta(rho3, p) == 0.0)
+
+
+def test_steepening_is_off_on_quadratics():
+    """D_{j+1} = D_{j-1} on a quadratic, so eta~ = 0 and the edge values are
+    untouched: the fluxes equal those without steepening bit for bit."""
+    x = torch.arange(40, dtype=torch.float64)
+    rho = (1.0 + 0.01 * x + 0.0003 * x * x).view(1, 40)
+    p = torch.ones_like(rho)
+    assert torch.all(_eta(rho, p) == 0.0)
+    u = 0.3 * torch.ones_like(rho)
+    Uc = (rho, rho * u, 0 * rho, 0 * rho, p / 0.4 + 0.5 * rho * u * u)
+    dtdx = torch.full((1, 1), 0.2, dtype=torch.float64)
+    F0 = H.pencil_fluxes(Uc, dtdx, 1.4, steepen=False)
+    F1 = H.pencil_fluxes(Uc, dtdx, 1.4, steepen=True)
+    for a, b in zip(F0, F1):
+        assert torch.equal(a, b)
+
+
+def test_steepened_fluxes_are_mirror_symmetric_on_a_smeared_contact():
+    """Mirror symmetry of the pencil fluxes (F0, F2, F3, F4 change sign, F1
+    does not) with steepening active on a contact spread over three cells,
+    where the neighbours' limited slopes are not zero."""
+    rho = torch.tensor([1.0] * 18 + [0.97, 0.6, 0.2, 0.14] + [0.125] * 18, dtype=torch.float64).view(1, 40)
+    p = torch.ones_like(rho)
+    eta = _eta(rho, p)
+    dm = H.limited_slope(rho[..., :-2], rho[..., 1:-1], rho[..., 2:])
+    on = torch.nonzero(eta[0] > 0).flatten() + 2
+    assert len(on) > 0 and any(float(dm[0, c - 2]) != 0.0 or float(dm[0, c]) != 0.0 for c in on.tolist())
+    u = 0.2 * torch.ones_like(rho)
+    v = 0.1 * torch.ones_like(rho)
+
+    def fluxes(r, un):
+        Uc = (r, r * un, r * v, 0 * r, p / 0.4 + 0.5 * r * (un * un + v * v))
+        return H.pencil_fluxes(Uc, torch.full((1, 1), 0.3, dtype=torch.float64), 1.4, steepen=True)
+    F = fluxes(rho, u)
+    Fm = fluxes(rho.flip(-1), -u)
+    for k, sgn in zip(range(5), (-1, 1, -1, -1, -1)):
+        assert torch.equal(Fm[k].flip(-1), sgn * F[k]), k

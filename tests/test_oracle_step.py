@@ -279,3 +279,51 @@ def test_sod_with_hllc_against_exact_solution():
         re, _, _ = exact.sample((x - 0.5) / T, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
         errs.append(np.abs(rho - re).mean())
     assert errs[0] < 0.01 and errs[1] < errs[0] / 2 ** 0.6, errs
+
+
+def _contact_run(steepen, steps=40):
+    """A density step (contact: uniform p = 1, u = 0.5) advected across a
+    periodic x box of 4 x 16 cells."""
+    d = M.Desc(root=(4, 1, 1), n=16, ghosts=4, max_level=0, hi=(1.0, 0.25, 0.25), gamma=1.4, steepen=steepen)
+    mesh = M.root_mesh(d)
+    x, _, _ = ics.cell_centres(mesh.leaves, d.root, d.n, d.ghosts, d.lo, d.hi)
+    rho = torch.where((x > 0.25) & (x < 0.5), torch.full_like(x, 1.0), torch.full_like(x, 0.125))
+    U = ics.conserved(rho, 0.5 * torch.ones_like(x), 0 * x, 0 * x, torch.ones_like(x), 1.4)
+    dts = [0.004] * steps
+    U1, _ = H.run(U, mesh, steps, 0.4, dts=dts)
+    r = torch.cat([_interior(mesh, U1)[b, 0, 0, 0, :] for b in range(4)])
+    xc = (torch.arange(64, dtype=torch.float64) + 0.5) / 64
+    shift = 0.5 * 0.004 * steps
+    exact = torch.where(((xc - shift) % 1.0 > 0.25) & ((xc - shift) % 1.0 < 0.5), 1.0, 0.125)
+    return r, exact
+
+
+def test_contact_steepening_sharpens_an_advected_contact():
+    r0, exact = _contact_run(False)
+    r1, _ = _contact_run(True)
+    mid0 = int(((r0 > 0.2) & (r0 < 0.9)).sum())
+    mid1 = int(((r1 > 0.2) & (r1 < 0.9)).sum())
+    assert mid1 < mid0, (mid0, mid1)
+    assert float((r1 - exact).abs().mean()) < float((r0 - exact).abs().mean())
+    # mass is conserved either way (periodic box)
+    assert abs(float(r1.sum()) - float(r0.sum())) < 1e-12 * float(r0.sum())
+
+
+def test_steepening_keeps_uniform_states_and_mirror_symmetry():
+    d = M.Desc(root=(2, 2, 2), n=8, ghosts=4, max_level=0, bc=(M.PERIODIC, M.OUTFLOW, M.PERIODIC), gamma=1.4,
+               steepen=True)
+    mesh = M.root_mesh(d)
+    U = _state(mesh, "uniform", rho=1.3, vel=(0.3, -0.2, 0.1), p=0.7)
+    U1, _ = H.run(U, mesh, 3, 0.4)
+    assert torch.equal(_interior(mesh, U1), _interior(mesh, U))
+    d2 = M.Desc(root=(4, 1, 1), n=16, ghosts=4, max_level=0, hi=(1.0, 0.25, 0.25),
+                bc=(M.OUTFLOW, M.PERIODIC, M.PERIODIC), gamma=1.4, steepen=True)
+    mesh = M.root_mesh(d2)
+    U = _state(mesh, "sod", x0=0.4)
+    Um = U.flip(0).flip(-1).clone()
+    Um[:, 1] = -Um[:, 1]
+    A, dts = H.run(U, mesh, 10, 0.4)
+    Bm, _ = H.run(Um, mesh, 10, 0.4, dts=dts)
+    Bb = Bm.flip(0).flip(-1).clone()
+    Bb[:, 1] = -Bb[:, 1]
+    assert torch.equal(_interior(mesh, A), _interior(mesh, Bb))
