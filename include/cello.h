@@ -62,12 +62,13 @@ typedef struct {
     int precision;
     double gamma;
     int riemann;      /* interface flux of the PPM sweeps: CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC */
-    int reserved;     /* must be 0 */
+    int steepening;   /* 1: contact steepening of the density edge values (Colella & Woodward 1984), 0: off */
 } cello_mesh_desc;
 
 /* Riemann solvers of the sweep (Sec. II.C, PPM): the Colella-Woodward
  * two-shock solver, or HLLC (Toro, Spruce & Speares 1994) with Davis wave
- * speeds.  The adjoint step supports the two-shock solver only. */
+ * speeds.  The adjoint step supports the two-shock solver without contact
+ * steepening only. */
 enum { CELLO_RIEMANN_TWO_SHOCK = 0, CELLO_RIEMANN_HLLC = 1 };
 
 /* Build a mesh (Sec. II.B, array of octrees; Refine drives adaptation).

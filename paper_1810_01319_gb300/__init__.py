@@ -22,7 +22,7 @@ __all__ = ["Mesh", "make_desc", "PERIODIC", "OUTFLOW", "EXEC_PLAIN", "EXEC_BATCH
 
 
 def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3,
-              precision=8, gamma=1.4, ghosts=4, riemann=0) -> _lib.MeshDesc:
+              precision=8, gamma=1.4, ghosts=4, riemann=0, steepening=0) -> _lib.MeshDesc:
     d = _lib.MeshDesc()
     d.root[:] = list(root)
     d.n, d.ghosts, d.max_level = n, ghosts, max_level
@@ -32,7 +32,7 @@ def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PE
     d.precision = precision
     d.gamma = float(gamma)
     d.riemann = int(riemann)
-    d.reserved = 0
+    d.steepening = int(steepening)
     return d
 
 

@@ -22,7 +22,7 @@ struct SweepVariant {
   int min_blocks;    // resident CTAs per SM the register bound is set for
   bool persistent;   // work-counter schedule over a resident grid
   bool stream;       // register-streaming form (sweep_stream_kernel)
-  int vec;           // streaming form reading x pencils four cells at a time: 1 unrolled, 2 rolled
+  int vec;           // streaming form moving x pencils four cells at a time: 1 registers, 3 staged by cp.async
 };
 int sweep_variant_count_f32();
 int sweep_variant_count_f64();
@@ -41,6 +41,7 @@ struct DevMesh {
   double dx0;             // cell width at level 0
   double gamma;
   int riemann;            // CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC
+  int steepen;            // contact steepening of the density edge values
   int B;                  // leaves
   const int4* leaf;       // (level, i, j, k)
   const int8_t* kind;     // [B][27]
@@ -161,6 +162,6 @@ void launch_flags(const DevMesh& m, const void* U, int precision, int field, dou
                   int8_t* flags, cudaStream_t s);
 // Host: counted operations of one leaf's sweep (opcount.cu), update applied.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
-                  int riemann, unsigned long long counts[6]);
+                  int riemann, int steepen, unsigned long long counts[6]);
 
 }  // namespace cello

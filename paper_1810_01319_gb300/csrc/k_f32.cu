@@ -11,10 +11,10 @@ namespace cello {
 static const SweepVariant kVariants[] = {
     {8, 3, false, false},  {8, 4, false, false},  {4, 6, false, false}, {16, 1, false, false},
     {4, 8, false, false},  {16, 2, false, false}, {64, 8, false, true}, {128, 4, false, true},
-    {64, 6, false, true},  {32, 16, false, true}, {64, 5, false, true, 2}, {64, 6, false, true, 1},
+    {64, 6, false, true},  {32, 16, false, true}, {64, 8, false, true, 3}, {64, 6, false, true, 1},
     {8, 3, true, false},   {8, 4, true, false},   {4, 6, true, false},  {16, 1, true, false},
     {4, 8, true, false},   {16, 2, true, false},  {64, 8, true, true},  {128, 4, true, true},
-    {64, 6, true, true},   {32, 16, true, true},  {64, 5, true, true, 2},  {64, 6, true, true, 1},
+    {64, 6, true, true},   {32, 16, true, true},  {64, 8, true, true, 3},  {64, 6, true, true, 1},
 };
 constexpr int kNT = 12;  // distinct kernel instantiations; variant v uses template v % kNT
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -22,28 +22,45 @@ static int g_resident[3][kNV];   // resident CTAs per GPU by [n index][variant],
 
 static int nb_index(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
 
-template <int NB, int P, int MINB>
-static size_t sweep_smem() {
+// Shared memory of the shared-memory form: 21 arrays of N x P values, 24
+// with contact steepening (weight and two steepened edge values).
+template <int NB, int P, int RS>
+static constexpr size_t sweep_smem() {
   constexpr int N = NB + 2 * kGhosts;
-  return sizeof(float) * 21 * N * P;
+  return sizeof(float) * ((RS & 2) ? 24 : 21) * N * P;
+}
+
+template <int NB, int P, int MINB, int RS>
+static void set_smem_attr() {
+  cudaFuncSetAttribute(sweep_kernel<float, NB, P, MINB, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sweep_smem<NB, P, RS>());
 }
 
 template <int NB, int P, int MINB>
 static void prepare_variant(int v, int sms) {
   constexpr int N = NB + 2 * kGhosts;
-  auto k = sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_TWO_SHOCK>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<NB, P, MINB>());
-  cudaFuncSetAttribute(sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_HLLC>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<NB, P, MINB>());
+  set_smem_attr<NB, P, MINB, 0>();
+  set_smem_attr<NB, P, MINB, 1>();
+  set_smem_attr<NB, P, MINB, 2>();
+  set_smem_attr<NB, P, MINB, 3>();
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, N * P, sweep_smem<NB, P, MINB>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<float, NB, P, MINB, 0>, N * P,
+                                                sweep_smem<NB, P, 0>());
   g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
+}
+
+// Dynamic shared memory of the streaming form: the staged form keeps three
+// groups of four cells of five fields per thread.
+template <int CT, int VEC>
+static constexpr size_t stream_smem() {
+  return VEC == 3 ? sizeof(float4) * 3 * 5 * CT : 0;
 }
 
 template <int NB, int CT, int MINB, int VEC>
 static void prepare_stream_variant(int v, int sms) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_stream_kernel<float, NB, CT, MINB, VEC, 0>, CT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_stream_kernel<float, NB, CT, MINB, VEC, 0>, CT,
+                                                stream_smem<CT, VEC>());
   g_resident[nb_index(NB)][v] = (nb > 0 ? nb : 1) * sms;
 }
 
@@ -69,20 +86,25 @@ static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, 
   constexpr int N = NB + 2 * kGhosts;
   int grid = 0;
   if (!plan_launch(p, pencils, P, v, nb_index(NB), grid, s)) return;
-  if (m.riemann == CELLO_RIEMANN_HLLC)
-    sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_HLLC><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
-  else
-    sweep_kernel<float, NB, P, MINB, CELLO_RIEMANN_TWO_SHOCK><<<grid, N * P, sweep_smem<NB, P, MINB>(), s>>>(m, p);
+  switch (method_code(m.riemann, m.steepen)) {
+    case 0: sweep_kernel<float, NB, P, MINB, 0><<<grid, N * P, sweep_smem<NB, P, 0>(), s>>>(m, p); break;
+    case 1: sweep_kernel<float, NB, P, MINB, 1><<<grid, N * P, sweep_smem<NB, P, 1>(), s>>>(m, p); break;
+    case 2: sweep_kernel<float, NB, P, MINB, 2><<<grid, N * P, sweep_smem<NB, P, 2>(), s>>>(m, p); break;
+    case 3: sweep_kernel<float, NB, P, MINB, 3><<<grid, N * P, sweep_smem<NB, P, 3>(), s>>>(m, p); break;
+  }
 }
 
 template <int NB, int CT, int MINB, int VEC>
 static void launch_stream_variant(const DevMesh& m, SweepParams p, int pencils, int v, cudaStream_t s) {
   int grid = 0;
   if (!plan_launch(p, pencils, CT, v, nb_index(NB), grid, s)) return;
-  if (m.riemann == CELLO_RIEMANN_HLLC)
-    sweep_stream_kernel<float, NB, CT, MINB, VEC, CELLO_RIEMANN_HLLC><<<grid, CT, 0, s>>>(m, p);
-  else
-    sweep_stream_kernel<float, NB, CT, MINB, VEC, CELLO_RIEMANN_TWO_SHOCK><<<grid, CT, 0, s>>>(m, p);
+  constexpr size_t sh = stream_smem<CT, VEC>();
+  switch (method_code(m.riemann, m.steepen)) {
+    case 0: sweep_stream_kernel<float, NB, CT, MINB, VEC, 0><<<grid, CT, sh, s>>>(m, p); break;
+    case 1: sweep_stream_kernel<float, NB, CT, MINB, VEC, 1><<<grid, CT, sh, s>>>(m, p); break;
+    case 2: sweep_stream_kernel<float, NB, CT, MINB, VEC, 2><<<grid, CT, sh, s>>>(m, p); break;
+    case 3: sweep_stream_kernel<float, NB, CT, MINB, VEC, 3><<<grid, CT, sh, s>>>(m, p); break;
+  }
 }
 
 template <int NB>
@@ -97,7 +119,7 @@ static void prepare_nb(int sms) {
   prepare_stream_variant<NB, 128, 4, 0>(7, sms);
   prepare_stream_variant<NB, 64, 6, 0>(8, sms);
   prepare_stream_variant<NB, 32, 16, 0>(9, sms);
-  prepare_stream_variant<NB, 64, 5, 2>(10, sms);
+  prepare_stream_variant<NB, 64, 8, 3>(10, sms);
   prepare_stream_variant<NB, 64, 6, 1>(11, sms);
   for (int v = kNT; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - kNT];
 }
@@ -116,7 +138,7 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
     case 7: launch_stream_variant<NB, 128, 4, 0>(m, p, pencils, v, s); break;
     case 8: launch_stream_variant<NB, 64, 6, 0>(m, p, pencils, v, s); break;
     case 9: launch_stream_variant<NB, 32, 16, 0>(m, p, pencils, v, s); break;
-    case 10: launch_stream_variant<NB, 64, 5, 2>(m, p, pencils, v, s); break;
+    case 10: launch_stream_variant<NB, 64, 8, 3>(m, p, pencils, v, s); break;
     case 11: launch_stream_variant<NB, 64, 6, 1>(m, p, pencils, v, s); break;
   }
 }

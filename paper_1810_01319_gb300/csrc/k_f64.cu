@@ -14,21 +14,27 @@ static int g_resident64[3];
 
 static int nb_index64(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
 
-template <int NB>
-static size_t sweep_smem64() {
+template <int NB, int RS>
+static constexpr size_t sweep_smem64() {
   constexpr int N = NB + 2 * kGhosts;
-  return sizeof(double) * 21 * N * 8;
+  return sizeof(double) * ((RS & 2) ? 24 : 21) * N * 8;
+}
+
+template <int NB, int RS>
+static void set_smem_attr64() {
+  cudaFuncSetAttribute(sweep_kernel<double, NB, 8, 2, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sweep_smem64<NB, RS>());
 }
 
 template <int NB>
 static void prepare_nb64(int sms) {
   constexpr int N = NB + 2 * kGhosts;
-  auto k = sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_TWO_SHOCK>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem64<NB>());
-  cudaFuncSetAttribute(sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_HLLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sweep_smem64<NB>());
+  set_smem_attr64<NB, 0>();
+  set_smem_attr64<NB, 1>();
+  set_smem_attr64<NB, 2>();
+  set_smem_attr64<NB, 3>();
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, N * 8, sweep_smem64<NB>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<double, NB, 8, 2, 0>, N * 8, sweep_smem64<NB, 0>());
   g_resident64[nb_index64(NB)] = (nb > 0 ? nb : 1) * sms;
 }
 
@@ -48,10 +54,12 @@ static void launch_nb64(const DevMesh& m, SweepParams p, int pencils, cudaStream
   } else {
     p.work = nullptr;
   }
-  if (m.riemann == CELLO_RIEMANN_HLLC)
-    sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_HLLC><<<grid, N * 8, sweep_smem64<NB>(), s>>>(m, p);
-  else
-    sweep_kernel<double, NB, 8, 2, CELLO_RIEMANN_TWO_SHOCK><<<grid, N * 8, sweep_smem64<NB>(), s>>>(m, p);
+  switch (method_code(m.riemann, m.steepen)) {
+    case 0: sweep_kernel<double, NB, 8, 2, 0><<<grid, N * 8, sweep_smem64<NB, 0>(), s>>>(m, p); break;
+    case 1: sweep_kernel<double, NB, 8, 2, 1><<<grid, N * 8, sweep_smem64<NB, 1>(), s>>>(m, p); break;
+    case 2: sweep_kernel<double, NB, 8, 2, 2><<<grid, N * 8, sweep_smem64<NB, 2>(), s>>>(m, p); break;
+    case 3: sweep_kernel<double, NB, 8, 2, 3><<<grid, N * 8, sweep_smem64<NB, 3>(), s>>>(m, p); break;
+  }
 }
 
 int sweep_variant_count_f64() { return kNV64; }

@@ -26,12 +26,14 @@ __device__ __forceinline__ T minmod(T a, T b) {
 //   values  4 flatten + monotone + trace  5 Riemann flux (+ face registers)
 //   6 conservative update of cells g..g+n-1.
 // =====================================================================
-// The interface flux of the sweep: RS = CELLO_RIEMANN_TWO_SHOCK or
-// CELLO_RIEMANN_HLLC, fixed at compile time so that each kernel carries
-// one solver.
+// The method variant of a sweep kernel, fixed at compile time so that each
+// kernel carries only what it uses: RS = solver | 2 * steepening, solver
+// CELLO_RIEMANN_TWO_SHOCK (0) or CELLO_RIEMANN_HLLC (1), steepening 0 or 1.
+__host__ __device__ constexpr int method_code(int riemann, int steepen) { return riemann | (steepen << 1); }
+
 template <int RS, typename T>
 __device__ __forceinline__ void interface_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
-  if (RS == CELLO_RIEMANN_HLLC) hllc_flux(L, R, gs, F);
+  if (RS & 1) hllc_flux(L, R, gs, F);
   else riemann_flux_bulk(L, R, gs, F);
 }
 
@@ -46,6 +48,9 @@ sweep_kernel(DevMesh m, SweepParams prm) {
   T* sB = sA + 5 * A;   // interface values, then fluxes
   T* sC = sB + 5 * A;   // right-edge states
   T* sFT = sC + 5 * A;  // shock detector
+  T* sE = sFT + A;      // contact-steepening weight (RS & 2 only)
+  T* sDL = sE + A;      // density left-edge value of the steepened profile
+  T* sDR = sDL + A;     // density right-edge value of the steepened profile
 
   const Gas<T> gs = Gas<T>::make(m.gamma);
   T* U = static_cast<T*>(prm.U);
@@ -124,6 +129,14 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         sB[k * A + j * S + p] = interface_value(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
                                                 sA[k * A + j * S + p], sA[k * A + (j + 1) * S + p]);
     }
+    if ((RS & 2) && j >= 3 && j <= N - 4) {   // contact steepening of cell j (density)
+      const T* r = sW + p;
+      const T* pr = sW + 4 * A + p;
+      sE[j * S + p] = steepening_eta(r[(j - 2) * S], r[(j - 1) * S], r[j * S], r[(j + 1) * S], r[(j + 2) * S],
+                                     pr[(j - 1) * S], pr[(j + 1) * S], gs.gamma);
+      sDL[j * S + p] = r[(j - 1) * S] + T(0.5) * sA[(j - 1) * S + p];
+      sDR[j * S + p] = r[(j + 1) * S] - T(0.5) * sA[(j + 1) * S + p];
+    }
     __syncthreads();
     // ---- phase 4
     if (j >= 3 && j <= N - 4) {
@@ -137,6 +150,11 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         W[k] = sW[k * A + j * S + p];
         aL[k] = sB[k * A + (j - 1) * S + p];
         aR[k] = sB[k * A + j * S + p];
+        if ((RS & 2) && k == 0) {
+          const T e = sE[j * S + p];
+          aL[0] = aL[0] * (T(1) - e) + sDL[j * S + p] * e;
+          aR[0] = aR[0] * (T(1) - e) + sDR[j * S + p] * e;
+        }
         flatten_monotone(W[k], f, aL[k], aR[k]);
       }
       trace(W, aL, aR, dtdx, gs, Wm, Wp);
@@ -216,6 +234,8 @@ struct PencilWindow {
   T ai[3][5];   // interface values k-4+1/2 .. k-2+1/2
   T wp[5];      // right-edge state of cell k-4 (left state of interface k-4+1/2)
   T fl[5];      // flux at interface k-5+1/2
+  T eta[3];     // contact-steepening weights of cells k-4 .. k-2 (RS & 2)
+  T dr[2];      // density slopes of cells k-4, k-3 (RS & 2)
 };
 
 // One step of the walk: cell k enters as conserved values Us (sweep-local
@@ -237,6 +257,8 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
   }
   if (k >= 4) {
     S.ft[2] = flatten_tilde(S.w[0][4], S.w[1][4], S.w[3][4], S.w[4][4], S.w[1][1], S.w[3][1]);
+    if (RS & 2)
+      S.eta[2] = steepening_eta(S.w[0][0], S.w[1][0], S.w[2][0], S.w[3][0], S.w[4][0], S.w[1][4], S.w[3][4], gs.gamma);
     if (k <= N - 2) {
 #pragma unroll
       for (int c = 0; c < 5; ++c)
@@ -252,6 +274,11 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
     for (int c = 0; c < 5; ++c) {
       aL[c] = S.ai[0][c];
       aR[c] = S.ai[1][c];
+      if ((RS & 2) && c == 0) {   // density of cell k-3: neighbours k-4 (slope dr[0]) and k-2 (slope dm[0])
+        const T e = S.eta[1];
+        aL[0] = aL[0] * (T(1) - e) + (S.w[0][0] + T(0.5) * S.dr[0]) * e;
+        aR[0] = aR[0] * (T(1) - e) + (S.w[2][0] - T(0.5) * S.dm[0][0]) * e;
+      }
       flatten_monotone(S.w[1][c], f, aL[c], aR[c]);
     }
     trace(S.w[1], aL, aR, dtdx, gs, Wm, Wp);
@@ -285,6 +312,10 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
     for (int c = 0; c < 5; ++c) S.wp[c] = Wp[c];
   }
   // slide the windows
+  if (RS & 2) {
+    S.eta[0] = S.eta[1]; S.eta[1] = S.eta[2];
+    S.dr[0] = S.dr[1]; S.dr[1] = S.dm[0][0];
+  }
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     S.w[0][c] = S.w[1][c]; S.w[1][c] = S.w[2][c]; S.w[2][c] = S.w[3][c]; S.w[3][c] = S.w[4][c];
@@ -307,7 +338,8 @@ __device__ __forceinline__ void set_lane4(float4& v, int i, float x) {
 // vectors (a group is read one group ahead; the group updated during group
 // g is g-1, written back at its end) instead of 4-byte accesses 160 bytes
 // apart across the warp; VEC = 1 unrolls the four cells of a group, VEC = 2
-// keeps one copy of the step; other axes take the one-cell path.
+// keeps one copy of the step, VEC = 3 stages the groups in shared memory by
+// asynchronous copies; other axes take the one-cell path.
 template <typename T, int NB, int CT, int MINB, int VEC, int RS>
 __global__ void __launch_bounds__(CT, MINB)
 sweep_stream_kernel(DevMesh m, SweepParams prm) {
@@ -351,7 +383,53 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
       const bool face_row = prm.reg && pa >= G && pa < G + NB && pb >= G && pb < G + NB;
       PencilWindow<T> S;
       T old[5];
-      if (VEC > 0 && axis == 0) {
+      if (VEC == 3 && axis == 0) {
+        // the groups of four cells are copied HBM -> shared memory by cp.async, one group
+        // ahead, into three per-thread slots (current group, the group being updated, the
+        // group in flight); nothing of the pencil is held in registers but the output group
+        extern __shared__ __align__(16) unsigned char stream_raw[];
+        float4* my = reinterpret_cast<float4*>(stream_raw) + t;   // slot s, field c at my[(s * 5 + c) * CT]
+        const float4* b4 = reinterpret_cast<const float4*>(base);
+        constexpr int NG = N / 4;
+        auto issue = [&](int grp, int slot) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&my[(slot * 5 + c) * CT]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(b4 + comp[c] * (SLAB / 4) + grp)
+                         : "memory");
+          }
+        };
+        issue(0, 0);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+#pragma unroll 1
+        for (int g = 0; g < NG; ++g) {
+          if (g + 1 < NG) issue(g + 1, (g + 1) % 3);
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+          asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // group g has landed
+          const float* cur = reinterpret_cast<const float*>(my + (g % 3) * 5 * CT);
+          const float* prv = reinterpret_cast<const float*>(my + ((g + 2) % 3) * 5 * CT);
+          float4 out4[5];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            T Us[5], up[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+              Us[c] = cur[c * CT * 4 + i];
+              old[c] = prv[c * CT * 4 + i];
+            }
+            stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
+                                         face_row, pa, pb, up);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) set_lane4(out4[c], i, up[c]);
+          }
+          if (g >= 2 && g - 1 <= NG - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
+            float4* w4 = reinterpret_cast<float4*>(base);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) w4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
+          }
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      } else if (VEC > 0 && axis == 0) {
         // rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
         float4* b4 = reinterpret_cast<float4*>(base);
         float4 nx4[5];   // the next group of four cells

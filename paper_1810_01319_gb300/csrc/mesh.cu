@@ -173,6 +173,7 @@ struct cello_mesh {
     m.dx0 = (desc.hi[0] - desc.lo[0]) / (desc.root[0] * desc.n);
     m.gamma = desc.gamma;
     m.riemann = desc.riemann;
+    m.steepen = desc.steepening;
     m.B = B;
     m.leaf = d_leaf;
     m.kind = d_kind;
@@ -218,7 +219,7 @@ cello_status check_desc(const cello_mesh_desc* d) {
   if (!(d->gamma > 1.0)) return fail(CELLO_EINVAL, "gamma must exceed 1");
   if (d->riemann != CELLO_RIEMANN_TWO_SHOCK && d->riemann != CELLO_RIEMANN_HLLC)
     return fail(CELLO_EINVAL, "riemann must be CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC");
-  if (d->reserved != 0) return fail(CELLO_EINVAL, "reserved must be 0");
+  if (d->steepening != 0 && d->steepening != 1) return fail(CELLO_EINVAL, "steepening must be 0 or 1");
   double ext[3];
   for (int a = 0; a < 3; ++a) {
     if (d->root[a] < 1 || d->root[a] > 1024) return fail(CELLO_EINVAL, "root blocks per axis must be in [1, 1024]");
@@ -852,8 +853,8 @@ cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, 
                                       void* stream) {
   if (!M || !Un || !lam || !dt) return fail(CELLO_EINVAL, "NULL argument");
   if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
-  if (M->desc.riemann != CELLO_RIEMANN_TWO_SHOCK)
-    return fail(CELLO_EINVAL, "the adjoint step is written for the two-shock Riemann solver");
+  if (M->desc.riemann != CELLO_RIEMANN_TWO_SHOCK || M->desc.steepening)
+    return fail(CELLO_EINVAL, "the adjoint step is written for the two-shock solver without contact steepening");
   return adjoint_step(M, Un, lam, dt, cycle, (cudaStream_t)stream);
 }
 
@@ -972,7 +973,8 @@ cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32
     unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t i = 0; i < count; ++i) {
       const double dtdx = dt / std::ldexp(dx0, -M->leaves[leaf_ids[i]].x);
-      opcount_leaf(U_host + i * slab, d.n, d.ghosts, axis, a0, a1, b0, b1, dtdx, d.gamma, d.riemann, c);
+      opcount_leaf(U_host + i * slab, d.n, d.ghosts, axis, a0, a1, b0, b1, dtdx, d.gamma, d.riemann, d.steepening,
+                   c);
     }
     for (int k = 0; k < 6; ++k) out[oi * 8 + k] = (double)c[k];
     out[oi * 8 + 6] = (double)count * (a1 - a0) * (b1 - b0);

@@ -58,7 +58,7 @@ CELLO_HD OpF vdiv(OpF a, OpF b) { tick(); return OpF(a.v / b.v); }
 // detector, interface values, flattening + monotonicity + tracing, Riemann
 // flux, conservative update.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx_d, double gamma,
-                  int riemann, unsigned long long counts[6]) {
+                  int riemann, int steepen, unsigned long long counts[6]) {
   const int N = n + 2 * g;
   const long SLAB = (long)N * N * N;
   const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
@@ -100,6 +100,13 @@ void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, i
       mark(2, t0);
       t0 = tl_ops;
       for (int j = 3; j <= N - 4; ++j) {
+        OpF sl = OpF(0), sr = OpF(0), e = OpF(0);
+        if (steepen) {
+          e = steepening_eta(W[(j - 2) * 5], W[(j - 1) * 5], W[j * 5], W[(j + 1) * 5], W[(j + 2) * 5],
+                             W[(j - 1) * 5 + 4], W[(j + 1) * 5 + 4], gs.gamma);
+          sl = W[(j - 1) * 5] + OpF(0.5) * dm[(j - 1) * 5];
+          sr = W[(j + 1) * 5] - OpF(0.5) * dm[(j + 1) * 5];
+        }
         const OpF s = W[(j + 1) * 5 + 4] - W[(j - 1) * 5 + 4];
         const OpF fj = ft[j], fm = ft[j - 1], fpp = ft[j + 1];
         const OpF f = (s > OpF(0)) ? vmax(fj, fm) : ((s < OpF(0)) ? vmax(fj, fpp) : fj);
@@ -108,6 +115,10 @@ void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, i
           w[k] = W[j * 5 + k];
           aL[k] = ai[(j - 1) * 5 + k];
           aR[k] = ai[j * 5 + k];
+          if (steepen && k == 0) {
+            aL[0] = aL[0] * (OpF(1) - e) + sl * e;
+            aR[0] = aR[0] * (OpF(1) - e) + sr * e;
+          }
           flatten_monotone(w[k], f, aL[k], aR[k]);
         }
         trace(w, aL, aR, dtdx, gs, m5, p5);

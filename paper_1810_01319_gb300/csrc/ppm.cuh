@@ -129,6 +129,28 @@ CELLO_HD T flatten_tilde(T pm2, T pm1, T pp1, T pp2, T um1, T up1) {
   return shock ? ft : T(0);
 }
 
+// Contact-steepening weight of a cell (Colella & Woodward 1984, Sec. 1 on a
+// uniform grid, with the gas-dynamics condition of their Sec. 3): from the
+// densities of cells j-2 .. j+2 and the pressures of cells j-1, j+1, with
+// second differences D, eta~ = -(D_{j+1} - D_{j-1}) / (6 (rho_{j+1} -
+// rho_{j-1})), zero where the D have one sign, where the density jump is
+// below 1 % or where the relative pressure jump exceeds gamma K0 times the
+// relative density jump; eta = clamp(20 (eta~ - 0.05), 0, 1).
+constexpr double kEpsSteep = 0.01;
+constexpr double kEta1 = 20.0, kEta2 = 0.05;
+constexpr double kK0Steep = 0.1;
+
+template <typename T>
+CELLO_HD T steepening_eta(T rm2, T rm1, T r0, T rp1, T rp2, T pm1, T pp1, T gamma) {
+  const T Dm = (r0 - T(2) * rm1) + rm2;
+  const T Dp = (rp2 - T(2) * rp1) + r0;
+  const T drho = rp1 - rm1;
+  const bool off = (Dp * Dm > T(0)) || (vabs(drho) - T(kEpsSteep) * vmin(vabs(rp1), vabs(rm1)) < T(0)) ||
+                   (vdiv((gamma * T(kK0Steep)) * vabs(drho), vmin(rp1, rm1)) < vdiv(vabs(pp1 - pm1), vmin(pp1, pm1)));
+  const T eta_t = off ? T(0) : vdiv(-(Dp - Dm), T(6) * drho);
+  return vmax(vmin(T(kEta1) * (eta_t - T(kEta2)), T(1)), T(0));
+}
+
 // Flatten towards the cell value, then apply the monotonicity constraints.
 template <typename T>
 CELLO_HD void flatten_monotone(T a, T f, T& aL, T& aR) {

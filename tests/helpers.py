@@ -6,10 +6,11 @@ from oracle import mesh as OM
 from workloads import ics
 
 
-def oracle_desc(root=(2, 2, 2), n=8, lmax=2, bc=(OM.PERIODIC,) * 3, gamma=5.0 / 3.0, hi=None, riemann="two-shock"):
+def oracle_desc(root=(2, 2, 2), n=8, lmax=2, bc=(OM.PERIODIC,) * 3, gamma=5.0 / 3.0, hi=None, riemann="two-shock",
+                steepen=False):
     hi = hi or tuple(r / max(root) for r in root)
     return OM.Desc(root=tuple(root), n=n, ghosts=4, max_level=lmax, bc=tuple(bc), gamma=gamma, hi=hi,
-                   riemann=riemann)
+                   riemann=riemann, steepen=steepen)
 
 
 def flag_sequence(desc, rounds, seed, p_refine=0.4, p_coarsen=0.0):
@@ -32,7 +33,7 @@ RIEMANN_CODES = {"two-shock": 0, "hllc": 1}
 def gpu_desc(odesc, precision):
     from paper_1810_01319_gb300 import make_desc
     return make_desc(odesc.root, odesc.n, odesc.max_level, odesc.lo, odesc.hi, odesc.bc, precision, odesc.gamma,
-                     riemann=RIEMANN_CODES[odesc.riemann])
+                     riemann=RIEMANN_CODES[odesc.riemann], steepening=int(odesc.steepen))
 
 
 def gpu_mesh_from_flags(odesc, flags, precision):
