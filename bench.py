@@ -365,6 +365,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tracers", action="store_true")
     ap.add_argument("--workload", default="blob-amr-large", choices=["blob-amr-large", "sedov-deep"])
     ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
     ap.add_argument("--variants", default="", help="sweep variants x,y,z instead of autotuning (profiling)")
@@ -543,6 +544,44 @@ def main():
                     "phase_ms": dict(zip(names, prof))}
 
 
+    # tracer particles (Sec. III's hydro workload carries tracers): one push of
+    # 2^27 tracers spread uniformly over the box, velocities from the refreshed
+    # state; particle-steps per second
+    tracers = None
+    if not args.no_tracers:
+        npart = 1 << 27
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        pos = torch.rand(3, npart, dtype=torch.float64, device="cuda", generator=gen)
+        leaf = mesh.particles_locate(pos)
+        mesh.ghost_refresh(U)
+        pdt = torch.full((1,), 1e-4, dtype=torch.float64, device="cuda")
+        mesh.particles_push(U, pos, leaf, pdt)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            mesh.particles_push(U, pos, leaf, pdt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / 3
+        # the same tracers grouped by leaf (the paper's per-Block particle batches)
+        order = torch.argsort(leaf.long(), stable=True)
+        pos = pos[:, order].contiguous()
+        leaf = leaf[order].contiguous()
+        del order
+        mesh.particles_push(U, pos, leaf, pdt)
+        a.record(stream)
+        for _ in range(3):
+            mesh.particles_push(U, pos, leaf, pdt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms_sorted = a.elapsed_time(b) / 3
+        tracers = {"particles": npart, "push_ms": pms, "particle_steps_per_s": npart / (pms / 1e3),
+                   "push_ms_grouped_by_leaf": pms_sorted,
+                   "particle_steps_per_s_grouped_by_leaf": npart / (pms_sorted / 1e3),
+                   "order": "uniform random positions; then the same tracers grouped by leaf"}
+        del pos, leaf
+        torch.cuda.empty_cache()
+
     # FP64 plain per-block path against FP32 batched on the 8^3-root blob box
     # (64 blobs, same blob density): the metric's comparison
     fp64 = None
@@ -584,7 +623,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(cfg, leaves=mesh.n_leaves, cells=cells, coarse_fine_faces=mesh.n_coarse_fine,
                                sweep_variant=variant, sweep_variant_ms=variant_ms),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "tracers": tracers,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
                 "hbm_frac_algorithmic": value * 40 / (hbm * 1e9)}
         print(json.dumps(line))

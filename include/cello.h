@@ -215,6 +215,26 @@ cello_status cello_set_sweep_variants(cello_mesh* mesh, const int* variants);
 cello_status cello_autotune(cello_mesh* mesh, void* U, int* variants_out, float* ms_out, int ms_len,
                             void* stream);
 
+/* Tracer particles (Sec. II.B, Fig. 4: Lagrangian particles move between
+ * Blocks; Sec. III: the hydro workload carries tracers).  pos_dev: device
+ * float64 [3][count] (all x, then all y, then all z); leaf_dev: device int32
+ * [count], the index of the containing leaf, -1 for a tracer lost through
+ * an outflow face.  cello_particles_locate writes the containing leaf of
+ * each point (points must lie in the box): the leaf whose Morton key is the
+ * last not above the key of the point's block at max_level.  Call it to
+ * start, and again after every adaptation (leaf indices change). */
+cello_status cello_particles_locate(cello_mesh* mesh, const double* pos_dev, int32_t* leaf_dev, int64_t count,
+                                    void* stream);
+
+/* One tracer step: each live tracer moves by dt (device double) times the
+ * fluid velocity (momentum / density) interpolated trilinearly between the
+ * cell centres of its leaf's padded block, so U's ghosts must be refreshed
+ * (cello_ghost_refresh); then periodic wrap, or loss (leaf -1) through an
+ * outflow face, and the lookup of its (possibly new) leaf.  float64
+ * arithmetic for either state precision. */
+cello_status cello_particles_push(cello_mesh* mesh, const void* U, double* pos_dev, int32_t* leaf_dev,
+                                  int64_t count, const double* dt_dev, void* stream);
+
 /* Algorithmic operation count of the three PPM sweeps of one step (Sec.
  * II.C), the numerator of the sweep kernel's ALU roofline.  Host only, no
  * device work: the sweep's formulas run in float32 through a counting

@@ -195,6 +195,28 @@ class Mesh:
                    "cello_hydro_step_host")
         return float(self._host_out[0]), [float(x) for x in self._host_out[1:]]
 
+    def particles_locate(self, pos, leaf=None, stream=None):
+        """Containing leaf of each tracer: pos a contiguous float64 CUDA tensor
+        [3, P]; returns (or fills) an int32 CUDA tensor [P]."""
+        if pos.dtype != torch.float64 or not pos.is_cuda or not pos.is_contiguous() or pos.dim() != 2 \
+                or pos.shape[0] != 3:
+            raise CelloError("pos must be a contiguous float64 CUDA tensor [3, P]")
+        if leaf is None:
+            leaf = torch.empty(pos.shape[1], dtype=torch.int32, device=pos.device)
+        _lib.check(_lib.lib().cello_particles_locate(self.handle, _ptr(pos), _ptr(leaf), pos.shape[1],
+                                                     _stream(stream)), "cello_particles_locate")
+        return leaf
+
+    def particles_push(self, U, pos, leaf, dt, stream=None):
+        """One tracer step in place (U's ghosts refreshed); dt a float64 CUDA
+        scalar tensor."""
+        self._check_state(U)
+        if pos.dtype != torch.float64 or not pos.is_contiguous() or leaf.dtype != torch.int32 \
+                or leaf.numel() != pos.shape[1]:
+            raise CelloError("pos must be float64 [3, P] and leaf int32 [P]")
+        _lib.check(_lib.lib().cello_particles_push(self.handle, _ptr(U), _ptr(pos), _ptr(leaf), pos.shape[1],
+                                                   _ptr(dt), _stream(stream)), "cello_particles_push")
+
     def check(self) -> int:
         """Read and clear the device error word (waits for the device); raises
         CelloError with CELLO_ENONFINITE if a reduction saw a bad state."""

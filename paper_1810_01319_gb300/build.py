@@ -30,6 +30,7 @@ UNITS = {
     "mesh.cu": [],
     "noalloc.cu": [],
     "opcount.cu": [],
+    "particles.cu": ["-fmad=false"],
 }
 
 

@@ -160,6 +160,12 @@ void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t
 void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);
+// Tracer particles (particles.cu): lookup of the containing leaf, and one push.
+void launch_particles_locate(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3],
+                             const double* pos, int* leaf, long count, cudaStream_t s);
+void launch_particles_push(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3],
+                           const void* U, int precision, double* pos, int* leaf, long count, const double* dt,
+                           cudaStream_t s);
 // Host: counted operations of one leaf's sweep (opcount.cu), update applied.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
                   int riemann, int steepen, unsigned long long counts[6]);

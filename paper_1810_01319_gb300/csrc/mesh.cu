@@ -954,6 +954,23 @@ cello_status cello_hydro_step_host(cello_mesh* M, void* U_host, void* U_dev, dou
   return CELLO_OK;
 }
 
+cello_status cello_particles_locate(cello_mesh* M, const double* pos, int32_t* leaf, int64_t count, void* stream) {
+  if (!M || (count > 0 && (!pos || !leaf)) || count < 0) return fail(CELLO_EINVAL, "NULL argument or negative count");
+  launch_particles_locate(M->dev(), M->d_keys, M->desc.lo, M->desc.hi, pos, leaf, (long)count, (cudaStream_t)stream);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status cello_particles_push(cello_mesh* M, const void* U, double* pos, int32_t* leaf, int64_t count,
+                                  const double* dt, void* stream) {
+  if (!M || !U || !dt || (count > 0 && (!pos || !leaf)) || count < 0)
+    return fail(CELLO_EINVAL, "NULL argument or negative count");
+  launch_particles_push(M->dev(), M->d_keys, M->desc.lo, M->desc.hi, U, M->desc.precision, pos, leaf, (long)count, dt,
+                        (cudaStream_t)stream);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
 cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32_t* leaf_ids, int64_t count,
                                  double dt, int cycle, double* out) {
   if (!M || !U_host || !leaf_ids || !out || count <= 0) return fail(CELLO_EINVAL, "NULL argument or empty sample");
