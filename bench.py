@@ -366,6 +366,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tracers", action="store_true")
+    ap.add_argument("--no-poisson", action="store_true")
     ap.add_argument("--workload", default="blob-amr-large", choices=["blob-amr-large", "sedov-deep"])
     ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
     ap.add_argument("--variants", default="", help="sweep variants x,y,z instead of autotuning (profiling)")
@@ -582,6 +583,34 @@ def main():
         del pos, leaf
         torch.cuda.empty_cache()
 
+    # multigrid Poisson solve (mg0, the self-gravity solver of the paper's
+    # uniform-grid runs) on a uniform 16^3-root mesh of 32^3 blocks: 512^3 cells
+    poisson = None
+    if not args.no_poisson:
+        from paper_1810_01319_gb300 import Mesh, make_desc, PERIODIC
+        pm = Mesh(make_desc([16, 16, 16], 32, 0, (0, 0, 0), (1, 1, 1), (PERIODIC,) * 3, 4, cfg["gamma"]))
+        gen = torch.Generator(device="cuda").manual_seed(11)
+        fsrc = torch.randn(pm.n_leaves, 32, 32, 32, dtype=torch.float64, device="cuda", generator=gen)
+        phi, _ = pm.poisson_solve(fsrc, 1, residuals=False)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        phi, _ = pm.poisson_solve(fsrc, 5, phi=phi, residuals=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        vms = a.elapsed_time(b) / 5
+        _, res = pm.poisson_solve(fsrc, 5, phi=phi, residuals=True)
+        cells = 512 ** 3
+        # algorithmic bytes per V-cycle: on each level four Jacobi sweeps (read
+        # phi and f, write phi: 24 B per cell), the residual restriction (read
+        # phi and f: 16 B) and the prolongation (read and write phi: 16 B);
+        # the levels add 1/7 to the finest
+        alg = 128.0 * cells * 8.0 / 7.0
+        poisson = {"grid": "512^3 (16^3 roots x 32^3, uniform, periodic)", "vcycle_ms": vms,
+                   "residual_reduction_per_cycle": (res[-1] / res[0]) ** (1.0 / (len(res) - 1)),
+                   "hbm_gbs_algorithmic": alg / (vms / 1e3) / 1e9, "hbm_frac": alg / (vms / 1e3) / 1e9 / hbm}
+        del fsrc, phi, pm
+        torch.cuda.empty_cache()
+
     # FP64 plain per-block path against FP32 batched on the 8^3-root blob box
     # (64 blobs, same blob density): the metric's comparison
     fp64 = None
@@ -623,7 +652,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(cfg, leaves=mesh.n_leaves, cells=cells, coarse_fine_faces=mesh.n_coarse_fine,
                                sweep_variant=variant, sweep_variant_ms=variant_ms),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "tracers": tracers,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "tracers": tracers, "poisson": poisson,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
                 "hbm_frac_algorithmic": value * 40 / (hbm * 1e9)}
         print(json.dumps(line))

@@ -235,6 +235,23 @@ cello_status cello_particles_locate(cello_mesh* mesh, const double* pos_dev, int
 cello_status cello_particles_push(cello_mesh* mesh, const void* U, double* pos_dev, int32_t* leaf_dev,
                                   int64_t count, const double* dt_dev, void* stream);
 
+/* Poisson solve, lap(phi) = f (Sec. II.C: Enzo-P's mg0 geometric multigrid
+ * V-cycle, the self-gravity solver of the paper's uniform-grid runs), on a
+ * uniform mesh (every leaf at one level), periodic on every axis, cubic
+ * root array, at most 1024 cells per axis.  f_dev and phi_dev: device
+ * float64 leaf interiors [B][n^3] (no ghosts; x fastest) in leaf order.
+ * The 7-point cell-centred Laplacian; the mean of f is removed first and
+ * the mean of phi last.  cycles V-cycles from phi = 0, each two damped
+ * Jacobi sweeps (w = 6/7) before and after, restriction by the mean of 8
+ * children, trilinear prolongation, coarsening by 2 while the size is even
+ * (50 sweeps on an odd coarsest grid).  resid_host (nullable, host,
+ * `cycles` doubles) receives the max-norm of the residual after each cycle,
+ * and then the call waits for the stream.  The first solve on a mesh
+ * allocates the level arrays (about 4/7 x 3 x 8 bytes per cell), freed with
+ * the mesh.  CELLO_EINVAL on a mesh it does not support. */
+cello_status cello_poisson_solve(cello_mesh* mesh, const double* f_dev, double* phi_dev, int cycles,
+                                 double* resid_host, void* stream);
+
 /* Algorithmic operation count of the three PPM sweeps of one step (Sec.
  * II.C), the numerator of the sweep kernel's ALU roofline.  Host only, no
  * device work: the sweep's formulas run in float32 through a counting

@@ -195,6 +195,21 @@ class Mesh:
                    "cello_hydro_step_host")
         return float(self._host_out[0]), [float(x) for x in self._host_out[1:]]
 
+    def poisson_solve(self, f, cycles=10, phi=None, residuals=True, stream=None):
+        """lap(phi) = f on a uniform periodic mesh by multigrid V-cycles; f a
+        contiguous float64 CUDA tensor [B, n, n, n] of leaf interiors.
+        Returns (phi, residual max-norm after each cycle or None)."""
+        n = self.desc.n
+        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.n_leaves * n ** 3:
+            raise CelloError("f must be a contiguous float64 CUDA tensor [B, n, n, n]")
+        if phi is None:
+            phi = torch.empty_like(f)
+        res = (ctypes.c_double * cycles)() if residuals else None
+        _lib.check(_lib.lib().cello_poisson_solve(self.handle, _ptr(f), _ptr(phi), int(cycles),
+                                                  ctypes.cast(res, ctypes.c_void_p) if res is not None else None,
+                                                  _stream(stream)), "cello_poisson_solve")
+        return phi, (list(res) if res is not None else None)
+
     def particles_locate(self, pos, leaf=None, stream=None):
         """Containing leaf of each tracer: pos a contiguous float64 CUDA tensor
         [3, P]; returns (or fills) an int32 CUDA tensor [P]."""

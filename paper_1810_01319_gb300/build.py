@@ -31,6 +31,7 @@ UNITS = {
     "noalloc.cu": [],
     "opcount.cu": [],
     "particles.cu": ["-fmad=false"],
+    "poisson.cu": ["-fmad=false"],
 }
 
 

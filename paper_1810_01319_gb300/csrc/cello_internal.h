@@ -160,6 +160,11 @@ void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t
 void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);
+// Multigrid Poisson solver (poisson.cu) on the M^3 grid of a uniform periodic mesh.
+struct PoissonScratch;
+void poisson_free(PoissonScratch* p);
+cudaError_t poisson_solve(PoissonScratch** scratch, const DevMesh& m, int M, double h, const double* f_leaves,
+                          double* phi_leaves, int cycles, double* resid_host, cudaStream_t s);
 // Tracer particles (particles.cu): lookup of the containing leaf, and one push.
 void launch_particles_locate(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3],
                              const double* pos, int* leaf, long count, cudaStream_t s);

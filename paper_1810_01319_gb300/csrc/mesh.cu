@@ -154,6 +154,7 @@ struct cello_mesh {
   int sweep_variant[3] = {0, 0, 0};   // per sweep axis; chosen by cello_autotune or set by the caller
   unsigned* d_work = nullptr;      // work counter of the persistent sweep variants
   unsigned* d_err = nullptr;       // error word set by the reduction
+  PoissonScratch* poisson = nullptr;   // multigrid levels, allocated by the first Poisson solve
   double* d_zero = nullptr;        // dt = 0, for timing sweeps without changing the state
   void* adj_scratch = nullptr;   // three states for the adjoint's forward recomputation
   size_t adj_bytes = 0;
@@ -185,6 +186,8 @@ struct cello_mesh {
   }
 
   void release() {
+    poisson_free(poisson);
+    poisson = nullptr;
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     graphs.clear();
     if (capture_stream) cudaStreamDestroy(capture_stream);
@@ -968,6 +971,23 @@ cello_status cello_particles_push(cello_mesh* M, const void* U, double* pos, int
   launch_particles_push(M->dev(), M->d_keys, M->desc.lo, M->desc.hi, U, M->desc.precision, pos, leaf, (long)count, dt,
                         (cudaStream_t)stream);
   CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status cello_poisson_solve(cello_mesh* M, const double* f, double* phi, int cycles, double* resid_host,
+                                 void* stream) {
+  if (!M || !f || !phi || cycles < 1) return fail(CELLO_EINVAL, "NULL argument or cycles < 1");
+  const cello_mesh_desc& d = M->desc;
+  for (int a = 0; a < 3; ++a)
+    if (d.bc[a] != CELLO_PERIODIC || d.root[a] != d.root[0])
+      return fail(CELLO_EINVAL, "the Poisson solver needs a cubic root array, periodic on every axis");
+  const int L = M->leaves[0].x;
+  for (const int4& lf : M->leaves)
+    if (lf.x != L) return fail(CELLO_EINVAL, "the Poisson solver needs a uniform mesh (every leaf at one level)");
+  const long Mg = (long)d.root[0] * (1L << L) * d.n;
+  if (Mg > 1024) return fail(CELLO_EINVAL, "grid too large for the Poisson solver (M > 1024)");
+  const double h = std::ldexp((d.hi[0] - d.lo[0]) / (d.root[0] * d.n), -L);
+  CELLO_CUDA(poisson_solve(&M->poisson, M->dev(), (int)Mg, h, f, phi, cycles, resid_host, (cudaStream_t)stream));
   return CELLO_OK;
 }
 
