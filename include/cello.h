@@ -244,12 +244,16 @@ cello_status cello_particles_push(cello_mesh* mesh, const void* U, double* pos_d
  * the mean of phi last.  cycles V-cycles from phi = 0, each two damped
  * Jacobi sweeps (w = 6/7) before and after, restriction by the mean of 8
  * children, trilinear prolongation, coarsening by 2 while the size is even
- * (50 sweeps on an odd coarsest grid).  resid_host (nullable, host,
+ * (50 sweeps on an odd coarsest grid).  inner = 8: float64 V-cycles;
+ * inner = 4: mixed precision, each cycle a float32 V-cycle on the float64
+ * residual rounded to float32, its result added to the float64 phi (the
+ * same convergence per cycle and float64's attainable accuracy, at float32
+ * cost).  resid_host (nullable, host,
  * `cycles` doubles) receives the max-norm of the residual after each cycle,
  * and then the call waits for the stream.  The first solve on a mesh
  * allocates the level arrays (about 4/7 x 3 x 8 bytes per cell), freed with
  * the mesh.  CELLO_EINVAL on a mesh it does not support. */
-cello_status cello_poisson_solve(cello_mesh* mesh, const double* f_dev, double* phi_dev, int cycles,
+cello_status cello_poisson_solve(cello_mesh* mesh, const double* f_dev, double* phi_dev, int cycles, int inner,
                                  double* resid_host, void* stream);
 
 /* Algorithmic operation count of the three PPM sweeps of one step (Sec.

@@ -115,14 +115,22 @@ def vcycle(phi, f, h):
     return phi
 
 
-def solve(f, h, cycles):
+def solve(f, h, cycles, inner="float64"):
     """V-cycles from phi = 0 on the mean-free f; returns (phi with zero
-    mean, list of the residual max-norms after each cycle)."""
+    mean, list of the residual max-norms after each cycle).  inner =
+    "float32": mixed-precision defect correction, each cycle a float32
+    V-cycle from zero on the float32-rounded float64 residual, its result
+    added to the float64 phi (the attainable accuracy stays float64's: the
+    residual that drives each cycle is computed in float64)."""
     f0 = f - f.mean()
     phi = torch.zeros_like(f0)
     norms = []
     for _ in range(cycles):
-        phi = vcycle(phi, f0, h)
+        if inner == "float64":
+            phi = vcycle(phi, f0, h)
+        else:
+            r = residual(phi, f0, h).to(torch.float32)
+            phi = phi + vcycle(torch.zeros_like(r), r, h).to(torch.float64)
         norms.append(float(residual(phi, f0, h).abs().max()))
     return phi - phi.mean(), norms
 

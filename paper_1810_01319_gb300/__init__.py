@@ -195,9 +195,10 @@ class Mesh:
                    "cello_hydro_step_host")
         return float(self._host_out[0]), [float(x) for x in self._host_out[1:]]
 
-    def poisson_solve(self, f, cycles=10, phi=None, residuals=True, stream=None):
+    def poisson_solve(self, f, cycles=10, phi=None, residuals=True, inner=8, stream=None):
         """lap(phi) = f on a uniform periodic mesh by multigrid V-cycles; f a
-        contiguous float64 CUDA tensor [B, n, n, n] of leaf interiors.
+        contiguous float64 CUDA tensor [B, n, n, n] of leaf interiors; inner
+        8 (float64 cycles) or 4 (float32 cycles on the float64 residual).
         Returns (phi, residual max-norm after each cycle or None)."""
         n = self.desc.n
         if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.n_leaves * n ** 3:
@@ -205,7 +206,7 @@ class Mesh:
         if phi is None:
             phi = torch.empty_like(f)
         res = (ctypes.c_double * cycles)() if residuals else None
-        _lib.check(_lib.lib().cello_poisson_solve(self.handle, _ptr(f), _ptr(phi), int(cycles),
+        _lib.check(_lib.lib().cello_poisson_solve(self.handle, _ptr(f), _ptr(phi), int(cycles), int(inner),
                                                   ctypes.cast(res, ctypes.c_void_p) if res is not None else None,
                                                   _stream(stream)), "cello_poisson_solve")
         return phi, (list(res) if res is not None else None)

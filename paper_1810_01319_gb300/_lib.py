@@ -38,7 +38,7 @@ SIGNATURES = {
     "cello_mesh_from_leaves": (ctypes.c_int, [ctypes.POINTER(MeshDesc), _vp, ctypes.c_int64, ctypes.POINTER(_vp)]),
     "cello_check": (ctypes.c_int, [_vp, _vp]),
     "cello_particles_locate": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
-    "cello_poisson_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
+    "cello_poisson_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "cello_particles_push": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
     "cello_hydro_step_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_int, ctypes.c_double,
                                              _vp, _vp, _vp]),

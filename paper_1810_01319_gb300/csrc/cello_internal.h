@@ -164,7 +164,7 @@ void launch_flags(const DevMesh& m, const void* U, int precision, int field, dou
 struct PoissonScratch;
 void poisson_free(PoissonScratch* p);
 cudaError_t poisson_solve(PoissonScratch** scratch, const DevMesh& m, int M, double h, const double* f_leaves,
-                          double* phi_leaves, int cycles, double* resid_host, cudaStream_t s);
+                          double* phi_leaves, int cycles, int inner, double* resid_host, cudaStream_t s);
 // Tracer particles (particles.cu): lookup of the containing leaf, and one push.
 void launch_particles_locate(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3],
                              const double* pos, int* leaf, long count, cudaStream_t s);

@@ -974,9 +974,10 @@ cello_status cello_particles_push(cello_mesh* M, const void* U, double* pos, int
   return CELLO_OK;
 }
 
-cello_status cello_poisson_solve(cello_mesh* M, const double* f, double* phi, int cycles, double* resid_host,
-                                 void* stream) {
+cello_status cello_poisson_solve(cello_mesh* M, const double* f, double* phi, int cycles, int inner,
+                                 double* resid_host, void* stream) {
   if (!M || !f || !phi || cycles < 1) return fail(CELLO_EINVAL, "NULL argument or cycles < 1");
+  if (inner != 4 && inner != 8) return fail(CELLO_EINVAL, "inner precision must be 4 or 8");
   const cello_mesh_desc& d = M->desc;
   for (int a = 0; a < 3; ++a)
     if (d.bc[a] != CELLO_PERIODIC || d.root[a] != d.root[0])
@@ -987,7 +988,8 @@ cello_status cello_poisson_solve(cello_mesh* M, const double* f, double* phi, in
   const long Mg = (long)d.root[0] * (1L << L) * d.n;
   if (Mg > 1024) return fail(CELLO_EINVAL, "grid too large for the Poisson solver (M > 1024)");
   const double h = std::ldexp((d.hi[0] - d.lo[0]) / (d.root[0] * d.n), -L);
-  CELLO_CUDA(poisson_solve(&M->poisson, M->dev(), (int)Mg, h, f, phi, cycles, resid_host, (cudaStream_t)stream));
+  CELLO_CUDA(poisson_solve(&M->poisson, M->dev(), (int)Mg, h, f, phi, cycles, inner, resid_host,
+                           (cudaStream_t)stream));
   return CELLO_OK;
 }
 

@@ -26,65 +26,86 @@ constexpr int kRedThreads = 256;
 __device__ __forceinline__ long gidx(int x, int y, int z, int M) { return ((long)z * M + y) * M + x; }
 __device__ __forceinline__ int wrapm(int v, int M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
 
-__device__ __forceinline__ double nbsum(const double* p, int x, int y, int z, int M) {
-  const double xm = p[gidx(wrapm(x - 1, M), y, z, M)], xp = p[gidx(wrapm(x + 1, M), y, z, M)];
-  const double ym = p[gidx(x, wrapm(y - 1, M), z, M)], yp = p[gidx(x, wrapm(y + 1, M), z, M)];
-  const double zm = p[gidx(x, y, wrapm(z - 1, M), M)], zp = p[gidx(x, y, wrapm(z + 1, M), M)];
+template <typename T>
+__device__ __forceinline__ T nbsum(const T* p, int x, int y, int z, int M) {
+  const T xm = p[gidx(wrapm(x - 1, M), y, z, M)], xp = p[gidx(wrapm(x + 1, M), y, z, M)];
+  const T ym = p[gidx(x, wrapm(y - 1, M), z, M)], yp = p[gidx(x, wrapm(y + 1, M), z, M)];
+  const T zm = p[gidx(x, y, wrapm(z - 1, M), M)], zp = p[gidx(x, y, wrapm(z + 1, M), M)];
   return ((((xm + xp) + ym) + yp) + zm) + zp;
 }
 
-__global__ void jacobi_kernel(const double* __restrict__ in, double* __restrict__ out, const double* __restrict__ f,
-                              int M, double h2) {
+template <typename T>
+__global__ void jacobi_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ f, int M, T h2) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)M * M * M) return;
   const unsigned u = (unsigned)i, uM = (unsigned)M;   // M^3 <= 2^30: 32-bit index arithmetic
   const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
-  out[i] = (1.0 - kOmega) * in[i] + kOmega * ((nbsum(in, x, y, z, M) - h2 * f[i]) * (1.0 / 6.0));
+  out[i] = T(1.0 - kOmega) * in[i] + T(kOmega) * ((nbsum(in, x, y, z, M) - h2 * f[i]) * T(1.0 / 6.0));
 }
 
 // Coarse right-hand side: mean of the residuals f - lap(phi) of the 8
 // children, in (dz, dy, dx) order.
-__global__ void residual_restrict_kernel(const double* __restrict__ phi, const double* __restrict__ f,
-                                         double* __restrict__ fc, int M, double ih2) {
+template <typename T>
+__global__ void residual_restrict_kernel(const T* __restrict__ phi, const T* __restrict__ f, T* __restrict__ fc,
+                                         int M, T ih2) {
   const int Mc = M / 2;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)Mc * Mc * Mc) return;
   const unsigned u = (unsigned)i, uM = (unsigned)Mc;
   const int X = (int)(u % uM), Y = (int)((u / uM) % uM), Z = (int)(u / (uM * uM));
-  double s = 0.0;
+  T s = T(0);
   bool first = true;
   for (int dz = 0; dz < 2; ++dz)
     for (int dy = 0; dy < 2; ++dy)
       for (int dx = 0; dx < 2; ++dx) {
         const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
         const long o = gidx(x, y, z, M);
-        const double r = f[o] - (nbsum(phi, x, y, z, M) - 6.0 * phi[o]) * ih2;
+        const T r = f[o] - (nbsum(phi, x, y, z, M) - T(6) * phi[o]) * ih2;
         s = first ? r : s + r;
         first = false;
       }
-  fc[i] = s * 0.125;
+  fc[i] = s * T(0.125);
 }
 
 // phi += trilinear prolongation of the coarse error ec.
-__global__ void prolong_add_kernel(const double* __restrict__ ec, double* __restrict__ phi, int M) {
+template <typename T>
+__global__ void prolong_add_kernel(const T* __restrict__ ec, T* __restrict__ phi, int M) {
   const int Mc = M / 2;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long)M * M * M) return;
-  const unsigned u = (unsigned)i, uM = (unsigned)M;   // M^3 <= 2^30: 32-bit index arithmetic
+  const unsigned u = (unsigned)i, uM = (unsigned)M;
   const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
   const int X = x >> 1, Y = y >> 1, Z = z >> 1;
   const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
   const int X1 = wrapm(X + sx, Mc), Y1 = wrapm(Y + sy, Mc), Z1 = wrapm(Z + sz, Mc);
-  const double c00 = 0.75 * ec[gidx(X, Y, Z, Mc)] + 0.25 * ec[gidx(X1, Y, Z, Mc)];
-  const double c10 = 0.75 * ec[gidx(X, Y1, Z, Mc)] + 0.25 * ec[gidx(X1, Y1, Z, Mc)];
-  const double c01 = 0.75 * ec[gidx(X, Y, Z1, Mc)] + 0.25 * ec[gidx(X1, Y, Z1, Mc)];
-  const double c11 = 0.75 * ec[gidx(X, Y1, Z1, Mc)] + 0.25 * ec[gidx(X1, Y1, Z1, Mc)];
-  const double c0 = 0.75 * c00 + 0.25 * c10;
-  const double c1 = 0.75 * c01 + 0.25 * c11;
-  phi[i] = phi[i] + (0.75 * c0 + 0.25 * c1);
+  const T a = T(0.75), q = T(0.25);
+  const T c00 = a * ec[gidx(X, Y, Z, Mc)] + q * ec[gidx(X1, Y, Z, Mc)];
+  const T c10 = a * ec[gidx(X, Y1, Z, Mc)] + q * ec[gidx(X1, Y1, Z, Mc)];
+  const T c01 = a * ec[gidx(X, Y, Z1, Mc)] + q * ec[gidx(X1, Y, Z1, Mc)];
+  const T c11 = a * ec[gidx(X, Y1, Z1, Mc)] + q * ec[gidx(X1, Y1, Z1, Mc)];
+  const T c0 = a * c00 + q * c10;
+  const T c1 = a * c01 + q * c11;
+  phi[i] = phi[i] + (a * c0 + q * c1);
 }
 
-__global__ void fill_kernel(double* p, long count, double v) {
+// Mixed precision: the float64 residual rounded to float32 (the right-hand
+// side of a float32 V-cycle), and the float32 correction added to phi.
+__global__ void residual_f32_kernel(const double* __restrict__ phi, const double* __restrict__ f,
+                                    float* __restrict__ r, int M, double ih2) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)M * M * M) return;
+  const unsigned u = (unsigned)i, uM = (unsigned)M;
+  const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
+  r[i] = (float)(f[i] - (nbsum(phi, x, y, z, M) - 6.0 * phi[i]) * ih2);
+}
+
+__global__ void correct_kernel(double* __restrict__ phi, const float* __restrict__ e, long count) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) phi[i] = phi[i] + (double)e[i];
+}
+
+template <typename T>
+__global__ void fill_kernel(T* p, long count, T v) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) p[i] = v;
 }
@@ -151,32 +172,31 @@ __global__ void leaves_grid_kernel(const int4* leaf, int B, int n, int M, double
 
 unsigned blocks_for(long count) { return (unsigned)((count + 255) / 256); }
 
+template <typename T>
 struct Level {
   int M;
   double h;
-  double *phi, *tmp, *f;
+  T *phi, *tmp, *f;
 };
 
-struct Solver {
-  std::vector<Level> lv;
-  double* partial;
-  int npart;
-  double* scalar;   // [2]: mean, residual max
+template <typename T>
+struct Cycle {
+  std::vector<Level<T>> lv;
   cudaStream_t s;
 
-  void sweeps(Level& L, int count) {
+  void sweeps(Level<T>& L, int count) {
     const long c = (long)L.M * L.M * L.M;
     for (int k = 0; k < count; ++k) {
-      jacobi_kernel<<<blocks_for(c), 256, 0, s>>>(L.phi, L.tmp, L.f, L.M, L.h * L.h);
+      jacobi_kernel<T><<<blocks_for(c), 256, 0, s>>>(L.phi, L.tmp, L.f, L.M, T(L.h * L.h));
       std::swap(L.phi, L.tmp);
     }
   }
 
   void vcycle(int l) {
-    Level& L = lv[l];
+    Level<T>& L = lv[l];
     const long c = (long)L.M * L.M * L.M;
     if (L.M == 1) {
-      fill_kernel<<<1, 32, 0, s>>>(L.phi, 1, 0.0);
+      fill_kernel<T><<<1, 32, 0, s>>>(L.phi, 1, T(0));
       return;
     }
     if (L.M % 2 == 1) {
@@ -184,94 +204,118 @@ struct Solver {
       return;
     }
     sweeps(L, kNu);
-    Level& C = lv[l + 1];
+    Level<T>& C = lv[l + 1];
     const long cc = (long)C.M * C.M * C.M;
-    residual_restrict_kernel<<<blocks_for(cc), 256, 0, s>>>(L.phi, L.f, C.f, L.M, 1.0 / (L.h * L.h));
-    fill_kernel<<<blocks_for(cc), 256, 0, s>>>(C.phi, cc, 0.0);
+    residual_restrict_kernel<T><<<blocks_for(cc), 256, 0, s>>>(L.phi, L.f, C.f, L.M, T(1.0 / (L.h * L.h)));
+    fill_kernel<T><<<blocks_for(cc), 256, 0, s>>>(C.phi, cc, T(0));
     vcycle(l + 1);
-    prolong_add_kernel<<<blocks_for(c), 256, 0, s>>>(C.phi, L.phi, L.M);
+    prolong_add_kernel<T><<<blocks_for(c), 256, 0, s>>>(C.phi, L.phi, L.M);
     sweeps(L, kNu);
-  }
-
-  // scalar[slot] = mean of a (op 0) or max |f - lap(a)| (op 1) on level 0
-  void reduce(const double* a, const double* f, int op, int slot) {
-    const Level& L = lv[0];
-    const long c = (long)L.M * L.M * L.M;
-    reduce_kernel<<<npart, kRedThreads, 0, s>>>(a, f, c, L.M, 1.0 / (L.h * L.h), op, partial);
-    fold_kernel<<<1, kRedThreads, 0, s>>>(partial, npart, op, op == 0 ? 1.0 / (double)c : 1.0, scalar + slot);
   }
 };
 
 }  // namespace
 
-// Scratch of the solver for one mesh: the level arrays, the reduction
-// partials.  Allocated on the first solve, freed with the mesh.
+// Scratch of the solver for one mesh: the level arrays (float64 and, for
+// mixed precision, float32), the reduction partials.  Allocated on the
+// first solve of each kind, freed with the mesh.
 struct PoissonScratch {
-  std::vector<double*> bufs;
+  std::vector<void*> d64, d32;
+  double* red = nullptr;   // 1024 partials + 2 scalars
   ~PoissonScratch() {
-    for (double* p : bufs) cudaFree(p);
+    for (void* p : d64) cudaFree(p);
+    for (void* p : d32) cudaFree(p);
+    if (red) cudaFree(red);
   }
 };
 
 void poisson_free(PoissonScratch* p) { delete p; }
 
+namespace {
+
+// Three arrays per level, for the levels not yet allocated.
+cudaError_t alloc_levels(std::vector<void*>& bufs, const std::vector<int>& sizes, size_t elem) {
+  for (size_t l = bufs.size() / 3; l < sizes.size(); ++l)
+    for (int k = 0; k < 3; ++k) {
+      const int Ml = sizes[l];
+      void* d = nullptr;
+      cudaError_t e = cudaMalloc(&d, elem * (size_t)Ml * Ml * Ml);
+      if (e != cudaSuccess) return e;
+      bufs.push_back(d);
+    }
+  return cudaSuccess;
+}
+
+template <typename T>
+Cycle<T> make_cycle(const std::vector<void*>& bufs, const std::vector<int>& sizes, double h, cudaStream_t s) {
+  Cycle<T> C;
+  C.s = s;
+  for (size_t l = 0; l < sizes.size(); ++l)
+    C.lv.push_back(Level<T>{sizes[l], h * (double)(1L << l), static_cast<T*>(bufs[3 * l]),
+                            static_cast<T*>(bufs[3 * l + 1]), static_cast<T*>(bufs[3 * l + 2])});
+  return C;
+}
+
+// scalar = mean of a (op 0) or max |f - lap(a)| (op 1) on the finest grid
+void reduce_to(const double* a, const double* f, int M, double h, int op, double* red, double* out, cudaStream_t s) {
+  const long c = (long)M * M * M;
+  reduce_kernel<<<1024, kRedThreads, 0, s>>>(a, f, c, M, 1.0 / (h * h), op, red);
+  fold_kernel<<<1, kRedThreads, 0, s>>>(red, 1024, op, op == 0 ? 1.0 / (double)c : 1.0, out);
+}
+
+}  // namespace
+
 cudaError_t poisson_solve(PoissonScratch** scratch, const DevMesh& m, int M, double h, const double* f_leaves,
-                          double* phi_leaves, int cycles, double* resid_host, cudaStream_t s) {
+                          double* phi_leaves, int cycles, int inner, double* resid_host, cudaStream_t s) {
   std::vector<int> sizes;
   for (int Ml = M;; Ml /= 2) {
     sizes.push_back(Ml);
     if (Ml == 1 || Ml % 2 == 1) break;
   }
-  if (!*scratch) {
-    auto* p = new PoissonScratch();
-    for (int Ml : sizes) {
-      const size_t bytes = sizeof(double) * (size_t)Ml * Ml * Ml;
-      for (int k = 0; k < 3; ++k) {
-        double* d = nullptr;
-        cudaError_t e = cudaMalloc(&d, bytes);
-        if (e != cudaSuccess) {
-          delete p;
-          return e;
-        }
-        p->bufs.push_back(d);
-      }
-    }
-    double* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, sizeof(double) * (1024 + 2));
-    if (e != cudaSuccess) {
-      delete p;
-      return e;
-    }
-    p->bufs.push_back(d);
-    *scratch = p;
-  }
-  Solver S;
-  S.s = s;
-  for (size_t l = 0; l < sizes.size(); ++l)
-    S.lv.push_back(Level{sizes[l], h * (double)(1L << l), (*scratch)->bufs[3 * l], (*scratch)->bufs[3 * l + 1],
-                         (*scratch)->bufs[3 * l + 2]});
-  S.partial = (*scratch)->bufs.back();
-  S.npart = 1024;
-  S.scalar = S.partial + 1024;
-  Level& L0 = S.lv[0];
+  if (!*scratch) *scratch = new PoissonScratch();
+  PoissonScratch* P = *scratch;
+  cudaError_t e = alloc_levels(P->d64, inner == 8 ? sizes : std::vector<int>{M}, sizeof(double));
+  if (e == cudaSuccess && inner == 4) e = alloc_levels(P->d32, sizes, sizeof(float));
+  if (e == cudaSuccess && !P->red) e = cudaMalloc(&P->red, sizeof(double) * (1024 + 2));
+  if (e != cudaSuccess) return e;
+  double* scalar = P->red + 1024;
+  // the float64 finest grid: level 0 of the float64 hierarchy
+  double* phi = static_cast<double*>(P->d64[0]);
+  double* tmp = static_cast<double*>(P->d64[1]);
+  double* f = static_cast<double*>(P->d64[2]);
   const long c = (long)M * M * M;
   const long nl = (long)m.B * m.n * m.n * m.n;
-  leaves_grid_kernel<<<blocks_for(nl), 256, 0, s>>>(m.leaf, m.B, m.n, M, const_cast<double*>(f_leaves), L0.f, 1);
-  S.reduce(L0.f, nullptr, 0, 0);
-  add_kernel<<<blocks_for(c), 256, 0, s>>>(L0.f, c, S.scalar, 1.0);
-  fill_kernel<<<blocks_for(c), 256, 0, s>>>(L0.phi, c, 0.0);
+  leaves_grid_kernel<<<blocks_for(nl), 256, 0, s>>>(m.leaf, m.B, m.n, M, const_cast<double*>(f_leaves), f, 1);
+  reduce_to(f, nullptr, M, h, 0, P->red, scalar, s);
+  add_kernel<<<blocks_for(c), 256, 0, s>>>(f, c, scalar, 1.0);
+  fill_kernel<double><<<blocks_for(c), 256, 0, s>>>(phi, c, 0.0);
+  Cycle<double> C64;
+  Cycle<float> C32;
+  if (inner == 8) C64 = make_cycle<double>(P->d64, sizes, h, s);
+  else C32 = make_cycle<float>(P->d32, sizes, h, s);
   for (int k = 0; k < cycles; ++k) {
-    S.vcycle(0);
+    if (inner == 8) {
+      C64.vcycle(0);
+    } else {
+      Level<float>& L = C32.lv[0];
+      residual_f32_kernel<<<blocks_for(c), 256, 0, s>>>(phi, f, L.f, M, 1.0 / (h * h));
+      fill_kernel<float><<<blocks_for(c), 256, 0, s>>>(L.phi, c, 0.0f);
+      C32.vcycle(0);
+      correct_kernel<<<blocks_for(c), 256, 0, s>>>(phi, L.phi, c);
+    }
+    const double* cur = inner == 8 ? C64.lv[0].phi : phi;
     if (resid_host) {
-      S.reduce(L0.phi, L0.f, 1, 1);
-      cudaError_t e = cudaMemcpyAsync(resid_host + k, S.scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+      reduce_to(cur, f, M, h, 1, P->red, scalar + 1, s);
+      e = cudaMemcpyAsync(resid_host + k, scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (e != cudaSuccess) return e;
     }
   }
-  S.reduce(L0.phi, nullptr, 0, 0);
-  add_kernel<<<blocks_for(c), 256, 0, s>>>(L0.phi, c, S.scalar, 1.0);
-  leaves_grid_kernel<<<blocks_for(nl), 256, 0, s>>>(m.leaf, m.B, m.n, M, phi_leaves, L0.phi, 0);
-  cudaError_t e = cudaGetLastError();
+  double* out = inner == 8 ? C64.lv[0].phi : phi;
+  (void)tmp;
+  reduce_to(out, nullptr, M, h, 0, P->red, scalar, s);
+  add_kernel<<<blocks_for(c), 256, 0, s>>>(out, c, scalar, 1.0);
+  leaves_grid_kernel<<<blocks_for(nl), 256, 0, s>>>(m.leaf, m.B, m.n, M, phi_leaves, out, 0);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (resid_host) e = cudaStreamSynchronize(s);
   return e;

@@ -26,6 +26,7 @@ def _uniform(root, n, level):
 
 @pytest.mark.parametrize("root,n,level,cycles", [(2, 16, 1, 8), (3, 16, 0, 6)])
 def test_poisson_matches_oracle(root, n, level, cycles):
+    """float64 cycles: the same arithmetic as the oracle."""
     od, om, flags = _uniform(root, n, level)
     gm = H.gpu_mesh_from_flags(od, flags, 8)
     g = torch.Generator().manual_seed(root * 10 + level)
@@ -52,3 +53,22 @@ def test_poisson_refuses_amr_and_outflow_meshes():
     gm2 = H.gpu_mesh_from_flags(od2, [], 8)
     with pytest.raises(CelloError):
         gm2.poisson_solve(torch.zeros(8, 8, 8, 8, dtype=torch.float64, device="cuda"), 2)
+
+
+@pytest.mark.parametrize("root,n,level", [(2, 16, 1), (3, 16, 0)])
+def test_mixed_precision_poisson(root, n, level):
+    """float32 cycles on the float64 residual: the residual history follows
+    the oracle's mixed-precision cycles (same float32 arithmetic up to the
+    mean removal), and 20 cycles reach the float64 discrete solution."""
+    od, om, flags = _uniform(root, n, level)
+    gm = H.gpu_mesh_from_flags(od, flags, 4)
+    g = torch.Generator().manual_seed(root * 7 + level)
+    f = torch.randn(om.n_leaves, n, n, n, generator=g, dtype=torch.float64)
+    phi, res = gm.poisson_solve(f.cuda().contiguous(), 20, inner=4)
+    h = od.dx(level)
+    po, ro = OP.solve(OP.to_global(om, f), h, 20, inner="float32")
+    p64, _ = OP.solve(OP.to_global(om, f), h, 20)
+    expect = OP.from_global(om, p64)
+    scale = float(expect.abs().max())
+    assert float((phi.cpu() - expect).abs().max()) <= 1e-10 * scale
+    assert np.allclose(res[:6], ro[:6], rtol=1e-3, atol=0)

@@ -80,3 +80,16 @@ def test_global_grid_round_trip_on_a_uniform_mesh():
     V = torch.randn(mesh.n_leaves, 8, 8, 8, dtype=torch.float64)
     G = P.to_global(mesh, V)
     assert G.shape == (32, 32, 32) and torch.equal(P.from_global(mesh, G), V)
+
+
+def test_mixed_precision_cycles_reach_the_float64_solution():
+    """float32 V-cycles on the float64 defect: same convergence factor and the
+    same discrete solution as the float64 cycles, to 1e-10."""
+    for Mn in (16, 24):
+        h = 1.0 / Mn
+        f = _random_f(Mn, Mn + 1)
+        phi, norms = P.solve(f, h, 20, inner="float32")
+        exact = _fft_solve(f, h)
+        assert float((phi - exact).abs().max()) < 1e-10 * float(exact.abs().max()), Mn
+        rates = [b / a for a, b in zip(norms[:6], norms[1:7])]
+        assert max(rates) < 0.35, rates
