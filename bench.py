@@ -79,7 +79,8 @@ def build_workload(cfg, precision, device="cuda", chunk=1024, log=print):
     from workloads import ics
     root, n, lmax = cfg["root"], cfg["n"], cfg["max_level"]
     hi = tuple(r / max(root) for r in root)
-    desc = make_desc(root, n, lmax, (0, 0, 0), hi, (PERIODIC,) * 3, precision, cfg["gamma"])
+    desc = make_desc(root, n, lmax, (0, 0, 0), hi, (PERIODIC,) * 3, precision, cfg["gamma"],
+                     riemann=1 if cfg.get("riemann") == "hllc" else 0, steepening=int(cfg.get("steepening", 0)))
 
     def sample(mesh):
         U = mesh.empty_state(device)
@@ -171,7 +172,8 @@ def oracle_sample(cfg, seconds=15.0):
     from workloads import ics
     r = 2
     od = OM.Desc(root=(r, r, r), n=cfg["n"], ghosts=4, max_level=cfg["max_level"], bc=(OM.PERIODIC,) * 3,
-                 gamma=cfg["gamma"], hi=(1.0, 1.0, 1.0))
+                 gamma=cfg["gamma"], hi=(1.0, 1.0, 1.0), riemann=cfg.get("riemann", "two-shock"),
+                 steepen=bool(cfg.get("steepening", 0)))
     count = max(1, int(round(cfg["blobs"] * (r / cfg["root"][0]) ** 3)))
 
     def st(mesh):
@@ -369,6 +371,8 @@ def main():
     ap.add_argument("--no-poisson", action="store_true")
     ap.add_argument("--workload", default="blob-amr-large", choices=["blob-amr-large", "sedov-deep"])
     ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
+    ap.add_argument("--riemann", default="two-shock", choices=["two-shock", "hllc"])
+    ap.add_argument("--steepening", action="store_true", help="contact steepening of the density edge values")
     ap.add_argument("--variants", default="", help="sweep variants x,y,z instead of autotuning (profiling)")
     ap.add_argument("--abc", type=float, default=0.0,
                     help="amplitude of an ABC flow added to every cell (0: blobs in a medium at rest)")
@@ -395,6 +399,9 @@ def main():
     cfg["root"] = [args.root] * 3
     if args.abc > 0.0:
         cfg["abc"] = args.abc
+    if args.riemann != "two-shock" or args.steepening:
+        cfg["riemann"] = args.riemann
+        cfg["steepening"] = int(args.steepening)
 
     if args.impl == "reference":
         if rank != 0:
