@@ -117,7 +117,7 @@ static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, const long l
                       cudaStream_t s) {
   const long threads = (long)ghost_runs<NB>() * nleaf;
   if (threads > 0) refresh_kernel<T, NB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, U, leaf0, nleaf);
-  if (nslow > 0) refresh_slow_kernel<T, NB><<<(unsigned)((5L * nslow + 127) / 128), 128, 0, s>>>(m, U, slow, nslow);
+  if (nslow > 0) refresh_slow_kernel<T, NB><<<(nslow + 127) / 128, 128, 0, s>>>(m, U, slow, nslow);
 }
 
 template <typename T>

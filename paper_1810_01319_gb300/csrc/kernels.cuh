@@ -542,15 +542,13 @@ __device__ __forceinline__ void ghost_coord(int q, int& x, int& y, int& z) {
 
 // Mean of the 8 cells (fine padded coords f0 + {0,1}^3) of leaf `leaf`,
 // summed in (dz, dy, dx) order, times 0.125.
-// NF = 5: all fields; NF = 1: the one field U points at (U offset by the
-// field's slab, the leaf stride still five slabs).
-template <typename T, int NB, int NF = 5>
+template <typename T, int NB>
 __device__ __forceinline__ void restrict8(const T* U, int leaf, int fx, int fy, int fz, T out[5]) {
   constexpr int N = NB + 2 * kGhosts;
   constexpr long SLAB = (long)N * N * N;
   const T* b = U + (long)leaf * 5 * SLAB + ((long)fz * N + fy) * N + fx;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
+  for (int f = 0; f < 5; ++f) {
     const T* c = b + f * SLAB;
     T v = c[0];
     v = v + c[1];
@@ -564,13 +562,13 @@ __device__ __forceinline__ void restrict8(const T* U, int leaf, int fx, int fy, 
   }
 }
 
-template <typename T, int NB, int NF = 5>
+template <typename T, int NB>
 __device__ __forceinline__ void load5(const T* U, int leaf, int x, int y, int z, T out[5]) {
   constexpr int N = NB + 2 * kGhosts;
   constexpr long SLAB = (long)N * N * N;
   const T* b = U + (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) out[f] = b[f * SLAB];
+  for (int f = 0; f < 5; ++f) out[f] = b[f * SLAB];
 }
 
 // Value of the level-(L-1) cell r (local to the coarse leaf C, r[a] may be
@@ -578,7 +576,7 @@ __device__ __forceinline__ void load5(const T* U, int leaf, int x, int y, int z,
 // C's own cell, a same-level copy, a restriction from level-L leaves, an
 // injection from the level-(L-2) leaf, or C's cell itself behind an outflow
 // boundary.
-template <typename T, int NB, int NF = 5>
+template <typename T, int NB>
 __device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int rc[3], int a, int side,
                                 const T Uc[5], T out[5]) {
   constexpr int G = kGhosts, H = NB / 2;
@@ -587,18 +585,17 @@ __device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int r
   const int8_t k = m.kind[e];
   if (k == kBoundary) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) out[f] = Uc[f];
+    for (int f = 0; f < 5; ++f) out[f] = Uc[f];
     return;
   }
   int r2[3] = {rc[0], rc[1], rc[2]};
   r2[a] = side < 0 ? NB - 1 : 0;   // position inside the neighbour node
   if (k == kSame) {
-    load5<T, NB, NF>(U, m.idx[e], r2[0] + G, r2[1] + G, r2[2] + G, out);
+    load5<T, NB>(U, m.idx[e], r2[0] + G, r2[1] + G, r2[2] + G, out);
   } else if (k == kFine) {
     const int o0 = r2[0] / H, o1 = r2[1] / H, o2 = r2[2] / H;
     const int child = m.fine8[e * 8 + o2 * 4 + o1 * 2 + o0];
-    restrict8<T, NB, NF>(U, child, 2 * r2[0] - o0 * NB + G, 2 * r2[1] - o1 * NB + G, 2 * r2[2] - o2 * NB + G,
-                         out);
+    restrict8<T, NB>(U, child, 2 * r2[0] - o0 * NB + G, 2 * r2[1] - o1 * NB + G, 2 * r2[2] - o2 * NB + G, out);
   } else {  // coarser: inject the level-(L-2) cell
     const int4 cl = m.leaf[C];
     const int K = m.idx[e];
@@ -609,13 +606,13 @@ __device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int r
     const int ncell = (m.root[a] << Lc) * NB;
     g[a] = wrap_mod(g[a], ncell);
     const int lx = (g[0] >> 1) - kl.y * NB, ly = (g[1] >> 1) - kl.z * NB, lz = (g[2] >> 1) - kl.w * NB;
-    load5<T, NB, NF>(U, K, lx + G, ly + G, lz + G, out);
+    load5<T, NB>(U, K, lx + G, ly + G, lz + G, out);
   }
 }
 
 // Value of one ghost cell (padded coords c, already inside the block
 // array) of leaf `leaf`: same-level copy, restriction or prolongation.
-template <typename T, int NB, int NF = 5>
+template <typename T, int NB>
 __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T v[5]) {
   constexpr int G = kGhosts, H = NB / 2;
   int d[3];
@@ -630,7 +627,7 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
   const int e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
   const int8_t k = m.kind[e];
   if (k == kSame) {
-    load5<T, NB, NF>(U, m.idx[e], c[0] - d[0] * NB, c[1] - d[1] * NB, c[2] - d[2] * NB, v);
+    load5<T, NB>(U, m.idx[e], c[0] - d[0] * NB, c[1] - d[1] * NB, c[2] - d[2] * NB, v);
   } else if (k == kFine) {
     int r[3], o[3];
 #pragma unroll
@@ -639,8 +636,7 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
       o[a] = r[a] / H;
     }
     const int child = m.fine8[e * 8 + o[2] * 4 + o[1] * 2 + o[0]];
-    restrict8<T, NB, NF>(U, child, 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G, 2 * r[2] - o[2] * NB + G,
-                         v);
+    restrict8<T, NB>(U, child, 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G, 2 * r[2] - o[2] * NB + G, v);
   } else {  // coarse: conservative minmod-limited linear prolongation
     const int4 lf = m.leaf[leaf];
     const int C = m.idx[e];
@@ -657,7 +653,7 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
       sgn[a] = (gl & 1) ? T(1) : T(-1);
     }
     T Uc[5];
-    load5<T, NB, NF>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+    load5<T, NB>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
     T D[3][5];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -665,15 +661,15 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
       int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
       rm[a] -= 1;
       rp[a] += 1;
-      if (rm[a] >= 0) load5<T, NB, NF>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
-      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, -1, Uc, Um);
-      if (rp[a] < NB) load5<T, NB, NF>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
-      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, 1, Uc, Up);
+      if (rm[a] >= 0) load5<T, NB>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, 1, Uc, Up);
 #pragma unroll
-      for (int f = 0; f < NF; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
     }
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
+    for (int f = 0; f < 5; ++f)
       v[f] = Uc[f] + T(0.25) * ((sgn[0] * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
   }
 }
@@ -751,19 +747,12 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0
 // cells per thread: a run clamped along x repeats one value; a run inside a
 // finer neighbour restricts cell by cell; a run inside a coarser neighbour
 // covers two parent cells, each prolonged once for its two children.
-// One field of one run per thread (threads 5 x the runs, field-major): five
-// times the independent loads in flight of a thread per run, for this
-// gather-bound kernel.
 template <typename T, int NB>
-__global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U0, const long long* runs, int nruns) {
+__global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, const long long* runs, int nruns) {
   constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
   constexpr long SLAB = (long)N * N * N;
-  constexpr int NF = 1;
-  const long gi = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= 5L * nruns) return;
-  const int fld = (int)(gi / nruns);
-  const int i = (int)(gi - (long)fld * nruns);
-  T* U = U0 + fld * SLAB;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nruns) return;
   const long long r = runs[i];
   const int leaf = (int)(r / NS);
   int x0, y, z;
@@ -785,19 +774,19 @@ __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U0, con
   if (xclamp) {   // every cell of the run reads the same boundary cell
     int cc[3] = {c[0], c[1], c[2]};
     T v[5];
-    ghost_value<T, NB, NF>(m, U, leaf, cc, v);
+    ghost_value<T, NB>(m, U, leaf, cc, v);
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int f = 0; f < NF; ++f) U[dst + q + f * SLAB] = v[f];
+      for (int f = 0; f < 5; ++f) U[dst + q + f * SLAB] = v[f];
     return;
   }
   if (k != kCoarse) {
     for (int q = 0; q < 4; ++q) {
       int cc[3] = {x0 + q, y, z};
       T v[5];
-      ghost_value<T, NB, NF>(m, U, leaf, cc, v);
+      ghost_value<T, NB>(m, U, leaf, cc, v);
 #pragma unroll
-      for (int f = 0; f < NF; ++f) U[dst + q + f * SLAB] = v[f];
+      for (int f = 0; f < 5; ++f) U[dst + q + f * SLAB] = v[f];
     }
     return;
   }
@@ -821,25 +810,25 @@ __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U0, con
     const int gl = wrap_mod(lij[0] * NB + (x0 + 2 * h - G), ncx);   // even: the lower child
     int rc[3] = {(gl >> 1) - cij[0] * NB, rcyz[1], rcyz[2]};
     T Uc[5], D[3][5];
-    load5<T, NB, NF>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+    load5<T, NB>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       T Um[5], Up[5];
       int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
       rm[a] -= 1;
       rp[a] += 1;
-      if (rm[a] >= 0) load5<T, NB, NF>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
-      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, -1, Uc, Um);
-      if (rp[a] < NB) load5<T, NB, NF>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
-      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, 1, Uc, Up);
+      if (rm[a] >= 0) load5<T, NB>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB>(m, U, C, rc, a, 1, Uc, Up);
 #pragma unroll
-      for (int f = 0; f < NF; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const T sx = q ? T(1) : T(-1);
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
+      for (int f = 0; f < 5; ++f)
         U[dst + 2 * h + q + f * SLAB] = Uc[f] + T(0.25) * ((sx * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
     }
   }
