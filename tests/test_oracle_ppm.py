@@ -3,6 +3,7 @@ published method's): polynomial exactness, limiter properties, the two-shock
 solver against the exact Riemann solver, consistency on equal states, and the
 exact solver against textbook star states."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -89,15 +90,28 @@ def test_two_shock_solver_exact_on_symmetric_collision(u0, gamma):
     assert abs(us) < 1e-12
 
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
 def test_exact_riemann_textbook_star_states():
-    # Toro, "Riemann Solvers and Numerical Methods for Fluid Dynamics", Table 4.2
-    cases = [((1.0, 0.0, 1.0, 0.125, 0.0, 0.1), (0.30313, 0.92745)),
-             ((1.0, -2.0, 0.4, 1.0, 2.0, 0.4), (0.00189, 0.0)),
-             ((1.0, 0.0, 1000.0, 1.0, 0.0, 0.01), (460.894, 19.5975))]
-    for args, (p, u) in cases:
-        ps, us = exact.star_state(*args, 1.4)
-        assert ps == pytest.approx(p, rel=5e-5, abs=1e-5)
-        assert us == pytest.approx(u, rel=5e-5, abs=1e-5)
+    """Toro, Table 4.2 (tests/golden/toro_star_states.txt)."""
+    rows = _golden_rows("toro_star_states.txt")
+    assert len(rows) == 3
+    for r in rows:
+        v = [float(x) for x in r]
+        ps, us = exact.star_state(*v[:6], 1.4)
+        assert ps == pytest.approx(v[6], rel=5e-5, abs=1e-5)
+        assert us == pytest.approx(v[7], rel=5e-5, abs=1e-5)
 
 
 def test_exact_riemann_rankine_hugoniot():
@@ -116,10 +130,12 @@ def test_exact_riemann_rankine_hugoniot():
 
 
 def test_sedov_constant():
-    # Taylor (1950): R = 1.033 (E t^2/rho)^(1/5) for gamma = 1.4
-    assert exact.sedov_xi0(1.4) == pytest.approx(1.033, abs=1e-3)
-    # Kamm & Timmes (2007), energy constants alpha = xi0^-(nu+2) for gamma = 1.4
-    assert exact.sedov_xi0(1.4, nu=3) ** -5 == pytest.approx(0.851072, abs=2e-6)
+    """Taylor (1950) and Kamm & Timmes (2007), tests/golden/sedov_constants.txt;
+    alpha = xi0^-(nu+2)."""
+    g = {r[0]: (float(r[1]), float(r[2])) for r in _golden_rows("sedov_constants.txt")}
+    assert exact.sedov_xi0(g["xi0"][0]) == pytest.approx(g["xi0"][1], abs=1e-3)
+    assert exact.sedov_xi0(g["alpha"][0], nu=3) ** -5 == pytest.approx(g["alpha"][1], abs=2e-6)
+    # Kamm & Timmes (2007), the cylindrical constant for gamma = 1.4
     assert exact.sedov_xi0(1.4, nu=2) ** -4 == pytest.approx(0.984074, abs=2e-6)
 
 
