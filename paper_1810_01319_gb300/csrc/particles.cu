@@ -12,6 +12,13 @@
 // between the cell centres of the leaf's padded block (ghosts refreshed),
 // along x, then y, then z.  Push: x += dt u, periodic wrap or outflow loss,
 // lookup again (migration).
+//
+// Where the block width at max_level and the level-0 cell width are powers
+// of two (a box whose extent over the root count is one), each division by a
+// width is a multiplication by its reciprocal, also a power of two: both
+// give the correctly rounded value of the same exact quotient, so the
+// results are bit-identical, and six float64 divisions per tracer leave the
+// slow float64 pipe.
 #include "cello_internal.h"
 #include "morton.h"
 #include "ppm.cuh"
@@ -24,14 +31,18 @@ struct PartMesh {
   const unsigned long long* keys;
   double lo[3], hi[3];
   double w;   // block width at max_level
+  double inv_w, inv_dx0;   // 1 / w and 1 / (level-0 cell width), exact when pow2
+  bool pow2;               // both widths powers of two
 };
+
+__device__ __forceinline__ double over_w(const PartMesh& P, double d) { return P.pow2 ? d * P.inv_w : d / P.w; }
 
 __device__ __forceinline__ int locate_point(const PartMesh& P, const double x[3]) {
   unsigned b[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const long nb = (long)P.m.root[a] << P.m.max_level;
-    long v = (long)floor((x[a] - P.lo[a]) / P.w);
+    long v = (long)floor(over_w(P, x[a] - P.lo[a]));
     v = v < 0 ? 0 : (v > nb - 1 ? nb - 1 : v);
     b[a] = (unsigned)v;
   }
@@ -63,8 +74,11 @@ __device__ __forceinline__ void cell_velocity(const T* blk, long SLAB, long o, d
   for (int c = 0; c < 3; ++c) v[c] = (double)blk[(1 + c) * SLAB + o] * ir;
 }
 
+// Three CTAs of 256 per SM (80 registers, a few spilled to L1): the corner
+// gathers of randomly placed tracers are latency bound, and the extra warps
+// hide more of it.
 template <typename T>
-__global__ void particles_push_kernel(PartMesh P, const T* U, double* pos, int* leaf, long count,
+__global__ void __launch_bounds__(256, 3) particles_push_kernel(PartMesh P, const T* U, double* pos, int* leaf, long count,
                                       const double* dt_dev) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
@@ -75,13 +89,15 @@ __global__ void particles_push_kernel(PartMesh P, const T* U, double* pos, int* 
   const long SLAB = (long)N * N * N;
   const int4 lf = m.leaf[b];
   const double dx = ldexp(m.dx0, -lf.x);
+  const double inv_dx = ldexp(P.inv_dx0, lf.x);
   const int lidx[3] = {lf.y, lf.z, lf.w};
   double x[3], f[3];
   int i0[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     x[a] = pos[a * count + i];
-    const double s = (x[a] - (P.lo[a] + (double)(lidx[a] * n) * dx)) / dx - 0.5;
+    const double d = x[a] - (P.lo[a] + (double)(lidx[a] * n) * dx);
+    const double s = (P.pow2 ? d * inv_dx : d / dx) - 0.5;
     const double c = floor(s);
     i0[a] = (int)c + g;
     f[a] = s - c;
@@ -126,12 +142,25 @@ __global__ void particles_locate_kernel(PartMesh P, const double* pos, int* leaf
   leaf[i] = locate_point(P, x);
 }
 
+bool is_pow2(double v) {
+  int e;
+  return v > 0.0 && std::frexp(v, &e) == 0.5;
+}
+
+PartMesh part_mesh(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3]) {
+  PartMesh P{m, keys, {lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, ldexp((hi[0] - lo[0]) / m.root[0], -m.max_level)};
+  P.pow2 = is_pow2(P.w) && is_pow2(m.dx0);
+  P.inv_w = 1.0 / P.w;
+  P.inv_dx0 = 1.0 / m.dx0;
+  return P;
+}
+
 }  // namespace
 
 void launch_particles_locate(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3],
                              const double* pos, int* leaf, long count, cudaStream_t s) {
   if (count <= 0) return;
-  PartMesh P{m, keys, {lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, ldexp((hi[0] - lo[0]) / m.root[0], -m.max_level)};
+  const PartMesh P = part_mesh(m, keys, lo, hi);
   particles_locate_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(P, pos, leaf, count);
 }
 
@@ -139,7 +168,7 @@ void launch_particles_push(const DevMesh& m, const unsigned long long* keys, con
                            const void* U, int precision, double* pos, int* leaf, long count, const double* dt,
                            cudaStream_t s) {
   if (count <= 0) return;
-  PartMesh P{m, keys, {lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, ldexp((hi[0] - lo[0]) / m.root[0], -m.max_level)};
+  const PartMesh P = part_mesh(m, keys, lo, hi);
   const unsigned grid = (unsigned)((count + 255) / 256);
   if (precision == 4)
     particles_push_kernel<float><<<grid, 256, 0, s>>>(P, static_cast<const float*>(U), pos, leaf, count, dt);

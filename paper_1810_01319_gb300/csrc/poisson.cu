@@ -34,12 +34,25 @@ __device__ __forceinline__ T nbsum(const T* p, int x, int y, int z, int M) {
   return ((((xm + xp) + ym) + yp) + zm) + zp;
 }
 
+// The grid kernels run one thread per cell of an M^3 (or, for the
+// restriction, (M/2)^3) grid on a 3-D launch: 32 x 8 threads per CTA in
+// (x, y), one CTA row per z plane, so no division recovers the coordinates.
+constexpr int kBX = 32, kBY = 8;
+dim3 grid3(int M) { return dim3((unsigned)((M + kBX - 1) / kBX), (unsigned)((M + kBY - 1) / kBY), (unsigned)M); }
+const dim3 kBlock3(kBX, kBY, 1);
+
+__device__ __forceinline__ bool cell3(int M, int& x, int& y, int& z) {
+  x = blockIdx.x * kBX + threadIdx.x;
+  y = blockIdx.y * kBY + threadIdx.y;
+  z = blockIdx.z;
+  return x < M && y < M;
+}
+
 template <typename T>
 __global__ void jacobi_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ f, int M, T h2) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)M * M * M) return;
-  const unsigned u = (unsigned)i, uM = (unsigned)M;   // M^3 <= 2^30: 32-bit index arithmetic
-  const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
+  int x, y, z;
+  if (!cell3(M, x, y, z)) return;
+  const long i = gidx(x, y, z, M);
   out[i] = T(1.0 - kOmega) * in[i] + T(kOmega) * ((nbsum(in, x, y, z, M) - h2 * f[i]) * T(1.0 / 6.0));
 }
 
@@ -49,10 +62,9 @@ template <typename T>
 __global__ void residual_restrict_kernel(const T* __restrict__ phi, const T* __restrict__ f, T* __restrict__ fc,
                                          int M, T ih2) {
   const int Mc = M / 2;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)Mc * Mc * Mc) return;
-  const unsigned u = (unsigned)i, uM = (unsigned)Mc;
-  const int X = (int)(u % uM), Y = (int)((u / uM) % uM), Z = (int)(u / (uM * uM));
+  int X, Y, Z;
+  if (!cell3(Mc, X, Y, Z)) return;
+  const long i = gidx(X, Y, Z, Mc);
   T s = T(0);
   bool first = true;
   for (int dz = 0; dz < 2; ++dz)
@@ -71,10 +83,9 @@ __global__ void residual_restrict_kernel(const T* __restrict__ phi, const T* __r
 template <typename T>
 __global__ void prolong_add_kernel(const T* __restrict__ ec, T* __restrict__ phi, int M) {
   const int Mc = M / 2;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)M * M * M) return;
-  const unsigned u = (unsigned)i, uM = (unsigned)M;
-  const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
+  int x, y, z;
+  if (!cell3(M, x, y, z)) return;
+  const long i = gidx(x, y, z, M);
   const int X = x >> 1, Y = y >> 1, Z = z >> 1;
   const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
   const int X1 = wrapm(X + sx, Mc), Y1 = wrapm(Y + sy, Mc), Z1 = wrapm(Z + sz, Mc);
@@ -92,10 +103,9 @@ __global__ void prolong_add_kernel(const T* __restrict__ ec, T* __restrict__ phi
 // side of a float32 V-cycle), and the float32 correction added to phi.
 __global__ void residual_f32_kernel(const double* __restrict__ phi, const double* __restrict__ f,
                                     float* __restrict__ r, int M, double ih2) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)M * M * M) return;
-  const unsigned u = (unsigned)i, uM = (unsigned)M;
-  const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
+  int x, y, z;
+  if (!cell3(M, x, y, z)) return;
+  const long i = gidx(x, y, z, M);
   r[i] = (float)(f[i] - (nbsum(phi, x, y, z, M) - 6.0 * phi[i]) * ih2);
 }
 
@@ -125,7 +135,7 @@ __global__ void reduce_kernel(const double* __restrict__ a, const double* __rest
       acc += a[i];
     } else {
       const unsigned u = (unsigned)i, uM = (unsigned)M;   // M^3 <= 2^30: 32-bit index arithmetic
-  const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
+      const int x = (int)(u % uM), y = (int)((u / uM) % uM), z = (int)(u / (uM * uM));
       const double r = fabs(f[i] - (nbsum(a, x, y, z, M) - 6.0 * a[i]) * ih2);
       acc = r > acc ? r : acc;
     }
@@ -185,16 +195,14 @@ struct Cycle {
   cudaStream_t s;
 
   void sweeps(Level<T>& L, int count) {
-    const long c = (long)L.M * L.M * L.M;
     for (int k = 0; k < count; ++k) {
-      jacobi_kernel<T><<<blocks_for(c), 256, 0, s>>>(L.phi, L.tmp, L.f, L.M, T(L.h * L.h));
+      jacobi_kernel<T><<<grid3(L.M), kBlock3, 0, s>>>(L.phi, L.tmp, L.f, L.M, T(L.h * L.h));
       std::swap(L.phi, L.tmp);
     }
   }
 
   void vcycle(int l) {
     Level<T>& L = lv[l];
-    const long c = (long)L.M * L.M * L.M;
     if (L.M == 1) {
       fill_kernel<T><<<1, 32, 0, s>>>(L.phi, 1, T(0));
       return;
@@ -206,10 +214,10 @@ struct Cycle {
     sweeps(L, kNu);
     Level<T>& C = lv[l + 1];
     const long cc = (long)C.M * C.M * C.M;
-    residual_restrict_kernel<T><<<blocks_for(cc), 256, 0, s>>>(L.phi, L.f, C.f, L.M, T(1.0 / (L.h * L.h)));
+    residual_restrict_kernel<T><<<grid3(C.M), kBlock3, 0, s>>>(L.phi, L.f, C.f, L.M, T(1.0 / (L.h * L.h)));
     fill_kernel<T><<<blocks_for(cc), 256, 0, s>>>(C.phi, cc, T(0));
     vcycle(l + 1);
-    prolong_add_kernel<T><<<blocks_for(c), 256, 0, s>>>(C.phi, L.phi, L.M);
+    prolong_add_kernel<T><<<grid3(L.M), kBlock3, 0, s>>>(C.phi, L.phi, L.M);
     sweeps(L, kNu);
   }
 };
@@ -298,7 +306,7 @@ cudaError_t poisson_solve(PoissonScratch** scratch, const DevMesh& m, int M, dou
       C64.vcycle(0);
     } else {
       Level<float>& L = C32.lv[0];
-      residual_f32_kernel<<<blocks_for(c), 256, 0, s>>>(phi, f, L.f, M, 1.0 / (h * h));
+      residual_f32_kernel<<<grid3(M), kBlock3, 0, s>>>(phi, f, L.f, M, 1.0 / (h * h));
       fill_kernel<float><<<blocks_for(c), 256, 0, s>>>(L.phi, c, 0.0f);
       C32.vcycle(0);
       correct_kernel<<<blocks_for(c), 256, 0, s>>>(phi, L.phi, c);
