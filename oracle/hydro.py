@@ -15,7 +15,9 @@ elementwise operation is written out in the stated order (no fused
 multiply-add, no reassociation), so a reader can check it term by term.
 
 Layout: U[B, 5, N, N, N] float64, leaves in mesh order, conserved fields
-(rho, rho*u, rho*v, rho*w, E), cells indexed [z, y, x] with N = n + 2g.
+(rho, rho*u, rho*v, rho*w, E), cells indexed [z, y, x] with N = n + 2g; with
+the dual-energy formalism (Desc.dual_energy) U[B, 6, N, N, N], the sixth
+field the internal energy density rho*e (see dual_energy_sync below).
 
 Parity pins (tests/test_oracle_*.py): uniform-state invariance, mirror
 symmetry, conservation on periodic AMR meshes, all-one-level AMR equal to a
@@ -39,13 +41,16 @@ N_RIEMANN = 5        # fixed Newton iterations of the two-shock solver, no early
 EPS_STEEP = 0.01     # CW84 contact steepening: least relative density jump
 ETA1, ETA2 = 20.0, 0.05   # CW84 contact steepening: eta = clamp(ETA1 (eta~ - ETA2), 0, 1)
 K0_STEEP = 0.1       # CW84 gas-dynamics condition: steepen where the density jump dominates
+DE_ETA1 = 1e-3       # dual energy: pressure from E where E - ke > DE_ETA1 E, else from rho e
+DE_ETA2 = 0.1        # dual energy: rho e reset to E - ke after a sweep where E - ke > DE_ETA2 E
 SIXTH = 1.0 / 6.0
 TWO_THIRDS = 2.0 / 3.0
 GHOSTS = 4           # the PPM stencil below reaches 4 cells on each side
 
 # conserved component order seen by a sweep along each axis:
-# (density, normal momentum, transverse momentum 1, transverse momentum 2, E)
-AXIS_COMPONENTS = {0: (0, 1, 2, 3, 4), 1: (0, 2, 1, 3, 4), 2: (0, 3, 1, 2, 4)}
+# (density, normal momentum, transverse momentum 1, transverse momentum 2, E,
+# and rho e with the dual-energy formalism)
+AXIS_COMPONENTS = {0: (0, 1, 2, 3, 4, 5), 1: (0, 2, 1, 3, 4, 5), 2: (0, 3, 1, 2, 4, 5)}
 AXIS_DIM = {0: 4, 1: 3, 2: 2}   # tensor dim of an axis in U[B, 5, z, y, x]
 
 
@@ -59,16 +64,38 @@ def ieee_sqrt(x):
     return s + (exact - s).detach()
 
 
-def primitives(rho_c, mn, mt1, mt2, E, gamma):
+def primitives(rho_c, mn, mt1, mt2, E, gamma, rhoe=None):
     """Conserved -> primitive (rho, u_n, u_t1, u_t2, p) with density and
-    pressure floors.  Kinetic energy 0.5*rho*(u_n^2 + (u_t1^2 + u_t2^2))."""
+    pressure floors.  Kinetic energy 0.5*rho*(u_n^2 + (u_t1^2 + u_t2^2)).
+    With the dual-energy formalism (rhoe given, Bryan et al. 1995): the
+    pressure comes from the internal energy E - ke where E - ke > DE_ETA1 E,
+    else from rho e, and the specific internal energy e = rho e / rho is a
+    sixth primitive."""
     rho = torch.clamp_min(rho_c, RHO_FLOOR)
     un = mn / rho
     ut1 = mt1 / rho
     ut2 = mt2 / rho
     ke = (0.5 * rho) * (un * un + (ut1 * ut1 + ut2 * ut2))
-    p = torch.clamp_min((gamma - 1.0) * (E - ke), P_FLOOR)
-    return rho, un, ut1, ut2, p
+    if rhoe is None:
+        p = torch.clamp_min((gamma - 1.0) * (E - ke), P_FLOOR)
+        return rho, un, ut1, ut2, p
+    eint = E - ke
+    p = torch.clamp_min((gamma - 1.0) * torch.where(eint > DE_ETA1 * E, eint, rhoe), P_FLOOR)
+    return rho, un, ut1, ut2, p, rhoe / rho
+
+
+def dual_energy_sync(rho_c, mn, mt1, mt2, E, rhoe):
+    """Dual-energy synchronisation after a sweep's update (Bryan et al.
+    1995): where the internal energy from the total energy, E - ke (ke as in
+    primitives, from the updated state), exceeds DE_ETA2 E it replaces rho e;
+    elsewhere rho e keeps its own update."""
+    rho = torch.clamp_min(rho_c, RHO_FLOOR)
+    un = mn / rho
+    ut1 = mt1 / rho
+    ut2 = mt2 / rho
+    ke = (0.5 * rho) * (un * un + (ut1 * ut1 + ut2 * ut2))
+    eint = E - ke
+    return torch.where(eint > DE_ETA2 * E, eint, rhoe)
 
 
 def limited_slope(am, a0, ap):
@@ -131,12 +158,15 @@ def trace(W, aL, aR, dtdx, gamma):
     average seen by the fastest wave moving right (or aR if none does); every
     other wave moving right subtracts its projection l.(ref - avg) along its
     right eigenvector.  Left edge mirrors it.  Transverse velocities ride the
-    entropy wave.  Returns (state at the left edge, state at the right edge),
-    each (rho, u_n, u_t1, u_t2, p), floored."""
+    entropy wave, and so does the specific internal energy e of the
+    dual-energy formalism (a sixth component, advected).  Returns (state at
+    the left edge, state at the right edge), each (rho, u_n, u_t1, u_t2, p)
+    [+ e], floored."""
+    nq = len(W)
     rho, un, p = W[0], W[1], W[4]
     csq = (gamma * p) / rho
     c = ieee_sqrt(csq)
-    a6 = [6.0 * (W[q] - 0.5 * (aL[q] + aR[q])) for q in range(5)]
+    a6 = [6.0 * (W[q] - 0.5 * (aL[q] + aR[q])) for q in range(nq)]
     lm, l0, lp = un - c, un, un + c
     half_rho_c = (0.5 * rho) / c
     half_inv_csq = 0.5 / csq
@@ -145,7 +175,7 @@ def trace(W, aL, aR, dtdx, gamma):
 
     # right edge: waves with lambda > 0
     sp, s0, sm = lp * dtdx, l0 * dtdx, lm * dtdx
-    ref = [torch.where(lp > 0.0, edge_avg_right(aL[q], aR[q], a6[q], sp), aR[q]) for q in range(5)]
+    ref = [torch.where(lp > 0.0, edge_avg_right(aL[q], aR[q], a6[q], sp), aR[q]) for q in range(nq)]
     bm = torch.where(lm > 0.0,
                      (ref[4] - edge_avg_right(aL[4], aR[4], a6[4], sm)) * half_inv_csq
                      - (ref[1] - edge_avg_right(aL[1], aR[1], a6[1], sm)) * half_rho_c, zero)
@@ -157,10 +187,11 @@ def trace(W, aL, aR, dtdx, gamma):
     r_p = torch.clamp_min(ref[4] - csq * bm, P_FLOOR)
     r_t1 = torch.where(l0 > 0.0, edge_avg_right(aL[2], aR[2], a6[2], s0), ref[2])
     r_t2 = torch.where(l0 > 0.0, edge_avg_right(aL[3], aR[3], a6[3], s0), ref[3])
+    r_e = [torch.where(l0 > 0.0, edge_avg_right(aL[q], aR[q], a6[q], s0), ref[q]) for q in range(5, nq)]
 
     # left edge: waves with lambda < 0
     tm, t0, tp = -lm * dtdx, -l0 * dtdx, -lp * dtdx
-    ref = [torch.where(lm < 0.0, edge_avg_left(aL[q], aR[q], a6[q], tm), aL[q]) for q in range(5)]
+    ref = [torch.where(lm < 0.0, edge_avg_left(aL[q], aR[q], a6[q], tm), aL[q]) for q in range(nq)]
     bp = torch.where(lp < 0.0,
                      (ref[4] - edge_avg_left(aL[4], aR[4], a6[4], tp)) * half_inv_csq
                      + (ref[1] - edge_avg_left(aL[1], aR[1], a6[1], tp)) * half_rho_c, zero)
@@ -172,17 +203,22 @@ def trace(W, aL, aR, dtdx, gamma):
     l_p = torch.clamp_min(ref[4] - csq * bp, P_FLOOR)
     l_t1 = torch.where(l0 < 0.0, edge_avg_left(aL[2], aR[2], a6[2], t0), ref[2])
     l_t2 = torch.where(l0 < 0.0, edge_avg_left(aL[3], aR[3], a6[3], t0), ref[3])
-    return (l_rho, l_un, l_t1, l_t2, l_p), (r_rho, r_un, r_t1, r_t2, r_p)
+    l_e = [torch.where(l0 < 0.0, edge_avg_left(aL[q], aR[q], a6[q], t0), ref[q]) for q in range(5, nq)]
+    return (l_rho, l_un, l_t1, l_t2, l_p, *l_e), (r_rho, r_un, r_t1, r_t2, r_p, *r_e)
 
 
-def riemann_flux(WL, WR, gamma):
+def riemann_flux(WL, WR, gamma, velocity=False):
     """CW84 two-shock approximate Riemann solver with N_RIEMANN fixed Newton
     steps on p* (shock curves on both sides, derivative Z = 2W^3/(W^2+C^2)),
     u* = Z-weighted mean, sampled at x/t = 0 (u* >= 0 takes the left side);
     inside a rarefaction the state is interpolated linearly between the head
-    and tail speeds.  Returns the five fluxes (rho, m_n, m_t1, m_t2, E)."""
-    rL, uL, t1L, t2L, pL = WL
-    rR, uR, t1R, t2R, pR = WR
+    and tail speeds.  Returns the five fluxes (rho, m_n, m_t1, m_t2, E); with
+    a sixth component e (dual energy) also the flux of rho e, the mass flux
+    times the e of the sampled side (e rides with the transverse
+    velocities).  velocity=True returns (fluxes, u) with u the normal
+    velocity of the sampled state."""
+    rL, uL, t1L, t2L, pL = WL[:5]
+    rR, uR, t1R, t2R, pR = WR[:5]
     g1 = (gamma + 1.0) / (2.0 * gamma)
     CL = ieee_sqrt((gamma * pL) * rL)
     CR = ieee_sqrt((gamma * pR) * rR)
@@ -240,7 +276,10 @@ def riemann_flux(WL, WR, gamma):
     f3 = f0 * t2
     E = p * inv_gm1 + (0.5 * r) * (u * u + (t1 * t1 + t2 * t2))
     f4 = u * (E + p)
-    return f0, f1, f2, f3, f4
+    F = (f0, f1, f2, f3, f4)
+    if len(WL) > 5:
+        F = F + (f0 * torch.where(left, WL[5], WR[5]),)
+    return (F, u) if velocity else F
 
 
 def hllc_waves(WL, WR, gamma):
@@ -252,21 +291,23 @@ def hllc_waves(WL, WR, gamma):
     with m_K = rho_K (S_K - u_K) (Toro eq. 10.37); star states U*_K = m_K /
     (S_K - S*) (1, S*, v_K, w_K, E_K / rho_K + (S* - u_K)(S* + p_K / m_K))
     (eq. 10.39) and star fluxes F*_K = F_K + S_K (U*_K - U_K) (eq. 10.38).
-    Returns a dict of the speeds, the side states U, fluxes F and the star
-    states and fluxes."""
+    A sixth component e (dual energy) is passive like v and w: conserved
+    rho e, flux rho u e, star value m_K / (S_K - S*) e_K.  Returns a dict of
+    the speeds, the side states U, fluxes F and the star states and
+    fluxes."""
     inv_gm1 = 1.0 / (gamma - 1.0)
 
     def side(W):
-        r, u, v, w, p = W
+        r, u, v, w, p = W[:5]
         c = ieee_sqrt((gamma * p) / r)
         E = p * inv_gm1 + (0.5 * r) * (u * u + (v * v + w * w))
         f0 = r * u
-        F = (f0, f0 * u + p, f0 * v, f0 * w, u * (E + p))
-        Uc = (r, r * u, r * v, r * w, E)
+        F = (f0, f0 * u + p, f0 * v, f0 * w, u * (E + p)) + tuple(f0 * e for e in W[5:])
+        Uc = (r, r * u, r * v, r * w, E) + tuple(r * e for e in W[5:])
         return c, E, F, Uc
 
-    rL, uL, vL, wL, pL = WL
-    rR, uR, vR, wR, pR = WR
+    rL, uL, vL, wL, pL = WL[:5]
+    rR, uR, vR, wR, pR = WR[:5]
     cL, EL, FL, UL = side(WL)
     cR, ER, FR, UR = side(WR)
     SL = torch.minimum(uL - cL, uR - cR)
@@ -275,29 +316,35 @@ def hllc_waves(WL, WR, gamma):
     mR = rR * (SR - uR)
     Ss = ((pR - pL) + (mL * uL - mR * uR)) / (mL - mR)
 
-    def star(S, m, r, u, v, w, p, E, F, Uc):
+    def star(S, m, r, u, v, w, p, E, F, Uc, extra):
         fac = m / (S - Ss)
-        Us = (fac, fac * Ss, fac * v, fac * w, fac * (E / r + (Ss - u) * (Ss + p / m)))
+        Us = ((fac, fac * Ss, fac * v, fac * w, fac * (E / r + (Ss - u) * (Ss + p / m)))
+              + tuple(fac * e for e in extra))
         return Us, tuple(Fk + S * (Usk - Uk) for Fk, Usk, Uk in zip(F, Us, Uc))
 
-    UsL, FsL = star(SL, mL, rL, uL, vL, wL, pL, EL, FL, UL)
-    UsR, FsR = star(SR, mR, rR, uR, vR, wR, pR, ER, FR, UR)
+    UsL, FsL = star(SL, mL, rL, uL, vL, wL, pL, EL, FL, UL, WL[5:])
+    UsR, FsR = star(SR, mR, rR, uR, vR, wR, pR, ER, FR, UR, WR[5:])
     return dict(SL=SL, SR=SR, Ss=Ss, UL=UL, UR=UR, FL=FL, FR=FR, UsL=UsL, UsR=UsR, FsL=FsL, FsR=FsR)
 
 
-def hllc_flux(WL, WR, gamma):
+def hllc_flux(WL, WR, gamma, velocity=False):
     """HLLC interface flux, an alternative to the two-shock flux of the PPM
     sweep: the flux of the region of the fan (hllc_waves) holding x/t = 0,
     F_L if S_L >= 0, F*_L if S* >= 0, F*_R if S_R > 0, else F_R.  Returns
-    the five fluxes (rho, m_n, m_t1, m_t2, E)."""
+    the five fluxes (rho, m_n, m_t1, m_t2, E) (six with dual energy);
+    velocity=True returns (fluxes, u) with u the normal velocity of that
+    region's state: u_L, S*, S*, u_R."""
     h = hllc_waves(WL, WR, gamma)
     SL, Ss, SR = h["SL"], h["Ss"], h["SR"]
     out = []
-    for k in range(5):
+    for k in range(len(WL)):
         out.append(torch.where(SL >= 0.0, h["FL"][k],
                                torch.where(Ss >= 0.0, h["FsL"][k],
                                            torch.where(SR > 0.0, h["FsR"][k], h["FR"][k]))))
-    return tuple(out)
+    if not velocity:
+        return tuple(out)
+    u = torch.where(SL >= 0.0, WL[1], torch.where(Ss >= 0.0, Ss, torch.where(SR > 0.0, Ss, WR[1])))
+    return tuple(out), u
 
 
 RIEMANN = {"two-shock": riemann_flux, "hllc": hllc_flux}
@@ -325,14 +372,17 @@ def steepening_eta(rm2, rm1, r0, rp1, rp2, pm1, pp1, gamma):
     return torch.clamp(torch.clamp(ETA1 * (eta_t - ETA2), max=1.0), min=0.0)
 
 
-def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock", steepen=False):
+def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock", steepen=False, dual=False):
     """Fluxes at the n+1 interfaces between cells c and c+1, c = 3 .. N-5, of
     pencils of length N = n + 8 (last tensor dim).  Uc = (rho, m_n, m_t1,
     m_t2, E) tensors; riemann names the interface solver; steepen applies
     contact steepening to the density edge values (before flattening and the
-    monotonicity constraints, as in CW84)."""
+    monotonicity constraints, as in CW84).  dual: Uc has a sixth tensor rho e
+    (dual-energy formalism); the return is then (fluxes, u, p) with u the
+    normal velocity of the interface states and p the cell pressures
+    (primitives), both for the source term of the internal energy."""
     N = Uc[0].shape[-1]
-    W = primitives(*Uc, gamma)
+    W = primitives(*Uc[:5], gamma, rhoe=Uc[5] if dual else None)
     p, un = W[4], W[1]
     dm = [limited_slope(a[..., :-2], a[..., 1:-1], a[..., 2:]) for a in W]           # cells 1..N-2
     ai = [0.5 * (a[..., 1:N - 2] + a[..., 2:N - 1]) - (d[..., 1:] - d[..., :-1]) * SIXTH
@@ -344,7 +394,7 @@ def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock", steepen=False):
     f = torch.where(s > 0.0, torch.maximum(fj, fm), torch.where(s < 0.0, torch.maximum(fj, fp), fj))
     Wc = [a[..., 3:N - 3] for a in W]
     aL, aR = [], []
-    for q in range(5):
+    for q in range(len(W)):
         l = ai[q][..., 1:N - 5]
         r = ai[q][..., 2:N - 4]
         if steepen and q == 0:                                                              # cells 3..N-4
@@ -362,7 +412,10 @@ def pencil_fluxes(Uc, dtdx, gamma, riemann="two-shock", steepen=False):
     Wm, Wp = trace(Wc, aL, aR, dtdx, gamma)        # cells 3..N-4
     left = [x[..., 0:N - 7] for x in Wp]
     right = [x[..., 1:N - 6] for x in Wm]
-    return RIEMANN[riemann](left, right, gamma)
+    if not dual:
+        return RIEMANN[riemann](left, right, gamma)
+    F, u = RIEMANN[riemann](left, right, gamma, velocity=True)
+    return F, u, p
 
 
 # ------------------------------------------------------------------ sweeps
@@ -383,27 +436,43 @@ def sweep(U, mesh: Mesh, axis: int, dt: float, rows):
     ranges of the two transverse tensor dims (in their U order) whose pencils
     are updated; cells g..g+n-1 along the axis are updated in place.
     Returns (U, faces) with faces = (F at interface g-1/2, F at g+n-1/2) on
-    interior rows, each [B, 5, n, n] indexed [t2, t1] (t1 < t2 axes)."""
-    n, g = mesh.desc.n, mesh.desc.ghosts
+    interior rows, each [B, nf, n, n] indexed [t2, t1] (t1 < t2 axes).
+
+    Dual-energy formalism (Bryan et al. 1995): rho e is updated by its flux
+    difference and by the compression term of the internal-energy equation,
+    rho e <- (rho e - (dt/dx) (F+ - F-)) - ((dt/dx) p) (u+ - u-), p the
+    cell's pressure from primitives and u+-, the normal velocities of the
+    interface states on its two faces; then dual_energy_sync on the updated
+    cells."""
+    d = mesh.desc
+    n, g = d.n, d.ghosts
     assert g == GHOSTS
+    nf = d.nf
     B = U.shape[0]
     dim = AXIS_DIM[axis]
     comp = AXIS_COMPONENTS[axis]
     V = U.movedim(dim, -1)
     dtdx = dtdx_of_leaves(mesh, dt).view(B, 1, 1, 1)
-    F = pencil_fluxes([V[:, comp[q]] for q in range(5)], dtdx, mesh.desc.gamma, mesh.desc.riemann,
-                      mesh.desc.steepen)
+    F = pencil_fluxes([V[:, comp[q]] for q in range(nf)], dtdx, d.gamma, d.riemann, d.steepen, d.dual_energy)
+    if d.dual_energy:
+        F, uf, pc = F
     (a0, a1), (b0, b1) = rows
     V2 = V.clone()
-    for q in range(5):
+    for q in range(nf):
         Fq = F[q][:, a0:a1, b0:b1]
         V2[:, comp[q], a0:a1, b0:b1, g:g + n] = (V[:, comp[q], a0:a1, b0:b1, g:g + n]
                                                 - dtdx * (Fq[..., 1:] - Fq[..., :-1]))
-    inv = [0] * 5
-    for q in range(5):
+    if d.dual_energy:
+        uq = uf[:, a0:a1, b0:b1]
+        pq = pc[:, a0:a1, b0:b1, g:g + n]
+        cell = (slice(None), slice(a0, a1), slice(b0, b1), slice(g, g + n))
+        e = V2[:, 5][cell] - (dtdx * pq) * (uq[..., 1:] - uq[..., :-1])
+        V2[:, 5][cell] = dual_energy_sync(*(V2[:, comp[q]][cell] for q in range(5)), e)
+    inv = [0] * nf
+    for q in range(nf):
         inv[comp[q]] = q
-    lo = torch.stack([F[inv[f]][:, g:g + n, g:g + n, 0] for f in range(5)], 1)
-    hi = torch.stack([F[inv[f]][:, g:g + n, g:g + n, n] for f in range(5)], 1)
+    lo = torch.stack([F[inv[f]][:, g:g + n, g:g + n, 0] for f in range(nf)], 1)
+    hi = torch.stack([F[inv[f]][:, g:g + n, g:g + n, n] for f in range(nf)], 1)
     return V2.movedim(-1, dim), (lo, hi)
 
 
@@ -453,6 +522,7 @@ class RefreshPlan:
         n, g = d.n, d.ghosts
         N = n + 2 * g
         self.N3 = N ** 3
+        self.nf = nf = d.nf
         maps = mesh.maps()
         zz, yy, xx = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
         inner = ((xx >= g) & (xx < g + n) & (yy >= g) & (yy < g + n) & (zz >= g) & (zz < g + n))
@@ -461,7 +531,7 @@ class RefreshPlan:
         N3 = self.N3
 
         def flat(b, z, y, x):
-            return b * 5 * N3 + (z * N + y) * N + x
+            return b * nf * N3 + (z * N + y) * N + x
 
         def leaf_at(M, X, Y, Z):
             return maps[M][Z // n, Y // n, X // n]
@@ -507,7 +577,7 @@ class RefreshPlan:
             X = _bc(mesh, L, 0, bi * n + gx - g)
             Y = _bc(mesh, L, 1, bj * n + gy - g)
             Z = _bc(mesh, L, 2, bk * n + gz - g)
-            dst = b * 5 * N3 + gcell
+            dst = b * nf * N3 + gcell
             m = leaf_at(L, X, Y, Z)
             s = m >= 0
             copy_d.append(dst[s])
@@ -551,12 +621,12 @@ class RefreshPlan:
         shape = U.shape
         Uf = U.reshape(-1)
         out = Uf.clone()
-        fo = (torch.arange(5, dtype=torch.int64) * self.N3).view(5, 1)
+        fo = (torch.arange(self.nf, dtype=torch.int64) * self.N3).view(self.nf, 1)
 
-        def gather(idx):            # idx [k] -> [5, k]
+        def gather(idx):            # idx [k] -> [nf, k]
             return Uf[idx.view(1, -1) + fo]
 
-        def restrict(idx8):         # idx8 [k, 8] -> [5, k]
+        def restrict(idx8):         # idx8 [k, 8] -> [nf, k]
             v = gather(idx8[:, 0])
             for t in range(1, 8):
                 v = v + gather(idx8[:, t])
@@ -637,14 +707,14 @@ def flux_correct(U, mesh: Mesh, faces, dt: float, cf=None):
     dxs = dx_of_leaves(mesh)
     for b, axis, side, kids in cf:
         dtdx = dt / float(dxs[b])
-        Fc = faces[axis][1 if side > 0 else 0][b]            # [5, n(t2), n(t1)]
+        Fc = faces[axis][1 if side > 0 else 0][b]            # [nf, n(t2), n(t1)]
         for f, o1, o2 in kids:
             Ff = faces[axis][0 if side > 0 else 1][f]       # fine leaf, opposite face
             F00 = Ff[:, 0::2, 0::2]
             F10 = Ff[:, 0::2, 1::2]
             F01 = Ff[:, 1::2, 0::2]
             F11 = Ff[:, 1::2, 1::2]
-            mean = ((F00 + F10) + (F01 + F11)) * 0.25       # [5, h(t2), h(t1)]
+            mean = ((F00 + F10) + (F01 + F11)) * 0.25       # [nf, h(t2), h(t1)]
             sl2 = slice(o2 * h, (o2 + 1) * h)
             sl1 = slice(o1 * h, (o1 + 1) * h)
             corr = (dtdx * (Fc[:, sl2, sl1] - mean)) * float(side)
@@ -661,16 +731,24 @@ def flux_correct(U, mesh: Mesh, faces, dt: float, cf=None):
 
 # ------------------------------------------------------ reductions and step
 def lab_primitives(U, gamma):
+    """(rho, u, v, w, p) in lab order; with a sixth field (dual energy) the
+    pressure is selected as in primitives."""
     rho = torch.clamp_min(U[:, 0], RHO_FLOOR)
     u, v, w = U[:, 1] / rho, U[:, 2] / rho, U[:, 3] / rho
     ke = (0.5 * rho) * (u * u + (v * v + w * w))
-    p = torch.clamp_min((gamma - 1.0) * (U[:, 4] - ke), P_FLOOR)
+    if U.shape[1] == 5:
+        p = torch.clamp_min((gamma - 1.0) * (U[:, 4] - ke), P_FLOOR)
+    else:
+        eint = U[:, 4] - ke
+        p = torch.clamp_min((gamma - 1.0) * torch.where(eint > DE_ETA1 * U[:, 4], eint, U[:, 5]), P_FLOOR)
     return rho, u, v, w, p
 
 
 def reduce_dt_totals(U, mesh: Mesh, cfl: float):
     """dt = cfl * min over leaf interior cells of dx_L / (max(|u|,|v|,|w|) + c),
-    c = sqrt(gamma*p/rho); totals = sum over leaves of dx_L^3 * sum of U."""
+    c = sqrt(gamma*p/rho); totals = sum over leaves of dx_L^3 * sum of U over
+    the five conserved fields (rho e of the dual-energy formalism is not a
+    conserved quantity and has no total)."""
     d = mesh.desc
     n, g = d.n, d.ghosts
     I = U[:, :, g:g + n, g:g + n, g:g + n]
@@ -680,7 +758,7 @@ def reduce_dt_totals(U, mesh: Mesh, cfl: float):
     dx = dx_of_leaves(mesh).view(-1, 1, 1, 1)
     dt = cfl * float(torch.min(dx / s))
     vol = dx.view(-1) ** 3
-    totals = (I.sum(dim=(2, 3, 4)) * vol.view(-1, 1)).sum(0)
+    totals = (I[:, :5].sum(dim=(2, 3, 4)) * vol.view(-1, 1)).sum(0)
     return dt, totals
 
 
@@ -765,7 +843,7 @@ def remap(U_old, old: Mesh, new: Mesh):
     d = new.desc
     n, g = d.n, d.ghosts
     N = n + 2 * g
-    out = torch.zeros((new.n_leaves, 5, N, N, N), dtype=U_old.dtype)
+    out = torch.zeros((new.n_leaves, U_old.shape[1], N, N, N), dtype=U_old.dtype)
     r = torch.arange(n)
     for b, (L, i, j, k) in enumerate(new.leaves):
         L, i, j, k = int(L), int(i), int(j), int(k)

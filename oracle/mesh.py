@@ -53,6 +53,13 @@ class Desc:
     gamma: float = 1.4
     riemann: str = "two-shock"   # interface flux: "two-shock" (CW84) or "hllc"
     steepen: bool = False        # CW84 contact steepening of the density edge values
+    dual_energy: bool = False    # a sixth field rho*e, the dual-energy formalism of Bryan et al. 1995
+
+    @property
+    def nf(self) -> int:
+        """Fields per cell: (rho, rho u, rho v, rho w, E), plus rho e with
+        the dual-energy formalism."""
+        return 6 if self.dual_energy else 5
 
     def dx(self, level: int) -> float:
         """Cell width at a level (cells are cubes; checked in Mesh)."""

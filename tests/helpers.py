@@ -7,10 +7,10 @@ from workloads import ics
 
 
 def oracle_desc(root=(2, 2, 2), n=8, lmax=2, bc=(OM.PERIODIC,) * 3, gamma=5.0 / 3.0, hi=None, riemann="two-shock",
-                steepen=False):
+                steepen=False, dual_energy=False):
     hi = hi or tuple(r / max(root) for r in root)
     return OM.Desc(root=tuple(root), n=n, ghosts=4, max_level=lmax, bc=tuple(bc), gamma=gamma, hi=hi,
-                   riemann=riemann, steepen=steepen)
+                   riemann=riemann, steepen=steepen, dual_energy=dual_energy)
 
 
 def flag_sequence(desc, rounds, seed, p_refine=0.4, p_coarsen=0.0):
@@ -48,8 +48,10 @@ def gpu_mesh_from_flags(odesc, flags, precision):
 def state(odesc, leaves, kind, **kw):
     f = getattr(ics, kind)
     if kind == "grf":
-        return f(leaves, odesc.root, odesc.n, odesc.ghosts, odesc.gamma, **kw)
-    return f(leaves, odesc.root, odesc.n, odesc.ghosts, odesc.lo, odesc.hi, odesc.gamma, **kw)
+        U = f(leaves, odesc.root, odesc.n, odesc.ghosts, odesc.gamma, **kw)
+    else:
+        U = f(leaves, odesc.root, odesc.n, odesc.ghosts, odesc.lo, odesc.hi, odesc.gamma, **kw)
+    return ics.with_internal_energy(U) if odesc.dual_energy else U
 
 
 def interior(U, n, g=4):

@@ -8,7 +8,8 @@ reduction) and imports neither side.
 
 Leaves are an int64 array [B, 4] of (level, i, j, k); the state is
 U[B, 5, N, N, N] float64 (rho, rho*u, rho*v, rho*w, E), cells [z, y, x],
-N = n + 2*ghosts, every cell (ghosts included) sampled at its centre.
+N = n + 2*ghosts, every cell (ghosts included) sampled at its centre
+(with_internal_energy appends rho*e for the dual-energy formalism).
 """
 from __future__ import annotations
 
@@ -40,6 +41,13 @@ def conserved(rho, u, v, w, p, gamma):
     """Initial conserved state from primitive fields (ideal gas)."""
     E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
     return torch.stack([rho, rho * u, rho * v, rho * w, E], 1)
+
+
+def with_internal_energy(U):
+    """The state with a sixth field, the internal energy density
+    rho e = E - |m|^2 / (2 rho), for runs with the dual-energy formalism."""
+    ke = 0.5 * (U[:, 1] * U[:, 1] + U[:, 2] * U[:, 2] + U[:, 3] * U[:, 3]) / U[:, 0]
+    return torch.cat([U, (U[:, 4] - ke).unsqueeze(1)], 1)
 
 
 def sod(leaves, root, n, ghosts, lo, hi, gamma, x0=0.5, axis=0, device="cpu"):
