@@ -79,8 +79,10 @@ def build_workload(cfg, precision, device="cuda", chunk=1024, log=print):
     from workloads import ics
     root, n, lmax = cfg["root"], cfg["n"], cfg["max_level"]
     hi = tuple(r / max(root) for r in root)
+    dual = int(cfg.get("dual_energy", 0))
     desc = make_desc(root, n, lmax, (0, 0, 0), hi, (PERIODIC,) * 3, precision, cfg["gamma"],
-                     riemann=1 if cfg.get("riemann") == "hllc" else 0, steepening=int(cfg.get("steepening", 0)))
+                     riemann=1 if cfg.get("riemann") == "hllc" else 0, steepening=int(cfg.get("steepening", 0)),
+                     dual_energy=dual)
 
     def sample(mesh):
         U = mesh.empty_state(device)
@@ -89,6 +91,8 @@ def build_workload(cfg, precision, device="cuda", chunk=1024, log=print):
             part = ics.blobs(leaves[s:s + chunk], root, n, 4, (0, 0, 0), hi, cfg["gamma"],
                              count=cfg["blobs"], seed=cfg["seed"], device=device, chunk=256,
                              abc=cfg.get("abc", 0.0))
+            if dual:
+                part = ics.with_internal_energy(part)
             U[s:s + chunk] = part.to(U.dtype)
             del part
         return U
@@ -173,12 +177,13 @@ def oracle_sample(cfg, seconds=15.0):
     r = 2
     od = OM.Desc(root=(r, r, r), n=cfg["n"], ghosts=4, max_level=cfg["max_level"], bc=(OM.PERIODIC,) * 3,
                  gamma=cfg["gamma"], hi=(1.0, 1.0, 1.0), riemann=cfg.get("riemann", "two-shock"),
-                 steepen=bool(cfg.get("steepening", 0)))
+                 steepen=bool(cfg.get("steepening", 0)), dual_energy=bool(cfg.get("dual_energy", 0)))
     count = max(1, int(round(cfg["blobs"] * (r / cfg["root"][0]) ** 3)))
 
     def st(mesh):
-        return ics.blobs(mesh.leaves, od.root, od.n, 4, od.lo, od.hi, od.gamma, count=count, seed=cfg["seed"],
-                         abc=cfg.get("abc", 0.0))
+        U = ics.blobs(mesh.leaves, od.root, od.n, 4, od.lo, od.hi, od.gamma, count=count, seed=cfg["seed"],
+                      abc=cfg.get("abc", 0.0))
+        return ics.with_internal_energy(U) if od.dual_energy else U
     mesh = OM.root_mesh(od)
     for _ in range(od.max_level):
         f = OH.refine_flags(OH.ghost_refresh(st(mesh), mesh), mesh, 0, cfg["tau"], cfg["tau"] / 4).numpy()
@@ -373,6 +378,8 @@ def main():
     ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
     ap.add_argument("--riemann", default="two-shock", choices=["two-shock", "hllc"])
     ap.add_argument("--steepening", action="store_true", help="contact steepening of the density edge values")
+    ap.add_argument("--dual-energy", action="store_true",
+                    help="dual-energy formalism (sixth field rho e; shared-memory sweep variants, no operation counts)")
     ap.add_argument("--variants", default="", help="sweep variants x,y,z instead of autotuning (profiling)")
     ap.add_argument("--abc", type=float, default=0.0,
                     help="amplitude of an ABC flow added to every cell (0: blobs in a medium at rest)")
@@ -402,6 +409,8 @@ def main():
     if args.riemann != "two-shock" or args.steepening:
         cfg["riemann"] = args.riemann
         cfg["steepening"] = int(args.steepening)
+    if args.dual_energy:
+        cfg["dual_energy"] = 1
 
     if args.impl == "reference":
         if rank != 0:
@@ -492,8 +501,10 @@ def main():
     sample_ids = np.unique(np.linspace(0, mesh.n_leaves - 1, 32).round().astype(np.int64))
     mesh.ghost_refresh(U)
     t_ops = time.time()
-    ops, pencils, swept_cells, _ = mesh.sweep_opcount(U, sample_ids, float(dt.item()), cycle)
-    log(f"[bench] operation count on {len(sample_ids)} leaves in {time.time() - t_ops:.1f}s")
+    ops = None   # operation counts cover the five-field sweep
+    if mesh.nf == 5:
+        ops, pencils, swept_cells, _ = mesh.sweep_opcount(U, sample_ids, float(dt.item()), cycle)
+        log(f"[bench] operation count on {len(sample_ids)} leaves in {time.time() - t_ops:.1f}s")
     scale = mesh.n_leaves / len(sample_ids)
     prof = mesh.profile_step(U, dt, cycle, cfg["cfl"])
     names = ["ghost_refresh", "sweep_1", "sweep_2", "sweep_3", "flux_correct", "reduce"]
@@ -502,30 +513,34 @@ def main():
     elem = 4
     N = cfg["n"] + 8
     ghost_cells = mesh.n_leaves * (N ** 3 - cfg["n"] ** 3)
-    # algorithmic bytes per launch: each sweep reads and writes the five
-    # fields of every leaf interior cell once; the refresh writes every ghost
-    # cell and reads one source value for it; the reduction reads the interior
-    alg_bytes = {"ghost_refresh": ghost_cells * 2 * 5 * elem, "sweep_1": cells * 2 * 5 * elem,
-                 "sweep_2": cells * 2 * 5 * elem, "sweep_3": cells * 2 * 5 * elem,
-                 "flux_correct": 0, "reduce": cells * 5 * elem}
+    # algorithmic bytes per launch: each sweep reads and writes the nf (five,
+    # six with dual energy) fields of every leaf interior cell once; the
+    # refresh writes every ghost cell and reads one source value for it; the
+    # reduction reads the interior
+    nf = mesh.nf
+    alg_bytes = {"ghost_refresh": ghost_cells * 2 * nf * elem, "sweep_1": cells * 2 * nf * elem,
+                 "sweep_2": cells * 2 * nf * elem, "sweep_3": cells * 2 * nf * elem,
+                 "flux_correct": 0, "reduce": cells * nf * elem}
     phase_names = ["primitives", "slopes_and_shock_detector", "interface_values", "flatten_and_trace",
                    "riemann_flux", "update"]
     sweeps = {}
     order = [0, 1, 2] if cycle % 2 == 0 else [2, 1, 0]
     for k in range(3):
-        ops_launch = float(ops[k].sum()) * scale
         t = prof[1 + k] / 1e3
         v = variant[order[k]]
         sweeps[f"sweep_{k + 1}"] = {
             "axis": "xyz"[order[k]], "variant": v,
             "form": ("streaming-vec4" if v % 12 >= 10 else "streaming") if v % 12 >= 6 else "shared-memory",
-            "ms": prof[1 + k],
-            "ops_per_launch": ops_launch, "ops_per_updated_cell": float(ops[k].sum() / swept_cells[k]),
-            "ops_by_phase_per_updated_cell": {p: float(ops[k][i] / swept_cells[k]) for i, p in enumerate(phase_names)},
-            "achieved_tops": ops_launch / t / 1e12,
-            "hbm_gbs_algorithmic": alg_bytes[f"sweep_{k + 1}"] / t / 1e9}
+            "ms": prof[1 + k], "hbm_gbs_algorithmic": alg_bytes[f"sweep_{k + 1}"] / t / 1e9}
+        if ops is not None:
+            ops_launch = float(ops[k].sum()) * scale
+            sweeps[f"sweep_{k + 1}"].update({
+                "ops_per_launch": ops_launch, "ops_per_updated_cell": float(ops[k].sum() / swept_cells[k]),
+                "ops_by_phase_per_updated_cell": {p: float(ops[k][i] / swept_cells[k])
+                                                  for i, p in enumerate(phase_names)},
+                "achieved_tops": ops_launch / t / 1e12})
     kname = names[top]
-    if kname.startswith("sweep"):
+    if kname.startswith("sweep") and ops is not None:
         sw = sweeps[kname]
         traffic, tsrc = None, None
         key = f"{sw['axis']}-{sw['form']}-{kname}"

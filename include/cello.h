@@ -11,7 +11,9 @@
  *
  * Conventions shared by every entry point
  *  - Field pool: caller-owned device memory, U[leaf][field][z][y][x], five
- *    conserved fields (rho, rho*u, rho*v, rho*w, E) per leaf, each a padded
+ *    conserved fields (rho, rho*u, rho*v, rho*w, E) per leaf, plus the
+ *    internal energy density rho*e as a sixth when the mesh has
+ *    dual_energy = 1, each a padded
  *    cube of N = n + 2g cells per edge (x fastest), element type float
  *    (precision 4) or double (precision 8), base 256-byte aligned.  Leaves
  *    are in the mesh's Morton order (see cello_mesh_leaves).  The library
@@ -63,6 +65,12 @@ typedef struct {
     double gamma;
     int riemann;      /* interface flux of the PPM sweeps: CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC */
     int steepening;   /* 1: contact steepening of the density edge values (Colella & Woodward 1984), 0: off */
+    int dual_energy;  /* 1: the dual-energy formalism (Bryan et al. 1995, cited with the modified PPM of
+                       * Sec. II.C): a sixth field rho*e; the sweep takes the pressure from E - ke where
+                       * that exceeds 1e-3 E, else from rho*e; rho*e is advected with the mass flux,
+                       * takes the compression term -(dt/dx) p (u+ - u-) with the interface-state
+                       * velocities, and is reset to E - ke after each sweep where that exceeds 0.1 E.
+                       * Shared-memory sweep variants only; no adjoint or operation counts.  0: off */
 } cello_mesh_desc;
 
 /* Riemann solvers of the sweep (Sec. II.C, PPM): the Colella-Woodward
@@ -102,7 +110,8 @@ cello_status cello_mesh_from_leaves(const cello_mesh_desc* desc, const int32_t* 
  * (nullable), clears it, and returns CELLO_ENONFINITE if bit 0 was set. */
 cello_status cello_check(cello_mesh* mesh, uint32_t* word);
 
-/* Sizes: leaves, elements per leaf (5 * N^3), coarse-fine faces. */
+/* Sizes: leaves, elements per leaf (fields * N^3: 5, or 6 with dual energy),
+ * coarse-fine faces. */
 cello_status cello_mesh_info(const cello_mesh* mesh, int64_t* n_leaves, int64_t* leaf_elems,
                              int64_t* n_coarse_fine_faces);
 
@@ -194,7 +203,9 @@ cello_status cello_set_exec(cello_mesh* mesh, int mode);
  * pencils per CTA, register bound (minimum resident CTAs per SM) and
  * schedule (one CTA per work item, or one resident wave pulling items from
  * a device counter).  Float32 has 24 variants (12 shared-memory, 12
- * streaming, of which 4 read x pencils as 16-byte vectors), float64 2.  The variants of one form compute the same values;
+ * streaming, of which 4 read x pencils as 16-byte vectors), float64 2; a
+ * dual-energy mesh refuses the streaming ones (CELLO_EINVAL) and the
+ * autotuner skips them (their ms_out entries are -1).  The variants of one form compute the same values;
  * the two float32 forms agree to float32 rounding (a multiply and an add
  * may be fused across what is a register in one form and shared memory in
  * the other).  Cached graphs are dropped. */

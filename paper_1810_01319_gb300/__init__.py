@@ -22,7 +22,7 @@ __all__ = ["Mesh", "make_desc", "PERIODIC", "OUTFLOW", "EXEC_PLAIN", "EXEC_BATCH
 
 
 def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3,
-              precision=8, gamma=1.4, ghosts=4, riemann=0, steepening=0) -> _lib.MeshDesc:
+              precision=8, gamma=1.4, ghosts=4, riemann=0, steepening=0, dual_energy=0) -> _lib.MeshDesc:
     d = _lib.MeshDesc()
     d.root[:] = list(root)
     d.n, d.ghosts, d.max_level = n, ghosts, max_level
@@ -33,6 +33,7 @@ def make_desc(root, n, max_level, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PE
     d.gamma = float(gamma)
     d.riemann = int(riemann)
     d.steepening = int(steepening)
+    d.dual_energy = int(dual_energy)
     return d
 
 
@@ -69,6 +70,7 @@ class Mesh:
         _lib.check(L.cello_mesh_info(out, ctypes.byref(nl), ctypes.byref(le), ctypes.byref(ncf)), "cello_mesh_info")
         self.n_leaves, self.leaf_elems, self.n_coarse_fine = nl.value, le.value, ncf.value
         self.N = desc.n + 2 * desc.ghosts
+        self.nf = 6 if desc.dual_energy else 5   # fields per cell (rho e with dual energy)
         self.dtype = torch.float32 if desc.precision == 4 else torch.float64
 
     def __del__(self):
@@ -95,7 +97,7 @@ class Mesh:
         return kind, idx, fine8
 
     def empty_state(self, device="cuda"):
-        return torch.empty((self.n_leaves, 5, self.N, self.N, self.N), dtype=self.dtype, device=device)
+        return torch.empty((self.n_leaves, self.nf, self.N, self.N, self.N), dtype=self.dtype, device=device)
 
     def _check_state(self, U):
         if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous()
@@ -120,7 +122,8 @@ class Mesh:
         returns U_new (allocated if not given; its ghosts are not written)."""
         old._check_state(U_old)
         if U_new is None:
-            U_new = torch.zeros((self.n_leaves, 5, self.N, self.N, self.N), dtype=self.dtype, device=U_old.device)
+            U_new = torch.zeros((self.n_leaves, self.nf, self.N, self.N, self.N), dtype=self.dtype,
+                                device=U_old.device)
         self._check_state(U_new)
         _lib.check(_lib.lib().cello_remap(old.handle, _ptr(U_old), self.handle, _ptr(U_new), _stream(stream)),
                    "cello_remap")
@@ -166,7 +169,7 @@ class Mesh:
         """Counted operations of the step's three sweeps on the given leaves
         (their slabs are copied to the host; the ghosts must be refreshed).
         Returns (ops [3, 6] per sweep and phase, pencils [3], cells [3], swept
-        host copy [count, 5, N, N, N])."""
+        host copy [count, 5, N, N, N]; five-field meshes only)."""
         ids = np.ascontiguousarray(np.asarray(leaf_ids, dtype=np.int32))
         host = U[torch.as_tensor(ids, dtype=torch.int64, device=U.device)].detach().to("cpu").contiguous()
         out = np.zeros(24, dtype=np.float64)
@@ -246,7 +249,8 @@ class Mesh:
     def autotune(self, U, stream=None):
         """Pick the fastest sweep variant of each axis for this mesh (U is not
         changed).  Returns (chosen variants [x, y, z], best milliseconds of
-        each variant as [[x, y, z], ...])."""
+        each variant as [[x, y, z], ...]; -1 for a variant the mesh cannot
+        use)."""
         self._check_state(U)
         v = (ctypes.c_int * 3)()
         ms = (ctypes.c_float * 192)()
@@ -254,7 +258,7 @@ class Mesh:
                                              ctypes.cast(ms, ctypes.c_void_p), 192, _stream(stream)),
                    "cello_autotune")
         t = [ms[3 * i:3 * i + 3] for i in range(64)]
-        return list(v), [list(x) for x in t if min(x) > 0]
+        return list(v), [list(x) for x in t if any(x)]
 
     def set_sweep_variants(self, variants):
         """One sweep variant per axis (x, y, z)."""

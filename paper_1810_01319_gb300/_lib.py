@@ -21,7 +21,8 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("root", ctypes.c_int * 3), ("n", ctypes.c_int), ("ghosts", ctypes.c_int),
                 ("max_level", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("riemann", ctypes.c_int), ("steepening", ctypes.c_int)]
+                ("riemann", ctypes.c_int), ("steepening", ctypes.c_int),
+                ("dual_energy", ctypes.c_int)]
 
 
 class CelloError(RuntimeError):

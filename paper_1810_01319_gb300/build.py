@@ -26,6 +26,8 @@ UNITS = {
     # float32 bulk path: hardware-approximate division and square root
     "k_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "k_f64.cu": ["-fmad=false"],
+    "k_de_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "k_de_f64.cu": ["-fmad=false"],
     "table.cu": [],
     "mesh.cu": [],
     "noalloc.cu": [],

@@ -8,7 +8,8 @@ import torch
 
 from . import Mesh, make_desc
 
-_DESC_FIELDS = ("root", "n", "ghosts", "max_level", "lo", "hi", "bc", "precision", "gamma", "riemann", "steepening")
+_DESC_FIELDS = ("root", "n", "ghosts", "max_level", "lo", "hi", "bc", "precision", "gamma", "riemann", "steepening",
+                "dual_energy")
 
 
 def save(path, mesh: Mesh, U, **meta):
@@ -23,6 +24,6 @@ def load(path, device="cuda"):
     ck = torch.load(path, map_location="cpu", weights_only=False)
     d = ck["desc"]
     desc = make_desc(d["root"], d["n"], d["max_level"], d["lo"], d["hi"], d["bc"], d["precision"], d["gamma"],
-                     d["ghosts"], d.get("riemann", 0), d.get("steepening", 0))
+                     d["ghosts"], d.get("riemann", 0), d.get("steepening", 0), d.get("dual_energy", 0))
     mesh = Mesh(desc, leaves=ck["leaves"].numpy())
     return mesh, ck["U"].to(device).contiguous(), ck["meta"]

@@ -42,6 +42,7 @@ struct DevMesh {
   double gamma;
   int riemann;            // CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC
   int steepen;            // contact steepening of the density edge values
+  int nf;                 // fields per cell: 5, or 6 with the dual-energy formalism's rho e
   int B;                  // leaves
   const int4* leaf;       // (level, i, j, k)
   const int8_t* kind;     // [B][27]
@@ -142,6 +143,14 @@ int ghost_run_count(int n);
 void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsigned char* out, cudaStream_t s);
 void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
+// Dual-energy sweeps (shared-memory form; k_de_f32.cu, k_de_f64.cu), launched
+// by the planners above with the grid they computed.
+template <int NB, int P, int MINB>
+void launch_sweep_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s);
+template <int NB>
+void launch_sweep_de_f64(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s);
+void prepare_kernels_de_f32();
+void prepare_kernels_de_f64();
 void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces,
                      const int* group_start, int ngroups, const double* reg, const double* dt,
                      cudaStream_t s);

@@ -22,12 +22,12 @@ static int g_resident[3][kNV];   // resident CTAs per GPU by [n index][variant],
 
 static int nb_index(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
 
-// Shared memory of the shared-memory form: 21 arrays of N x P values, 24
-// with contact steepening (weight and two steepened edge values).
+// Shared memory of the shared-memory form: sweep_arrays(RS) arrays of N x P
+// values (21; 24 with contact steepening).
 template <int NB, int P, int RS>
 static constexpr size_t sweep_smem() {
   constexpr int N = NB + 2 * kGhosts;
-  return sizeof(float) * ((RS & 2) ? 24 : 21) * N * P;
+  return sizeof(float) * sweep_arrays(RS) * N * P;
 }
 
 template <int NB, int P, int MINB, int RS>
@@ -86,11 +86,12 @@ static void launch_variant(const DevMesh& m, SweepParams p, int pencils, int v, 
   constexpr int N = NB + 2 * kGhosts;
   int grid = 0;
   if (!plan_launch(p, pencils, P, v, nb_index(NB), grid, s)) return;
-  switch (method_code(m.riemann, m.steepen)) {
+  switch (method_code(m.riemann, m.steepen, m.nf == 6)) {
     case 0: sweep_kernel<float, NB, P, MINB, 0><<<grid, N * P, sweep_smem<NB, P, 0>(), s>>>(m, p); break;
     case 1: sweep_kernel<float, NB, P, MINB, 1><<<grid, N * P, sweep_smem<NB, P, 1>(), s>>>(m, p); break;
     case 2: sweep_kernel<float, NB, P, MINB, 2><<<grid, N * P, sweep_smem<NB, P, 2>(), s>>>(m, p); break;
     case 3: sweep_kernel<float, NB, P, MINB, 3><<<grid, N * P, sweep_smem<NB, P, 3>(), s>>>(m, p); break;
+    default: launch_sweep_de_f32<NB, P, MINB>(m, p, grid, s); break;   // dual energy (k_de_f32.cu)
   }
 }
 
@@ -99,6 +100,7 @@ static void launch_stream_variant(const DevMesh& m, SweepParams p, int pencils, 
   int grid = 0;
   if (!plan_launch(p, pencils, CT, v, nb_index(NB), grid, s)) return;
   constexpr size_t sh = stream_smem<CT, VEC>();
+  if (m.nf != 5) return;   // the streaming form carries five fields; dual-energy meshes never select it
   switch (method_code(m.riemann, m.steepen)) {
     case 0: sweep_stream_kernel<float, NB, CT, MINB, VEC, 0><<<grid, CT, sh, s>>>(m, p); break;
     case 1: sweep_stream_kernel<float, NB, CT, MINB, VEC, 1><<<grid, CT, sh, s>>>(m, p); break;
@@ -144,6 +146,14 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
 }
 
 void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s) {
+  if (m.nf == 6) {
+    switch (m.n) {
+      case 8: reduce_partials_f32_kernel<8, 6><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+      case 16: reduce_partials_f32_kernel<16, 6><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+      case 32: reduce_partials_f32_kernel<32, 6><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+    }
+    return;
+  }
   switch (m.n) {
     case 8: reduce_partials_f32_kernel<8><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
     case 16: reduce_partials_f32_kernel<16><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;

@@ -17,7 +17,7 @@ static int nb_index64(int n) { return n == 8 ? 0 : (n == 16 ? 1 : 2); }
 template <int NB, int RS>
 static constexpr size_t sweep_smem64() {
   constexpr int N = NB + 2 * kGhosts;
-  return sizeof(double) * ((RS & 2) ? 24 : 21) * N * 8;
+  return sizeof(double) * sweep_arrays(RS) * N * 8;
 }
 
 template <int NB, int RS>
@@ -54,11 +54,12 @@ static void launch_nb64(const DevMesh& m, SweepParams p, int pencils, cudaStream
   } else {
     p.work = nullptr;
   }
-  switch (method_code(m.riemann, m.steepen)) {
+  switch (method_code(m.riemann, m.steepen, m.nf == 6)) {
     case 0: sweep_kernel<double, NB, 8, 2, 0><<<grid, N * 8, sweep_smem64<NB, 0>(), s>>>(m, p); break;
     case 1: sweep_kernel<double, NB, 8, 2, 1><<<grid, N * 8, sweep_smem64<NB, 1>(), s>>>(m, p); break;
     case 2: sweep_kernel<double, NB, 8, 2, 2><<<grid, N * 8, sweep_smem64<NB, 2>(), s>>>(m, p); break;
     case 3: sweep_kernel<double, NB, 8, 2, 3><<<grid, N * 8, sweep_smem64<NB, 3>(), s>>>(m, p); break;
+    default: launch_sweep_de_f64<NB>(m, p, grid, s); break;   // dual energy (k_de_f64.cu)
   }
 }
 
@@ -116,8 +117,14 @@ template <typename T, int NB>
 static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, const long long* slow, int nslow,
                       cudaStream_t s) {
   const long threads = (long)ghost_runs<NB>() * nleaf;
-  if (threads > 0) refresh_kernel<T, NB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, U, leaf0, nleaf);
-  if (nslow > 0) refresh_slow_kernel<T, NB><<<(nslow + 127) / 128, 128, 0, s>>>(m, U, slow, nslow);
+  const unsigned grid = (unsigned)((threads + 255) / 256), sgrid = (unsigned)((nslow + 127) / 128);
+  if (m.nf == 6) {
+    if (threads > 0) refresh_kernel<T, NB, 6><<<grid, 256, 0, s>>>(m, U, leaf0, nleaf);
+    if (nslow > 0) refresh_slow_kernel<T, NB, 6><<<sgrid, 128, 0, s>>>(m, U, slow, nslow);
+    return;
+  }
+  if (threads > 0) refresh_kernel<T, NB><<<grid, 256, 0, s>>>(m, U, leaf0, nleaf);
+  if (nslow > 0) refresh_slow_kernel<T, NB><<<sgrid, 128, 0, s>>>(m, U, slow, nslow);
 }
 
 template <typename T>
@@ -154,7 +161,8 @@ void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsign
 
 template <typename T, int NB>
 static void reduce_n(const DevMesh& m, const void* U, double* partials, cudaStream_t s) {
-  reduce_partials_kernel<T, NB><<<m.B, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials);
+  if (m.nf == 6) reduce_partials_kernel<T, NB, 6><<<m.B, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials);
+  else reduce_partials_kernel<T, NB><<<m.B, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials);
 }
 
 void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
@@ -258,8 +266,11 @@ void launch_remap(const DevMesh& neu, const DevMesh& old, const void* Uold, void
   const long threads = (long)neu.B * neu.n * neu.n * neu.n;
   if (threads <= 0) return;
   const unsigned grid = (unsigned)((threads + 255) / 256);
-#define CELLO_RM(T, NB) \
-  remap_kernel<T, NB><<<grid, 256, 0, s>>>(neu, old, static_cast<const T*>(Uold), static_cast<T*>(Unew), map)
+#define CELLO_RM(T, NB)                                                                                      \
+  if (neu.nf == 6)                                                                                          \
+    remap_kernel<T, NB, 6><<<grid, 256, 0, s>>>(neu, old, static_cast<const T*>(Uold), static_cast<T*>(Unew), map); \
+  else                                                                                                      \
+    remap_kernel<T, NB><<<grid, 256, 0, s>>>(neu, old, static_cast<const T*>(Uold), static_cast<T*>(Unew), map)
 #define CELLO_RM_T(T)                       \
   switch (neu.n) {                          \
     case 8: CELLO_RM(T, 8); break;          \
@@ -275,7 +286,11 @@ void launch_flags(const DevMesh& m, const void* U, int precision, int field, dou
                   int8_t* flags, cudaStream_t s) {
   if (m.B <= 0) return;
   const double thr = 2.0 * tau, thr_c = 2.0 * tau_c;
-#define CELLO_FLG(T, NB) flags_kernel<T, NB><<<m.B, 256, 0, s>>>(m, static_cast<const T*>(U), field, thr, thr_c, flags)
+#define CELLO_FLG(T, NB)                                                                                     \
+  if (m.nf == 6)                                                                                            \
+    flags_kernel<T, NB, 6><<<m.B, 256, 0, s>>>(m, static_cast<const T*>(U), field, thr, thr_c, flags);     \
+  else                                                                                                      \
+    flags_kernel<T, NB><<<m.B, 256, 0, s>>>(m, static_cast<const T*>(U), field, thr, thr_c, flags)
 #define CELLO_FLG_T(T)                        \
   switch (m.n) {                              \
     case 8: CELLO_FLG(T, 8); break;           \
@@ -290,8 +305,11 @@ void launch_flags(const DevMesh& m, const void* U, int precision, int field, dou
 void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces, const int* group_start,
                      int ngroups, const double* reg, const double* dt, cudaStream_t s) {
   if (ngroups <= 0) return;
-#define CELLO_FC(T, NB) \
-  fluxcorr_kernel<T, NB><<<ngroups, 256, 0, s>>>(m, static_cast<T*>(U), faces, group_start, reg, dt)
+#define CELLO_FC(T, NB)                                                                                      \
+  if (m.nf == 6)                                                                                            \
+    fluxcorr_kernel<T, NB, 6><<<ngroups, 256, 0, s>>>(m, static_cast<T*>(U), faces, group_start, reg, dt);  \
+  else                                                                                                      \
+    fluxcorr_kernel<T, NB><<<ngroups, 256, 0, s>>>(m, static_cast<T*>(U), faces, group_start, reg, dt)
 #define CELLO_FC_T(T)                       \
   switch (m.n) {                            \
     case 8: CELLO_FC(T, 8); break;          \

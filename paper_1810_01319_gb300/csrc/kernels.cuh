@@ -27,9 +27,19 @@ __device__ __forceinline__ T minmod(T a, T b) {
 //   6 conservative update of cells g..g+n-1.
 // =====================================================================
 // The method variant of a sweep kernel, fixed at compile time so that each
-// kernel carries only what it uses: RS = solver | 2 * steepening, solver
-// CELLO_RIEMANN_TWO_SHOCK (0) or CELLO_RIEMANN_HLLC (1), steepening 0 or 1.
-__host__ __device__ constexpr int method_code(int riemann, int steepen) { return riemann | (steepen << 1); }
+// kernel carries only what it uses: RS = solver | 2 * steepening | 4 * dual
+// energy, solver CELLO_RIEMANN_TWO_SHOCK (0) or CELLO_RIEMANN_HLLC (1),
+// steepening and dual energy 0 or 1.
+__host__ __device__ constexpr int method_code(int riemann, int steepen, int dual = 0) {
+  return riemann | (steepen << 1) | (dual << 2);
+}
+
+// Shared arrays of N x P values of the shared-memory sweep: four groups of
+// one per primitive (5, or 6 with dual energy), the shock detector, three
+// for contact steepening, one for the interface velocities of dual energy.
+__host__ __device__ constexpr int sweep_arrays(int RS) {
+  return 4 * ((RS & 4) ? 6 : 5) + 1 + ((RS & 2) ? 3 : 0) + ((RS & 4) ? 1 : 0);
+}
 
 template <int RS, typename T>
 __device__ __forceinline__ void interface_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
@@ -37,20 +47,29 @@ __device__ __forceinline__ void interface_flux(const T L[5], const T R[5], const
   else riemann_flux_bulk(L, R, gs, F);
 }
 
+template <int RS, typename T>
+__device__ __forceinline__ void interface_flux6(const T L[6], const T R[6], const Gas<T>& gs, T F[6], T* uf) {
+  if (RS & 1) hllc_flux<T, 6>(L, R, gs, F, uf);
+  else riemann_flux_bulk6(L, R, gs, F, uf);
+}
+
 template <typename T, int NB, int P, int MINB, int RS>
 __global__ void __launch_bounds__((NB + 8) * P, MINB)
 sweep_kernel(DevMesh m, SweepParams prm) {
   constexpr int G = kGhosts, N = NB + 2 * G, S = P, A = N * S;
   constexpr long SLAB = (long)N * N * N;
+  constexpr bool DE = (RS & 4) != 0;   // dual energy: a sixth field rho e
+  constexpr int NQ = DE ? 6 : 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sW = reinterpret_cast<T*>(smem_raw);
-  T* sA = sW + 5 * A;   // slopes, then left-edge states
-  T* sB = sA + 5 * A;   // interface values, then fluxes
-  T* sC = sB + 5 * A;   // right-edge states
-  T* sFT = sC + 5 * A;  // shock detector
+  T* sA = sW + NQ * A;  // slopes, then left-edge states
+  T* sB = sA + NQ * A;  // interface values, then fluxes
+  T* sC = sB + NQ * A;  // right-edge states
+  T* sFT = sC + NQ * A; // shock detector
   T* sE = sFT + A;      // contact-steepening weight (RS & 2 only)
   T* sDL = sE + A;      // density left-edge value of the steepened profile
   T* sDR = sDL + A;     // density right-edge value of the steepened profile
+  T* sUF = sFT + A + ((RS & 2) ? 3 * A : 0);   // interface velocities (dual energy only)
 
   const Gas<T> gs = Gas<T>::make(m.gamma);
   T* U = static_cast<T*>(prm.U);
@@ -59,8 +78,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
   const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
   const long sTA = axis == 2 ? N : (long)N * N;   // transverse A: z (x, y sweeps) or y (z sweep)
   const long sTB = axis == 0 ? N : 1;             // transverse B: y (x sweep) or x (y, z sweeps)
-  int comp[5];
-  comp[0] = 0; comp[1] = 1 + axis; comp[4] = 4;
+  int comp[6];
+  comp[0] = 0; comp[1] = 1 + axis; comp[4] = 4; comp[5] = 5;
   comp[2] = axis == 0 ? 2 : 1;
   comp[3] = axis == 2 ? 2 : 3;
 
@@ -92,17 +111,18 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     const bool valid = q < cA * cB;
     const int qa = (int)prm.div_cb.div((unsigned)q);
     const int pa = prm.a0 + (valid ? qa : 0), pb = prm.b0 + (valid ? q - qa * cB : 0);
-    T* base = U + (long)leaf * 5 * SLAB + pa * sTA + pb * sTB + lc * sAx;
-    T Uc[5];
+    T* base = U + (long)leaf * NQ * SLAB + pa * sTA + pb * sTB + lc * sAx;
+    T Uc[NQ];
     if (valid) {
 #pragma unroll
-      for (int f = 0; f < 5; ++f) Uc[f] = base[f * SLAB];
-      T Us[5], W[5];
+      for (int f = 0; f < NQ; ++f) Uc[f] = base[f * SLAB];
+      T Us[NQ], W[NQ];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) Us[k] = Uc[comp[k]];
-      to_primitive(Us, gs, W);
+      for (int k = 0; k < NQ; ++k) Us[k] = Uc[comp[k]];
+      if constexpr (DE) to_primitive_de(Us, gs, W);
+      else to_primitive(Us, gs, W);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) sW[k * A + lc * S + lp] = W[k];
+      for (int k = 0; k < NQ; ++k) sW[k * A + lc * S + lp] = W[k];
     }
     __syncthreads();
 
@@ -110,7 +130,7 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     // ---- phase 2 (slopes of cells 2..N-3: the interfaces used below are 2..N-4)
     if (j >= 2 && j <= N - 3) {
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < NQ; ++k) {
         const T* a = sW + k * A + p;
         sA[k * A + j * S + p] = limited_slope(a[(j - 1) * S], a[j * S], a[(j + 1) * S]);
       }
@@ -125,7 +145,7 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     // ---- phase 3 (interfaces j+1/2 read by cells 3..N-4)
     if (j >= 2 && j <= N - 4) {
 #pragma unroll
-      for (int k = 0; k < 5; ++k)
+      for (int k = 0; k < NQ; ++k)
         sB[k * A + j * S + p] = interface_value(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
                                                 sA[k * A + j * S + p], sA[k * A + (j + 1) * S + p]);
     }
@@ -144,9 +164,9 @@ sweep_kernel(DevMesh m, SweepParams prm) {
       const T s = pr[(j + 1) * S] - pr[(j - 1) * S];
       const T fj = sFT[j * S + p], fm = sFT[(j - 1) * S + p], fpp = sFT[(j + 1) * S + p];
       const T f = (s > T(0)) ? vmax(fj, fm) : ((s < T(0)) ? vmax(fj, fpp) : fj);
-      T W[5], aL[5], aR[5], Wm[5], Wp[5];
+      T W[NQ], aL[NQ], aR[NQ], Wm[NQ], Wp[NQ];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < NQ; ++k) {
         W[k] = sW[k * A + j * S + p];
         aL[k] = sB[k * A + (j - 1) * S + p];
         aR[k] = sB[k * A + j * S + p];
@@ -157,9 +177,9 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         }
         flatten_monotone(W[k], f, aL[k], aR[k]);
       }
-      trace(W, aL, aR, dtdx, gs, Wm, Wp);
+      trace<T, NQ>(W, aL, aR, dtdx, gs, Wm, Wp);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < NQ; ++k) {
         sA[k * A + j * S + p] = Wm[k];
         sC[k * A + j * S + p] = Wp[k];
       }
@@ -167,15 +187,21 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     __syncthreads();
     // ---- phase 5
     if (j >= 3 && j <= N - 5) {
-      T L[5], R[5], F[5];
+      T L[NQ], R[NQ], F[NQ];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < NQ; ++k) {
         L[k] = sC[k * A + j * S + p];
         R[k] = sA[k * A + (j + 1) * S + p];
       }
-      interface_flux<RS>(L, R, gs, F);
+      if constexpr (DE) {
+        T uf;
+        interface_flux6<RS>(L, R, gs, F, &uf);
+        sUF[j * S + p] = uf;
+      } else {
+        interface_flux<RS>(L, R, gs, F);
+      }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) sB[k * A + j * S + p] = F[k];
+      for (int k = 0; k < NQ; ++k) sB[k * A + j * S + p] = F[k];
       if (prm.reg && (j == G - 1 || j == G + NB - 1)) {
         const int qq = tile * P + p;
         if (qq < cA * cB) {
@@ -185,22 +211,31 @@ sweep_kernel(DevMesh m, SweepParams prm) {
             const int face = 2 * axis + (j == G - 1 ? 0 : 1);
             const int slot = m.face_slot[leaf * 6 + face];
             if (slot >= 0) {
-              double* r = prm.reg + (long)slot * 5 * NB * NB + (ca - G) * NB + (cb - G);
+              double* r = prm.reg + (long)slot * NQ * NB * NB + (ca - G) * NB + (cb - G);
 #pragma unroll
-              for (int k = 0; k < 5; ++k) r[(long)comp[k] * NB * NB] = double(F[k]);
+              for (int k = 0; k < NQ; ++k) r[(long)comp[k] * NB * NB] = double(F[k]);
             }
           }
         }
       }
     }
     __syncthreads();
-    // ---- phase 6
+    // ---- phase 6 (dual energy: rho e also takes the compression term
+    // -(dt/dx) p (u+ - u-) with the cell's pressure, then the synchronisation)
     if (valid && lc >= G && lc < G + NB) {
+      T Un[NQ];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < NQ; ++k) {
         const T Fp = sB[k * A + lc * S + lp], Fm = sB[k * A + (lc - 1) * S + lp];
-        base[comp[k] * SLAB] = Uc[comp[k]] - dtdx * sub_rn(Fp, Fm);
+        Un[k] = Uc[comp[k]] - dtdx * sub_rn(Fp, Fm);
       }
+      if constexpr (DE) {
+        const T pc = sW[4 * A + lc * S + lp];
+        Un[5] = Un[5] - (dtdx * pc) * sub_rn(sUF[lc * S + lp], sUF[(lc - 1) * S + lp]);
+        Un[5] = dual_sync(Un);
+      }
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) base[comp[k] * SLAB] = Un[k];
     }
     __syncthreads();
     if (prm.work) {
@@ -519,7 +554,8 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
 }
 
 // =====================================================================
-// Ghost refresh: one thread per ghost cell of a leaf, all five fields.
+// Ghost refresh: one thread per ghost cell of a leaf, all NF fields (five,
+// or six with the dual-energy formalism's rho e).
 // =====================================================================
 template <int NB>
 __device__ __forceinline__ void ghost_coord(int q, int& x, int& y, int& z) {
@@ -542,13 +578,13 @@ __device__ __forceinline__ void ghost_coord(int q, int& x, int& y, int& z) {
 
 // Mean of the 8 cells (fine padded coords f0 + {0,1}^3) of leaf `leaf`,
 // summed in (dz, dy, dx) order, times 0.125.
-template <typename T, int NB>
-__device__ __forceinline__ void restrict8(const T* U, int leaf, int fx, int fy, int fz, T out[5]) {
+template <typename T, int NB, int NF = 5>
+__device__ __forceinline__ void restrict8(const T* U, int leaf, int fx, int fy, int fz, T out[NF]) {
   constexpr int N = NB + 2 * kGhosts;
   constexpr long SLAB = (long)N * N * N;
-  const T* b = U + (long)leaf * 5 * SLAB + ((long)fz * N + fy) * N + fx;
+  const T* b = U + (long)leaf * NF * SLAB + ((long)fz * N + fy) * N + fx;
 #pragma unroll
-  for (int f = 0; f < 5; ++f) {
+  for (int f = 0; f < NF; ++f) {
     const T* c = b + f * SLAB;
     T v = c[0];
     v = v + c[1];
@@ -562,13 +598,13 @@ __device__ __forceinline__ void restrict8(const T* U, int leaf, int fx, int fy, 
   }
 }
 
-template <typename T, int NB>
-__device__ __forceinline__ void load5(const T* U, int leaf, int x, int y, int z, T out[5]) {
+template <typename T, int NB, int NF = 5>
+__device__ __forceinline__ void load5(const T* U, int leaf, int x, int y, int z, T out[NF]) {
   constexpr int N = NB + 2 * kGhosts;
   constexpr long SLAB = (long)N * N * N;
-  const T* b = U + (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x;
+  const T* b = U + (long)leaf * NF * SLAB + ((long)z * N + y) * N + x;
 #pragma unroll
-  for (int f = 0; f < 5; ++f) out[f] = b[f * SLAB];
+  for (int f = 0; f < NF; ++f) out[f] = b[f * SLAB];
 }
 
 // Value of the level-(L-1) cell r (local to the coarse leaf C, r[a] may be
@@ -576,26 +612,26 @@ __device__ __forceinline__ void load5(const T* U, int leaf, int x, int y, int z,
 // C's own cell, a same-level copy, a restriction from level-L leaves, an
 // injection from the level-(L-2) leaf, or C's cell itself behind an outflow
 // boundary.
-template <typename T, int NB>
+template <typename T, int NB, int NF = 5>
 __device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int rc[3], int a, int side,
-                                const T Uc[5], T out[5]) {
+                                const T Uc[NF], T out[NF]) {
   constexpr int G = kGhosts, H = NB / 2;
   const int fe = face_dir(a, side);
   const int e = C * 27 + fe;
   const int8_t k = m.kind[e];
   if (k == kBoundary) {
 #pragma unroll
-    for (int f = 0; f < 5; ++f) out[f] = Uc[f];
+    for (int f = 0; f < NF; ++f) out[f] = Uc[f];
     return;
   }
   int r2[3] = {rc[0], rc[1], rc[2]};
   r2[a] = side < 0 ? NB - 1 : 0;   // position inside the neighbour node
   if (k == kSame) {
-    load5<T, NB>(U, m.idx[e], r2[0] + G, r2[1] + G, r2[2] + G, out);
+    load5<T, NB, NF>(U, m.idx[e], r2[0] + G, r2[1] + G, r2[2] + G, out);
   } else if (k == kFine) {
     const int o0 = r2[0] / H, o1 = r2[1] / H, o2 = r2[2] / H;
     const int child = m.fine8[e * 8 + o2 * 4 + o1 * 2 + o0];
-    restrict8<T, NB>(U, child, 2 * r2[0] - o0 * NB + G, 2 * r2[1] - o1 * NB + G, 2 * r2[2] - o2 * NB + G, out);
+    restrict8<T, NB, NF>(U, child, 2 * r2[0] - o0 * NB + G, 2 * r2[1] - o1 * NB + G, 2 * r2[2] - o2 * NB + G, out);
   } else {  // coarser: inject the level-(L-2) cell
     const int4 cl = m.leaf[C];
     const int K = m.idx[e];
@@ -606,14 +642,14 @@ __device__ void slope_neighbour(const DevMesh& m, const T* U, int C, const int r
     const int ncell = (m.root[a] << Lc) * NB;
     g[a] = wrap_mod(g[a], ncell);
     const int lx = (g[0] >> 1) - kl.y * NB, ly = (g[1] >> 1) - kl.z * NB, lz = (g[2] >> 1) - kl.w * NB;
-    load5<T, NB>(U, K, lx + G, ly + G, lz + G, out);
+    load5<T, NB, NF>(U, K, lx + G, ly + G, lz + G, out);
   }
 }
 
 // Value of one ghost cell (padded coords c, already inside the block
 // array) of leaf `leaf`: same-level copy, restriction or prolongation.
-template <typename T, int NB>
-__device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T v[5]) {
+template <typename T, int NB, int NF = 5>
+__device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T v[NF]) {
   constexpr int G = kGhosts, H = NB / 2;
   int d[3];
 #pragma unroll
@@ -627,7 +663,7 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
   const int e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
   const int8_t k = m.kind[e];
   if (k == kSame) {
-    load5<T, NB>(U, m.idx[e], c[0] - d[0] * NB, c[1] - d[1] * NB, c[2] - d[2] * NB, v);
+    load5<T, NB, NF>(U, m.idx[e], c[0] - d[0] * NB, c[1] - d[1] * NB, c[2] - d[2] * NB, v);
   } else if (k == kFine) {
     int r[3], o[3];
 #pragma unroll
@@ -636,7 +672,7 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
       o[a] = r[a] / H;
     }
     const int child = m.fine8[e * 8 + o[2] * 4 + o[1] * 2 + o[0]];
-    restrict8<T, NB>(U, child, 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G, 2 * r[2] - o[2] * NB + G, v);
+    restrict8<T, NB, NF>(U, child, 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G, 2 * r[2] - o[2] * NB + G, v);
   } else {  // coarse: conservative minmod-limited linear prolongation
     const int4 lf = m.leaf[leaf];
     const int C = m.idx[e];
@@ -652,24 +688,24 @@ __device__ void ghost_value(const DevMesh& m, const T* U, int leaf, int c[3], T 
       rc[a] = (gl >> 1) - cij[a] * NB;
       sgn[a] = (gl & 1) ? T(1) : T(-1);
     }
-    T Uc[5];
-    load5<T, NB>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
-    T D[3][5];
+    T Uc[NF];
+    load5<T, NB, NF>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+    T D[3][NF];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      T Um[5], Up[5];
+      T Um[NF], Up[NF];
       int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
       rm[a] -= 1;
       rp[a] += 1;
-      if (rm[a] >= 0) load5<T, NB>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
-      else slope_neighbour<T, NB>(m, U, C, rc, a, -1, Uc, Um);
-      if (rp[a] < NB) load5<T, NB>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
-      else slope_neighbour<T, NB>(m, U, C, rc, a, 1, Uc, Up);
+      if (rm[a] >= 0) load5<T, NB, NF>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB, NF>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, 1, Uc, Up);
 #pragma unroll
-      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+      for (int f = 0; f < NF; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
     }
 #pragma unroll
-    for (int f = 0; f < 5; ++f)
+    for (int f = 0; f < NF; ++f)
       v[f] = Uc[f] + T(0.25) * ((sgn[0] * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
   }
 }
@@ -723,7 +759,7 @@ __device__ __forceinline__ bool run_is_copy(const DevMesh& m, int leaf, int x0, 
 
 // Same-level copies: one thread per run, one 16-byte vector per field.  Runs
 // that are not plain copies are left to refresh_slow_kernel.
-template <typename T, int NB>
+template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
   constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
   constexpr long SLAB = (long)N * N * N;
@@ -733,21 +769,21 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0
   int x0, y, z, c[3], d[3], e;
   ghost_coord<NB>((int)(gid % NS) * 4, x0, y, z);
   if (!run_is_copy<NB>(m, leaf, x0, y, z, c, d, e)) return;
-  const long dst = (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x0;
-  const long src = (long)m.idx[e] * 5 * SLAB + ((long)(c[2] - d[2] * NB) * N + (c[1] - d[1] * NB)) * N +
+  const long dst = (long)leaf * NF * SLAB + ((long)z * N + y) * N + x0;
+  const long src = (long)m.idx[e] * NF * SLAB + ((long)(c[2] - d[2] * NB) * N + (c[1] - d[1] * NB)) * N +
                    (c[0] - d[0] * NB);
-  Vec4<T> v[5];
+  Vec4<T> v[NF];
 #pragma unroll
-  for (int f = 0; f < 5; ++f) v[f].load(U + src + f * SLAB);
+  for (int f = 0; f < NF; ++f) v[f].load(U + src + f * SLAB);
 #pragma unroll
-  for (int f = 0; f < 5; ++f) v[f].store(U + dst + f * SLAB);
+  for (int f = 0; f < NF; ++f) v[f].store(U + dst + f * SLAB);
 }
 
 // The remaining runs (listed per mesh as leaf * runs + run), one run of four
 // cells per thread: a run clamped along x repeats one value; a run inside a
 // finer neighbour restricts cell by cell; a run inside a coarser neighbour
 // covers two parent cells, each prolonged once for its two children.
-template <typename T, int NB>
+template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, const long long* runs, int nruns) {
   constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
   constexpr long SLAB = (long)N * N * N;
@@ -757,7 +793,7 @@ __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, cons
   const int leaf = (int)(r / NS);
   int x0, y, z;
   ghost_coord<NB>((int)(r % NS) * 4, x0, y, z);
-  const long dst = (long)leaf * 5 * SLAB + ((long)z * N + y) * N + x0;
+  const long dst = (long)leaf * NF * SLAB + ((long)z * N + y) * N + x0;
   int d[3] = {x0 < G ? -1 : (x0 >= G + NB ? 1 : 0), y < G ? -1 : (y >= G + NB ? 1 : 0),
               z < G ? -1 : (z >= G + NB ? 1 : 0)};
   int c[3] = {x0, y, z};
@@ -773,20 +809,20 @@ __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, cons
   const int8_t k = m.kind[e];
   if (xclamp) {   // every cell of the run reads the same boundary cell
     int cc[3] = {c[0], c[1], c[2]};
-    T v[5];
-    ghost_value<T, NB>(m, U, leaf, cc, v);
+    T v[NF];
+    ghost_value<T, NB, NF>(m, U, leaf, cc, v);
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int f = 0; f < 5; ++f) U[dst + q + f * SLAB] = v[f];
+      for (int f = 0; f < NF; ++f) U[dst + q + f * SLAB] = v[f];
     return;
   }
   if (k != kCoarse) {
     for (int q = 0; q < 4; ++q) {
       int cc[3] = {x0 + q, y, z};
-      T v[5];
-      ghost_value<T, NB>(m, U, leaf, cc, v);
+      T v[NF];
+      ghost_value<T, NB, NF>(m, U, leaf, cc, v);
 #pragma unroll
-      for (int f = 0; f < 5; ++f) U[dst + q + f * SLAB] = v[f];
+      for (int f = 0; f < NF; ++f) U[dst + q + f * SLAB] = v[f];
     }
     return;
   }
@@ -809,26 +845,26 @@ __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, cons
   for (int h = 0; h < 2; ++h) {
     const int gl = wrap_mod(lij[0] * NB + (x0 + 2 * h - G), ncx);   // even: the lower child
     int rc[3] = {(gl >> 1) - cij[0] * NB, rcyz[1], rcyz[2]};
-    T Uc[5], D[3][5];
-    load5<T, NB>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+    T Uc[NF], D[3][NF];
+    load5<T, NB, NF>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      T Um[5], Up[5];
+      T Um[NF], Up[NF];
       int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
       rm[a] -= 1;
       rp[a] += 1;
-      if (rm[a] >= 0) load5<T, NB>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
-      else slope_neighbour<T, NB>(m, U, C, rc, a, -1, Uc, Um);
-      if (rp[a] < NB) load5<T, NB>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
-      else slope_neighbour<T, NB>(m, U, C, rc, a, 1, Uc, Up);
+      if (rm[a] >= 0) load5<T, NB, NF>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB, NF>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, 1, Uc, Up);
 #pragma unroll
-      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+      for (int f = 0; f < NF; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const T sx = q ? T(1) : T(-1);
 #pragma unroll
-      for (int f = 0; f < 5; ++f)
+      for (int f = 0; f < NF; ++f)
         U[dst + 2 * h + q + f * SLAB] = Uc[f] + T(0.25) * ((sx * D[0][f] + sgn[1] * D[1][f]) + sgn[2] * D[2][f]);
     }
   }
@@ -852,7 +888,7 @@ __global__ void __launch_bounds__(256) classify_runs_kernel(DevMesh m, const int
 // =====================================================================
 // Remap onto a rebuilt mesh: one thread per interior cell of a new leaf.
 // =====================================================================
-template <typename T, int NB>
+template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(256) remap_kernel(DevMesh neu, DevMesh old, const T* Uold, T* Unew,
                                                     const RemapEntry* map) {
   constexpr int G = kGhosts, N = NB + 2 * G, H = NB / 2;
@@ -863,12 +899,12 @@ __global__ void __launch_bounds__(256) remap_kernel(DevMesh neu, DevMesh old, co
   const int i = (int)(gid % (NB * NB * NB));
   const int r[3] = {i % NB, (i / NB) % NB, i / (NB * NB)};
   const RemapEntry e = map[leaf];
-  T v[5];
+  T v[NF];
   if (e.kind == 0) {
-    load5<T, NB>(Uold, e.src[0], r[0] + G, r[1] + G, r[2] + G, v);
+    load5<T, NB, NF>(Uold, e.src[0], r[0] + G, r[1] + G, r[2] + G, v);
   } else if (e.kind == 2) {
     const int o[3] = {r[0] / H, r[1] / H, r[2] / H};
-    restrict8<T, NB>(Uold, e.src[o[2] * 4 + o[1] * 2 + o[0]], 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G,
+    restrict8<T, NB, NF>(Uold, e.src[o[2] * 4 + o[1] * 2 + o[0]], 2 * r[0] - o[0] * NB + G, 2 * r[1] - o[1] * NB + G,
                      2 * r[2] - o[2] * NB + G, v);
   } else {
     const int4 nl = neu.leaf[leaf];
@@ -883,25 +919,25 @@ __global__ void __launch_bounds__(256) remap_kernel(DevMesh neu, DevMesh old, co
       c[a] = (gf >> k) - aij[a] * NB + G;
       xi[a] = T((double((gf & ((1 << k) - 1))) + 0.5) / double(1 << k) - 0.5);
     }
-    T Uc[5], D[3][5];
-    load5<T, NB>(Uold, e.src[0], c[0], c[1], c[2], Uc);
+    T Uc[NF], D[3][NF];
+    load5<T, NB, NF>(Uold, e.src[0], c[0], c[1], c[2], Uc);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
       cm[a] -= 1;
       cp[a] += 1;
-      T Um[5], Up[5];
-      load5<T, NB>(Uold, e.src[0], cm[0], cm[1], cm[2], Um);
-      load5<T, NB>(Uold, e.src[0], cp[0], cp[1], cp[2], Up);
+      T Um[NF], Up[NF];
+      load5<T, NB, NF>(Uold, e.src[0], cm[0], cm[1], cm[2], Um);
+      load5<T, NB, NF>(Uold, e.src[0], cp[0], cp[1], cp[2], Up);
 #pragma unroll
-      for (int f = 0; f < 5; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+      for (int f = 0; f < NF; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
     }
 #pragma unroll
-    for (int f = 0; f < 5; ++f) v[f] = Uc[f] + ((xi[0] * D[0][f] + xi[1] * D[1][f]) + xi[2] * D[2][f]);
+    for (int f = 0; f < NF; ++f) v[f] = Uc[f] + ((xi[0] * D[0][f] + xi[1] * D[1][f]) + xi[2] * D[2][f]);
   }
-  const long dst = (long)leaf * 5 * SLAB + ((long)(r[2] + G) * N + (r[1] + G)) * N + (r[0] + G);
+  const long dst = (long)leaf * NF * SLAB + ((long)(r[2] + G) * N + (r[1] + G)) * N + (r[0] + G);
 #pragma unroll
-  for (int f = 0; f < 5; ++f) Unew[dst + f * SLAB] = v[f];
+  for (int f = 0; f < NF; ++f) Unew[dst + f * SLAB] = v[f];
 }
 
 // =====================================================================
@@ -935,7 +971,9 @@ __device__ __forceinline__ void block_reduce6(double v[6], double* sh) {
   }
 }
 
-template <typename T, int NB>
+// NF = 6 (dual energy): the pressure for the sound speed and the health
+// check is selected as in the sweep's primitives, from E - ke or from rho e.
+template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh m, const T* U, double* partials) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
@@ -944,7 +982,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh
   const int4 lf = m.leaf[leaf];
   const T dx = T(ldexp(m.dx0, -lf.x));
   const T gamma = T(m.gamma), gm1 = T(m.gamma - 1.0);
-  const T* b = U + (long)leaf * 5 * SLAB;
+  const T* b = U + (long)leaf * NF * SLAB;
   double v[6] = {INFINITY, 0, 0, 0, 0, 0};
   int bad = 0;
   for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
@@ -954,7 +992,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh
     const T rho = vmax(r0, T(kRhoFloor));
     const T u = m1 / rho, vv = m2 / rho, w = m3 / rho;
     const T ke = (T(0.5) * rho) * (u * u + (vv * vv + w * w));
-    const T praw = gm1 * (E - ke);
+    T src = E - ke;
+    if constexpr (NF == 6) src = (src > T(kDualEta1) * E) ? src : b[5 * SLAB + o];
+    const T praw = gm1 * src;
     bad |= !(r0 > T(0)) || !(praw > T(0)) || !isfinite(praw + (m1 + m2 + m3));
     const T p = vmax(praw, T(kPFloor));
     const T c = vsqrt((gamma * p) / rho);
@@ -985,7 +1025,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += e;
 }
 
-template <int NB>
+template <int NB, int NF = 5>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(DevMesh m, const float* U,
                                                                              double* partials) {
   constexpr int G = kGhosts, N = NB + 2 * G;
@@ -995,7 +1035,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
   const int4 lf = m.leaf[leaf];
   const float dx = float(ldexp(m.dx0, -lf.x));
   const float gamma = float(m.gamma), gm1 = float(m.gamma - 1.0);
-  const float* b = U + (long)leaf * 5 * SLAB;
+  const float* b = U + (long)leaf * NF * SLAB;
   float mn = INFINITY, hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
@@ -1005,7 +1045,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
     const float rho = vmax(r0, float(kRhoFloor));
     const float u = m1 / rho, vv = m2 / rho, w = m3 / rho;
     const float ke = (0.5f * rho) * (u * u + (vv * vv + w * w));
-    const float praw = gm1 * (E - ke);
+    float src = E - ke;
+    if constexpr (NF == 6) src = (src > float(kDualEta1) * E) ? src : b[5 * SLAB + o];
+    const float praw = gm1 * src;
     bad |= !(r0 > 0.0f) || !(praw > 0.0f) || !isfinite(praw + (m1 + m2 + m3));
     const float p = vmax(praw, float(kPFloor));
     const float c = sqrtf((gamma * p) / rho);
@@ -1053,14 +1095,14 @@ __global__ void __launch_bounds__(1024) reduce_finish_kernel(const double* parti
 // =====================================================================
 // Refinement flags: relative slope of rho or p, compared in float64.
 // =====================================================================
-template <typename T, int NB>
+template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(256) flags_kernel(DevMesh m, const T* U, int field, double thr, double thr_c,
                                                     int8_t* flags) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   const int leaf = blockIdx.x;
   const int4 lf = m.leaf[leaf];
-  const T* b = U + (long)leaf * 5 * SLAB;
+  const T* b = U + (long)leaf * NF * SLAB;
   const double gm1 = m.gamma - 1.0;
   auto q = [&](long o) -> double {
     const double r0 = double(b[o]);
@@ -1068,7 +1110,10 @@ __global__ void __launch_bounds__(256) flags_kernel(DevMesh m, const T* U, int f
     if (field == 0) return rho;
     const double u = double(b[SLAB + o]) / rho, v = double(b[2 * SLAB + o]) / rho, w = double(b[3 * SLAB + o]) / rho;
     const double ke = (0.5 * rho) * (u * u + (v * v + w * w));
-    const double p = gm1 * (double(b[4 * SLAB + o]) - ke);
+    const double E = double(b[4 * SLAB + o]);
+    double src = E - ke;
+    if constexpr (NF == 6) src = (src > kDualEta1 * E) ? src : double(b[5 * SLAB + o]);
+    const double p = gm1 * src;
     return p > kPFloor ? p : kPFloor;
   };
   int hit = 0, hit_c = 0;
@@ -1098,7 +1143,7 @@ __global__ void __launch_bounds__(256) flags_kernel(DevMesh m, const T* U, int f
 // Coarse-fine flux correction: one CTA per coarse leaf, its faces in order
 // -x, +x, -y, +y, -z, +z, arithmetic in float64.
 // =====================================================================
-template <typename T, int NB>
+template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(256) fluxcorr_kernel(DevMesh m, T* U, const CoarseFace* faces,
                                                        const int* group_start, const double* reg,
                                                        const double* dt) {
@@ -1115,15 +1160,15 @@ __global__ void __launch_bounds__(256) fluxcorr_kernel(DevMesh m, T* U, const Co
       const int t1 = i % NB, t2 = i / NB;
       const int o1 = t1 / H, o2 = t2 / H;
       const int b1 = t1 - o1 * H, b2 = t2 - o2 * H;
-      const double* Rf = reg + (long)cf.fslot[o2 * 2 + o1] * 5 * FS + (2 * b2) * NB + 2 * b1;
-      const double* Rc = reg + (long)cf.cslot * 5 * FS + t2 * NB + t1;
+      const double* Rf = reg + (long)cf.fslot[o2 * 2 + o1] * NF * FS + (2 * b2) * NB + 2 * b1;
+      const double* Rc = reg + (long)cf.cslot * NF * FS + t2 * NB + t1;
       int cc[3];
       cc[cf.axis] = cf.side > 0 ? G + NB - 1 : G;
       cc[t1a] = G + t1;
       cc[t2a] = G + t2;
-      T* cell = U + (long)cf.leaf * 5 * SLAB + ((long)cc[2] * N + cc[1]) * N + cc[0];
+      T* cell = U + (long)cf.leaf * NF * SLAB + ((long)cc[2] * N + cc[1]) * N + cc[0];
 #pragma unroll
-      for (int f = 0; f < 5; ++f) {
+      for (int f = 0; f < NF; ++f) {
         const double* r = Rf + f * FS;
         const double mean = ((r[0] + r[1]) + (r[NB] + r[NB + 1])) * 0.25;
         const double corr = (dtdx * (Rc[f * FS] - mean)) * double(cf.side);

@@ -21,6 +21,9 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Fields per cell: five conserved, plus rho e with the dual-energy formalism.
+int nfields(const cello_mesh_desc& d) { return d.dual_energy ? 6 : 5; }
+
 cello_status fail(cello_status st, const std::string& msg) {
   g_last_error = msg;
   return st;
@@ -114,6 +117,8 @@ void prepare_kernels() {
   std::call_once(once, [] {
     prepare_kernels_f32();
     prepare_kernels_f64();
+    prepare_kernels_de_f32();
+    prepare_kernels_de_f64();
   });
 }
 }  // namespace cello
@@ -175,6 +180,7 @@ struct cello_mesh {
     m.gamma = desc.gamma;
     m.riemann = desc.riemann;
     m.steepen = desc.steepening;
+    m.nf = desc.dual_energy ? 6 : 5;
     m.B = B;
     m.leaf = d_leaf;
     m.kind = d_kind;
@@ -223,6 +229,7 @@ cello_status check_desc(const cello_mesh_desc* d) {
   if (d->riemann != CELLO_RIEMANN_TWO_SHOCK && d->riemann != CELLO_RIEMANN_HLLC)
     return fail(CELLO_EINVAL, "riemann must be CELLO_RIEMANN_TWO_SHOCK or CELLO_RIEMANN_HLLC");
   if (d->steepening != 0 && d->steepening != 1) return fail(CELLO_EINVAL, "steepening must be 0 or 1");
+  if (d->dual_energy != 0 && d->dual_energy != 1) return fail(CELLO_EINVAL, "dual_energy must be 0 or 1");
   double ext[3];
   for (int a = 0; a < 3; ++a) {
     if (d->root[a] < 1 || d->root[a] > 1024) return fail(CELLO_EINVAL, "root blocks per axis must be in [1, 1024]");
@@ -402,7 +409,7 @@ cello_status finish_build(cello_mesh* M) {
   CELLO_TRY(upload(&M->d_face_slot, M->face_slot));
   CELLO_TRY(upload(&M->d_cfaces, M->cfaces));
   CELLO_TRY(upload(&M->d_group_start, M->group_start));
-  if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * 5 * d.n * d.n * sizeof(double)));
+  if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * nfields(d) * d.n * d.n * sizeof(double)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_partials, (size_t)std::max(B, 1) * 6 * sizeof(double)));
   // ghost runs the vector-copy refresh leaves to the per-cell kernel: only
   // leaves with a neighbour that is not a same-level leaf can have any
@@ -528,8 +535,8 @@ cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double
   bool uniform_periodic = true;   // then the ghost copy's transpose is a deterministic gather
   for (int a = 0; a < 3; ++a) uniform_periodic = uniform_periodic && d.bc[a] == CELLO_PERIODIC;
   for (int b = 1; b < M->B && uniform_periodic; ++b) uniform_periodic = M->leaves[b].x == M->leaves[0].x;
-  const size_t state = (size_t)M->B * 5 * M->N * M->N * M->N * d.precision;
-  const size_t regs = (size_t)M->nslots * 5 * d.n * d.n * sizeof(double);
+  const size_t state = (size_t)M->B * nfields(d) * M->N * M->N * M->N * d.precision;
+  const size_t regs = (size_t)M->nslots * nfields(d) * d.n * d.n * sizeof(double);
   if (M->adj_bytes < 3 * state + regs) {
     if (M->adj_scratch) cudaFree(M->adj_scratch);
     M->adj_scratch = nullptr;
@@ -709,7 +716,7 @@ void cello_mesh_free(cello_mesh* mesh) { delete mesh; }
 cello_status cello_mesh_info(const cello_mesh* M, int64_t* n_leaves, int64_t* leaf_elems, int64_t* n_cf) {
   if (!M) return fail(CELLO_EINVAL, "mesh is NULL");
   if (n_leaves) *n_leaves = M->B;
-  if (leaf_elems) *leaf_elems = 5LL * M->N * M->N * M->N;
+  if (leaf_elems) *leaf_elems = (int64_t)nfields(M->desc) * M->N * M->N * M->N;
   if (n_cf) *n_cf = (int64_t)M->cfaces.size();
   return CELLO_OK;
 }
@@ -856,8 +863,9 @@ cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, 
                                       void* stream) {
   if (!M || !Un || !lam || !dt) return fail(CELLO_EINVAL, "NULL argument");
   if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
-  if (M->desc.riemann != CELLO_RIEMANN_TWO_SHOCK || M->desc.steepening)
-    return fail(CELLO_EINVAL, "the adjoint step is written for the two-shock solver without contact steepening");
+  if (M->desc.riemann != CELLO_RIEMANN_TWO_SHOCK || M->desc.steepening || M->desc.dual_energy)
+    return fail(CELLO_EINVAL,
+                "the adjoint step is written for the two-shock solver without contact steepening or dual energy");
   return adjoint_step(M, Un, lam, dt, cycle, (cudaStream_t)stream);
 }
 
@@ -866,6 +874,10 @@ cello_status cello_set_sweep_variants(cello_mesh* M, const int* variants) {
   const int nv = M->desc.precision == 4 ? sweep_variant_count_f32() : sweep_variant_count_f64();
   for (int a = 0; a < 3; ++a)
     if (variants[a] < 0 || variants[a] >= nv) return fail(CELLO_EINVAL, "sweep variant out of range");
+  if (M->desc.dual_energy && M->desc.precision == 4)
+    for (int a = 0; a < 3; ++a)
+      if (sweep_variant_f32(variants[a]).stream)
+        return fail(CELLO_EINVAL, "the streaming sweep carries five fields: dual-energy meshes take shared-memory variants");
   for (int a = 0; a < 3; ++a) M->sweep_variant[a] = variants[a];
   for (auto& g : M->graphs) cudaGraphExecDestroy(g.exec);
   M->graphs.clear();
@@ -890,6 +902,11 @@ cello_status cello_autotune(cello_mesh* M, void* U, int* variants_out, float* ms
   float best_ms[3] = {1e30f, 1e30f, 1e30f};
   cudaError_t err = cudaSuccess;
   for (int v = 0; v < nv && err == cudaSuccess; ++v) {
+    if (d.dual_energy && d.precision == 4 && sweep_variant_f32(v).stream) {
+      for (int a = 0; a < 3; ++a)
+        if (ms_out && 3 * v + a < ms_len) ms_out[3 * v + a] = -1.0f;
+      continue;
+    }
     float vbest[3] = {1e30f, 1e30f, 1e30f};
     for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
       float axis_ms[3] = {0, 0, 0};
@@ -947,7 +964,7 @@ cello_status cello_hydro_step_host(cello_mesh* M, void* U_host, void* U_dev, dou
                                    int cycle, double cfl, double* scratch_dev, double* out_host, void* stream) {
   if (!M || !U_host || !U_dev || !dt_dev || !scratch_dev || !out_host) return fail(CELLO_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)M->B * 5 * M->N * M->N * M->N * (size_t)M->desc.precision;
+  const size_t bytes = (size_t)M->B * nfields(M->desc) * M->N * M->N * M->N * (size_t)M->desc.precision;
   CELLO_CUDA(cudaMemcpyAsync(U_dev, U_host, bytes, cudaMemcpyHostToDevice, s));
   CELLO_CUDA(cudaMemcpyAsync(dt_dev, &dt_host, sizeof(double), cudaMemcpyHostToDevice, s));
   CELLO_TRY(cello_hydro_step(M, U_dev, dt_dev, cycle, cfl, scratch_dev, scratch_dev + 1, stream));
@@ -997,6 +1014,7 @@ cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32
                                  double dt, int cycle, double* out) {
   if (!M || !U_host || !leaf_ids || !out || count <= 0) return fail(CELLO_EINVAL, "NULL argument or empty sample");
   if (M->desc.precision != 4) return fail(CELLO_EINVAL, "operation counts are taken on float32 meshes");
+  if (M->desc.dual_energy) return fail(CELLO_EINVAL, "operation counts cover the five-field sweep");
   for (int64_t i = 0; i < count; ++i)
     if (leaf_ids[i] < 0 || leaf_ids[i] >= M->B) return fail(CELLO_EINVAL, "leaf id out of range");
   const cello_mesh_desc& d = M->desc;

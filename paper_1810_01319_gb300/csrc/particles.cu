@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256, 3) particles_push_kernel(PartMesh P, cons
     i0[a] = (int)c + g;
     f[a] = s - c;
   }
-  const T* blk = U + (long)b * 5 * SLAB;
+  const T* blk = U + (long)b * m.nf * SLAB;
   const long o000 = ((long)i0[2] * N + i0[1]) * N + i0[0];
   const long sx = 1, sy = N, sz = (long)N * N;
   const double dt = *dt_dev;

@@ -102,6 +102,70 @@ CELLO_HD void to_primitive(const float U[5], const Gas<float>& gs, float W[5]) {
   W[0] = rho; W[1] = un; W[2] = ut1; W[3] = ut2; W[4] = p;
 }
 
+// Dual-energy formalism (Bryan et al. 1995): a sixth field, the internal
+// energy density rho e.  The pressure comes from E - ke where that exceeds
+// kDualEta1 E, else from rho e; after a sweep's update rho e is reset to
+// E - ke where that exceeds kDualEta2 E.
+constexpr double kDualEta1 = 1e-3;
+constexpr double kDualEta2 = 0.1;
+
+// (rho, m_n, m_t1, m_t2, E, rho e) -> (rho, u_n, u_t1, u_t2, p, e).
+template <typename T>
+CELLO_HD void to_primitive_de(const T U[6], const Gas<T>& gs, T W[6]) {
+  T rho = vmax(U[0], T(kRhoFloor));
+  T un = U[1] / rho;
+  T ut1 = U[2] / rho;
+  T ut2 = U[3] / rho;
+  T ke = (T(0.5) * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
+  const T eint = U[4] - ke;
+  const T src = (eint > T(kDualEta1) * U[4]) ? eint : U[5];
+  W[0] = rho; W[1] = un; W[2] = ut1; W[3] = ut2;
+  W[4] = vmax(gs.gm1 * src, T(kPFloor));
+  W[5] = U[5] / rho;
+}
+
+CELLO_HD void to_primitive_de(const float U[6], const Gas<float>& gs, float W[6]) {
+  const float rho = vmax(U[0], float(kRhoFloor));
+  const float ir = vdiv(1.0f, rho);
+#ifdef __CUDA_ARCH__
+  const float un = __fmul_rn(U[1], ir), ut1 = __fmul_rn(U[2], ir), ut2 = __fmul_rn(U[3], ir);
+  const float e = __fmul_rn(U[5], ir);
+#else
+  const float un = U[1] * ir, ut1 = U[2] * ir, ut2 = U[3] * ir, e = U[5] * ir;
+#endif
+  const float ke = (0.5f * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
+  const float eint = U[4] - ke;
+  const float src = (eint > float(kDualEta1) * U[4]) ? eint : U[5];
+  W[0] = rho; W[1] = un; W[2] = ut1; W[3] = ut2;
+  W[4] = vmax(gs.gm1 * src, float(kPFloor));
+  W[5] = e;
+}
+
+// The synchronised rho e of an updated cell (sweep-ordered state U[6]).
+template <typename T>
+CELLO_HD T dual_sync(const T U[6]) {
+  T rho = vmax(U[0], T(kRhoFloor));
+  T un = U[1] / rho;
+  T ut1 = U[2] / rho;
+  T ut2 = U[3] / rho;
+  T ke = (T(0.5) * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
+  const T eint = U[4] - ke;
+  return (eint > T(kDualEta2) * U[4]) ? eint : U[5];
+}
+
+CELLO_HD float dual_sync(const float U[6]) {
+  const float rho = vmax(U[0], float(kRhoFloor));
+  const float ir = vdiv(1.0f, rho);
+#ifdef __CUDA_ARCH__
+  const float un = __fmul_rn(U[1], ir), ut1 = __fmul_rn(U[2], ir), ut2 = __fmul_rn(U[3], ir);
+#else
+  const float un = U[1] * ir, ut1 = U[2] * ir, ut2 = U[3] * ir;
+#endif
+  const float ke = (0.5f * rho) * (un * un + (ut1 * ut1 + ut2 * ut2));
+  const float eint = U[4] - ke;
+  return (eint > float(kDualEta2) * U[4]) ? eint : U[5];
+}
+
 // Monotonised centred slope, zero at a local extremum.
 template <typename T>
 CELLO_HD T limited_slope(T am, T a0, T ap) {
@@ -180,16 +244,18 @@ CELLO_HD T avg_left(T aL, T aR, T a6, T s) {
 // Characteristic tracing of one cell to its two edges at the half step.
 // W = cell-centre primitives, aL/aR = monotone edge values; outputs the state
 // at the left edge (Wm, right state of interface j-1/2) and at the right edge
-// (Wp, left state of interface j+1/2).
-template <typename T>
-CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
-                                      const Gas<T>& gs, T Wm[5], T Wp[5]) {
+// (Wp, left state of interface j+1/2).  NQ = 6: the specific internal energy
+// of the dual-energy formalism rides the entropy wave like the transverse
+// velocities.
+template <typename T, int NQ = 5>
+CELLO_HD void trace(const T W[NQ], const T aL[NQ], const T aR[NQ], T dtdx,
+                                      const Gas<T>& gs, T Wm[NQ], T Wp[NQ]) {
   const T rho = W[0], un = W[1], p = W[4];
   const T csq = vdiv(gs.gamma * p, rho);
   const T c = vsqrt(csq);
-  T a6[5];
+  T a6[NQ];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) a6[q] = T(6) * (W[q] - T(0.5) * (aL[q] + aR[q]));
+  for (int q = 0; q < NQ; ++q) a6[q] = T(6) * (W[q] - T(0.5) * (aL[q] + aR[q]));
   const T lm = un - c, l0 = un, lp = un + c;
   const T half_rho_c = vdiv(T(0.5) * rho, c);
   const T half_inv_csq = vdiv(T(0.5), csq);
@@ -197,9 +263,9 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
 
   {  // right edge: waves moving right
     const T sp = lp * dtdx, s0 = l0 * dtdx, sm = lm * dtdx;
-    T ref[5];
+    T ref[NQ];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) ref[q] = (lp > T(0)) ? avg_right(aL[q], aR[q], a6[q], sp) : aR[q];
+    for (int q = 0; q < NQ; ++q) ref[q] = (lp > T(0)) ? avg_right(aL[q], aR[q], a6[q], sp) : aR[q];
     T bm = T(0), b0 = T(0);
     if (lm > T(0))
       bm = (ref[4] - avg_right(aL[4], aR[4], a6[4], sm)) * half_inv_csq -
@@ -211,12 +277,14 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
     Wp[4] = vmax(ref[4] - csq * bm, T(kPFloor));
     Wp[2] = (l0 > T(0)) ? avg_right(aL[2], aR[2], a6[2], s0) : ref[2];
     Wp[3] = (l0 > T(0)) ? avg_right(aL[3], aR[3], a6[3], s0) : ref[3];
+#pragma unroll
+    for (int q = 5; q < NQ; ++q) Wp[q] = (l0 > T(0)) ? avg_right(aL[q], aR[q], a6[q], s0) : ref[q];
   }
   {  // left edge: waves moving left
     const T tm = -lm * dtdx, t0 = -l0 * dtdx, tp = -lp * dtdx;
-    T ref[5];
+    T ref[NQ];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) ref[q] = (lm < T(0)) ? avg_left(aL[q], aR[q], a6[q], tm) : aL[q];
+    for (int q = 0; q < NQ; ++q) ref[q] = (lm < T(0)) ? avg_left(aL[q], aR[q], a6[q], tm) : aL[q];
     T bp = T(0), b0 = T(0);
     if (lp < T(0))
       bp = (ref[4] - avg_left(aL[4], aR[4], a6[4], tp)) * half_inv_csq +
@@ -228,6 +296,8 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
     Wm[4] = vmax(ref[4] - csq * bp, T(kPFloor));
     Wm[2] = (l0 < T(0)) ? avg_left(aL[2], aR[2], a6[2], t0) : ref[2];
     Wm[3] = (l0 < T(0)) ? avg_left(aL[3], aR[3], a6[3], t0) : ref[3];
+#pragma unroll
+    for (int q = 5; q < NQ; ++q) Wm[q] = (l0 < T(0)) ? avg_left(aL[q], aR[q], a6[q], t0) : ref[q];
   }
 }
 
@@ -235,9 +305,11 @@ CELLO_HD void trace(const T W[5], const T aL[5], const T aR[5], T dtdx,
 // Newton steps on p* along shock curves on both sides (a lane whose p* stops
 // changing leaves the loop early, which gives bit-identical results), u* the Z-weighted
 // mean, sampled at x/t = 0 (u* >= 0 takes the left side), linear in a
-// rarefaction fan between head and tail.  Fluxes (rho, m_n, m_t1, m_t2, E).
-template <typename T>
-CELLO_HD void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+// rarefaction fan between head and tail.  Fluxes (rho, m_n, m_t1, m_t2, E);
+// NQ = 6 adds the flux of rho e (mass flux times the e of the sampled side)
+// and uf, the normal velocity of the sampled state.
+template <typename T, int NQ = 5>
+CELLO_HD void riemann_flux(const T L[NQ], const T R[NQ], const Gas<T>& gs, T F[NQ], T* uf = nullptr) {
   const T rL = L[0], uL = L[1], pL = L[4];
   const T rR = R[0], uR = R[1], pR = R[4];
   const T CL = vsqrt((gs.gamma * pL) * rL);
@@ -297,6 +369,10 @@ CELLO_HD void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5])
   F[3] = f0 * t2;
   const T E = p * gs.inv_gm1 + (T(0.5) * r) * (u * u + (t1 * t1 + t2 * t2));
   F[4] = u * (E + p);
+  if constexpr (NQ > 5) {
+    F[5] = f0 * (left ? L[5] : R[5]);
+    *uf = u;
+  }
 }
 
 // Float32 form of the same solver for the bulk path: the shock-curve
@@ -304,7 +380,9 @@ CELLO_HD void riemann_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5])
 // to riemann_flux (x = 1 + g1 (p*/p - 1) = (g1/p) p* + (1 - g1),
 // W = C sqrt(x), (p* - p)/W = (p* - p) rsqrt(x)/C, Z = 2W^3/(W^2 + C^2) =
 // 2 W x/(x + 1)); the float64 path keeps the literal formulas.
-CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<float>& gs, float F[5]) {
+template <int NQ = 5>
+CELLO_HD void riemann_flux_fast(const float L[NQ], const float R[NQ], const Gas<float>& gs, float F[NQ],
+                                float* uf = nullptr) {
   const float rL = L[0], uL = L[1], pL = L[4];
   const float rR = R[0], uR = R[1], pR = R[4];
   const float qL = (gs.gamma * pL) * rL, qR = (gs.gamma * pR) * rR;
@@ -376,6 +454,10 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
   F[3] = f0 * t2;
   const float E = p * gs.inv_gm1 + (0.5f * r) * (u * u + (t1 * t1 + t2 * t2));
   F[4] = u * (E + p);
+  if constexpr (NQ > 5) {
+    F[5] = f0 * (left ? L[5] : R[5]);
+    *uf = u;
+  }
 }
 
 // HLLC flux (Toro, Spruce & Speares 1994; Toro, Riemann Solvers and
@@ -385,9 +467,12 @@ CELLO_HD void riemann_flux_fast(const float L[5], const float R[5], const Gas<fl
 // U*_K = m_K / (S_K - S*) (1, S*, v_K, w_K, E_K / rho_K + (S* - u_K)(S* +
 // p_K / m_K)), m_K = rho_K (S_K - u_K).  Only the side that is sampled is
 // evaluated past the wave speeds; each quantity is the same expression in
-// the same order as a full evaluation of both sides.
-template <typename T>
-CELLO_HD void hllc_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
+// the same order as a full evaluation of both sides.  NQ = 6: rho e is
+// passive like the transverse momenta (flux rho u e, star value m_K / (S_K
+// - S*) e_K), and uf is the normal velocity of the sampled region's state
+// (u_K outside the fan, S* inside).
+template <typename T, int NQ = 5>
+CELLO_HD void hllc_flux(const T L[NQ], const T R[NQ], const Gas<T>& gs, T F[NQ], T* uf = nullptr) {
   const T rL = L[0], uL = L[1], pL = L[4];
   const T rR = R[0], uR = R[1], pR = R[4];
   const T cL = vsqrt(vdiv(gs.gamma * pL, rL));
@@ -408,12 +493,19 @@ CELLO_HD void hllc_flux(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
   F[3] = f0 * w;
   F[4] = u * (E + p);
   const bool outer = left ? (SL >= T(0)) : !(SR > T(0));
+  T e = T(0);
+  if constexpr (NQ > 5) {
+    e = left ? L[5] : R[5];
+    F[5] = f0 * e;
+    *uf = outer ? u : Ss;
+  }
   if (!outer) {
     const T fac = vdiv(m, S - Ss);
     const T Us[5] = {fac, fac * Ss, fac * v, fac * w, fac * (vdiv(E, r) + (Ss - u) * (Ss + vdiv(p, m)))};
     const T Uc[5] = {r, r * u, r * v, r * w, E};
 #pragma unroll
     for (int k = 0; k < 5; ++k) F[k] = F[k] + S * (Us[k] - Uc[k]);
+    if constexpr (NQ > 5) F[5] = F[5] + S * (fac * e - r * e);
   }
 }
 
@@ -424,6 +516,15 @@ CELLO_HD void riemann_flux_bulk(const T L[5], const T R[5], const Gas<T>& gs, T 
 template <>
 CELLO_HD void riemann_flux_bulk<float>(const float L[5], const float R[5], const Gas<float>& gs, float F[5]) {
   riemann_flux_fast(L, R, gs, F);
+}
+
+// Six-component (dual-energy) forms with the interface velocity.
+template <typename T>
+CELLO_HD void riemann_flux_bulk6(const T L[6], const T R[6], const Gas<T>& gs, T F[6], T* uf) {
+  riemann_flux<T, 6>(L, R, gs, F, uf);
+}
+CELLO_HD void riemann_flux_bulk6(const float L[6], const float R[6], const Gas<float>& gs, float F[6], float* uf) {
+  riemann_flux_fast<6>(L, R, gs, F, uf);
 }
 
 }  // namespace cello

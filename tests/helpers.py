@@ -33,7 +33,8 @@ RIEMANN_CODES = {"two-shock": 0, "hllc": 1}
 def gpu_desc(odesc, precision):
     from paper_1810_01319_gb300 import make_desc
     return make_desc(odesc.root, odesc.n, odesc.max_level, odesc.lo, odesc.hi, odesc.bc, precision, odesc.gamma,
-                     riemann=RIEMANN_CODES[odesc.riemann], steepening=int(odesc.steepen))
+                     riemann=RIEMANN_CODES[odesc.riemann], steepening=int(odesc.steepen),
+                     dual_energy=int(odesc.dual_energy))
 
 
 def gpu_mesh_from_flags(odesc, flags, precision):
