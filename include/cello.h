@@ -70,7 +70,7 @@ typedef struct {
                        * that exceeds 1e-3 E, else from rho*e; rho*e is advected with the mass flux,
                        * takes the compression term -(dt/dx) p (u+ - u-) with the interface-state
                        * velocities, and is reset to E - ke after each sweep where that exceeds 0.1 E.
-                       * Shared-memory sweep variants only; no adjoint or operation counts.  0: off */
+                       * No adjoint or operation counts.  0: off */
 } cello_mesh_desc;
 
 /* Riemann solvers of the sweep (Sec. II.C, PPM): the Colella-Woodward
@@ -203,9 +203,8 @@ cello_status cello_set_exec(cello_mesh* mesh, int mode);
  * pencils per CTA, register bound (minimum resident CTAs per SM) and
  * schedule (one CTA per work item, or one resident wave pulling items from
  * a device counter).  Float32 has 24 variants (12 shared-memory, 12
- * streaming, of which 4 read x pencils as 16-byte vectors), float64 2; a
- * dual-energy mesh refuses the streaming ones (CELLO_EINVAL) and the
- * autotuner skips them (their ms_out entries are -1).  The variants of one form compute the same values;
+ * streaming, of which 4 read x pencils as 16-byte vectors), float64 2, the
+ * same for dual-energy meshes.  The variants of one form compute the same values;
  * the two float32 forms agree to float32 rounding (a multiply and an add
  * may be fused across what is a register in one form and shared memory in
  * the other).  Cached graphs are dropped. */

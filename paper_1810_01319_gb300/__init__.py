@@ -249,8 +249,7 @@ class Mesh:
     def autotune(self, U, stream=None):
         """Pick the fastest sweep variant of each axis for this mesh (U is not
         changed).  Returns (chosen variants [x, y, z], best milliseconds of
-        each variant as [[x, y, z], ...]; -1 for a variant the mesh cannot
-        use)."""
+        each variant as [[x, y, z], ...])."""
         self._check_state(U)
         v = (ctypes.c_int * 3)()
         ms = (ctypes.c_float * 192)()

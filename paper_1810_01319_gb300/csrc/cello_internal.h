@@ -143,10 +143,12 @@ int ghost_run_count(int n);
 void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsigned char* out, cudaStream_t s);
 void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
-// Dual-energy sweeps (shared-memory form; k_de_f32.cu, k_de_f64.cu), launched
-// by the planners above with the grid they computed.
+// Dual-energy sweeps (both float32 forms, k_de_f32.cu; float64, k_de_f64.cu),
+// launched by the planners above with the grid they computed.
 template <int NB, int P, int MINB>
 void launch_sweep_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s);
+template <int NB, int CT, int MINB, int VEC>
+void launch_stream_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s);
 template <int NB>
 void launch_sweep_de_f64(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s);
 void prepare_kernels_de_f32();

@@ -1,6 +1,7 @@
-// Float32 dual-energy sweeps (the shared-memory form with a sixth field rho
-// e; method code RS | 4).  Compiled with the float32 sweep's flags; the
-// planner in k_f32.cu computes the grid and calls launch_sweep_de_f32.
+// Float32 dual-energy sweeps (both forms with a sixth field rho e; method
+// code RS | 4).  Compiled with the float32 sweep's flags; the planners in
+// k_f32.cu compute the grid and call launch_sweep_de_f32 (shared-memory
+// form) or launch_stream_de_f32 (register streaming).
 #include "kernels.cuh"
 
 namespace cello {
@@ -20,6 +21,30 @@ void launch_sweep_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaS
     case 3: sweep_kernel<float, NB, P, MINB, 7><<<grid, T, de_smem<NB, P, 7>(), s>>>(m, p); break;
   }
 }
+
+// Register-streaming form: VEC = 3 stages three groups of four cells of the
+// six fields per thread in shared memory.
+template <int NB, int CT, int MINB, int VEC>
+void launch_stream_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s) {
+  constexpr size_t sh = VEC == 3 ? sizeof(float4) * 3 * 6 * CT : 0;
+  switch (method_code(m.riemann, m.steepen)) {
+    case 0: sweep_stream_kernel<float, NB, CT, MINB, VEC, 4><<<grid, CT, sh, s>>>(m, p); break;
+    case 1: sweep_stream_kernel<float, NB, CT, MINB, VEC, 5><<<grid, CT, sh, s>>>(m, p); break;
+    case 2: sweep_stream_kernel<float, NB, CT, MINB, VEC, 6><<<grid, CT, sh, s>>>(m, p); break;
+    case 3: sweep_stream_kernel<float, NB, CT, MINB, VEC, 7><<<grid, CT, sh, s>>>(m, p); break;
+  }
+}
+
+// The streaming variants of the float32 table: {CTA size, min CTAs per SM, vector I/O}.
+#define CELLO_DE_STREAM(X, NB) X(NB, 64, 8, 0) X(NB, 128, 4, 0) X(NB, 64, 6, 0) X(NB, 32, 16, 0) X(NB, 64, 8, 3) \
+  X(NB, 64, 6, 1)
+#define CELLO_DE_SINST(NB, CT, MINB, VEC) \
+  template void launch_stream_de_f32<NB, CT, MINB, VEC>(const DevMesh&, const SweepParams&, int, cudaStream_t);
+CELLO_DE_STREAM(CELLO_DE_SINST, 8)
+CELLO_DE_STREAM(CELLO_DE_SINST, 16)
+CELLO_DE_STREAM(CELLO_DE_SINST, 32)
+#undef CELLO_DE_SINST
+#undef CELLO_DE_STREAM
 
 template <int NB, int P, int MINB>
 static void prepare_de() {

@@ -100,7 +100,10 @@ static void launch_stream_variant(const DevMesh& m, SweepParams p, int pencils, 
   int grid = 0;
   if (!plan_launch(p, pencils, CT, v, nb_index(NB), grid, s)) return;
   constexpr size_t sh = stream_smem<CT, VEC>();
-  if (m.nf != 5) return;   // the streaming form carries five fields; dual-energy meshes never select it
+  if (m.nf == 6) {   // dual energy (k_de_f32.cu)
+    launch_stream_de_f32<NB, CT, MINB, VEC>(m, p, grid, s);
+    return;
+  }
   switch (method_code(m.riemann, m.steepen)) {
     case 0: sweep_stream_kernel<float, NB, CT, MINB, VEC, 0><<<grid, CT, sh, s>>>(m, p); break;
     case 1: sweep_stream_kernel<float, NB, CT, MINB, VEC, 1><<<grid, CT, sh, s>>>(m, p); break;

@@ -20,7 +20,7 @@ __device__ __forceinline__ T minmod(T a, T b) {
 // =====================================================================
 // Directional PPM sweep.  One CTA item = P pencils of one leaf; a thread
 // owns one cell of one pencil (pencil index fastest across the threads of a
-// warp).  Shared arrays are [5][N][P], pencil fastest, so that a warp's
+// warp).  Shared arrays are [NQ][N][P], pencil fastest, so that a warp's
 // accesses at one stencil offset fall in consecutive banks.  Phases:
 //   1 load + primitives  2 limited slopes, shock detector  3 interface
 //   values  4 flatten + monotone + trace  5 Riemann flux (+ face registers)
@@ -252,7 +252,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
 // Register-streaming form of the same sweep: one thread per pencil walks
 // its cells once, keeping a sliding window of the pencil in registers
 // (primitives of 5 cells, 2 slopes, 3 shock detectors, 3 interface values,
-// the last right-edge state and the last flux), so that no value passes
+// the last right-edge state and the last flux, each of 5 fields or 6 with
+// dual energy), so that no value passes
 // through shared memory and no phase waits at a barrier.  At step k the
 // thread reads cell k and produces: the slope of cell k-1, the shock
 // detector of cell k-2, the interface value k-2+1/2, the traced edge states
@@ -261,34 +262,39 @@ sweep_kernel(DevMesh m, SweepParams prm) {
 // forms evaluate the same expressions on the same values.
 // =====================================================================
 // The sliding window of one pencil.
-template <typename T>
+// NQ = 6 with the dual-energy formalism (e as a sixth primitive).
+template <typename T, int NQ = 5>
 struct PencilWindow {
-  T w[5][5];    // primitives of cells k-4 .. k (sweep-local components)
-  T dm[2][5];   // slopes of cells k-2, k-1
+  T w[5][NQ];   // primitives of cells k-4 .. k (sweep-local components)
+  T dm[2][NQ];  // slopes of cells k-2, k-1
   T ft[3];      // shock detectors of cells k-4 .. k-2
-  T ai[3][5];   // interface values k-4+1/2 .. k-2+1/2
-  T wp[5];      // right-edge state of cell k-4 (left state of interface k-4+1/2)
-  T fl[5];      // flux at interface k-5+1/2
+  T ai[3][NQ];  // interface values k-4+1/2 .. k-2+1/2
+  T wp[NQ];     // right-edge state of cell k-4 (left state of interface k-4+1/2)
+  T fl[NQ];     // flux at interface k-5+1/2
   T eta[3];     // contact-steepening weights of cells k-4 .. k-2 (RS & 2)
   T dr[2];      // density slopes of cells k-4, k-3 (RS & 2)
+  T ufl;        // interface-state velocity at k-5+1/2 (dual energy)
 };
 
 // One step of the walk: cell k enters as conserved values Us (sweep-local
 // components); old holds cell k-4 as stored (component order), read
 // before it is overwritten here.
-// DEFER: the updated cell is returned in upd[5] (component order) instead
-// of being stored.
+// DEFER: the updated cell is returned in upd[NQ] (component order) instead
+// of being stored.  RS & 4 (dual energy): six fields, rho e taking the
+// compression term with the pressure of its cell and the synchronisation.
 template <typename T, int NB, int RS, bool DEFER = false>
-__device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T Us[5], const T old[5], T* base,
-                                            long sAx, const int comp[5], T dtdx, const Gas<T>& gs,
+__device__ __forceinline__ void stream_step(PencilWindow<T, (RS & 4) ? 6 : 5>& S, int k, const T* Us, const T* old,
+                                            T* base, long sAx, const int* comp, T dtdx, const Gas<T>& gs,
                                             const DevMesh& m, const SweepParams& prm, int leaf, int axis,
                                             bool face_row, int pa, int pb, T* upd = nullptr) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
-  to_primitive(Us, gs, S.w[4]);
+  constexpr int NQ = (RS & 4) ? 6 : 5;
+  if constexpr (NQ == 6) to_primitive_de(Us, gs, S.w[4]);
+  else to_primitive(Us, gs, S.w[4]);
   if (k >= 3 && k <= N - 2) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) S.dm[1][c] = limited_slope(S.w[2][c], S.w[3][c], S.w[4][c]);
+    for (int c = 0; c < NQ; ++c) S.dm[1][c] = limited_slope(S.w[2][c], S.w[3][c], S.w[4][c]);
   }
   if (k >= 4) {
     S.ft[2] = flatten_tilde(S.w[0][4], S.w[1][4], S.w[3][4], S.w[4][4], S.w[1][1], S.w[3][1]);
@@ -296,7 +302,7 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
       S.eta[2] = steepening_eta(S.w[0][0], S.w[1][0], S.w[2][0], S.w[3][0], S.w[4][0], S.w[1][4], S.w[3][4], gs.gamma);
     if (k <= N - 2) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
+      for (int c = 0; c < NQ; ++c)
         S.ai[2][c] = interface_value(S.w[2][c], S.w[3][c], S.dm[0][c], S.dm[1][c]);
     }
   }
@@ -304,9 +310,9 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
     // cell j = k-3: W = w[1], aL = ai[0], aR = ai[1], shock detectors ft[0..2]
     const T s = S.w[2][4] - S.w[0][4];
     const T f = (s > T(0)) ? vmax(S.ft[1], S.ft[0]) : ((s < T(0)) ? vmax(S.ft[1], S.ft[2]) : S.ft[1]);
-    T aL[5], aR[5], Wm[5], Wp[5];
+    T aL[NQ], aR[NQ], Wm[NQ], Wp[NQ];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < NQ; ++c) {
       aL[c] = S.ai[0][c];
       aR[c] = S.ai[1][c];
       if ((RS & 2) && c == 0) {   // density of cell k-3: neighbours k-4 (slope dr[0]) and k-2 (slope dm[0])
@@ -316,35 +322,44 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
       }
       flatten_monotone(S.w[1][c], f, aL[c], aR[c]);
     }
-    trace(S.w[1], aL, aR, dtdx, gs, Wm, Wp);
+    trace<T, NQ>(S.w[1], aL, aR, dtdx, gs, Wm, Wp);
     if (k >= 7) {
       // interface j = k-4 (+1/2): left state wp (cell k-4), right state Wm (cell k-3)
-      T F[5];
-      interface_flux<RS>(S.wp, Wm, gs, F);
+      T F[NQ];
+      T uf = T(0);
+      if constexpr (NQ == 6) interface_flux6<RS>(S.wp, Wm, gs, F, &uf);
+      else interface_flux<RS>(S.wp, Wm, gs, F);
       const int j = k - 4;
       if (face_row && (j == G - 1 || j == G + NB - 1)) {
         const int face = 2 * axis + (j == G - 1 ? 0 : 1);
         const int slot = m.face_slot[leaf * 6 + face];
         if (slot >= 0) {
-          double* r = prm.reg + (long)slot * 5 * NB * NB + (pa - G) * NB + (pb - G);
+          double* r = prm.reg + (long)slot * NQ * NB * NB + (pa - G) * NB + (pb - G);
 #pragma unroll
-          for (int c = 0; c < 5; ++c) r[(long)comp[c] * NB * NB] = double(F[c]);
+          for (int c = 0; c < NQ; ++c) r[(long)comp[c] * NB * NB] = double(F[c]);
         }
       }
       if (k >= 8) {
-        // cell j = k-4 between interfaces j-1/2 (fl) and j+1/2 (F)
+        // cell j = k-4 (window slot w[0]) between interfaces j-1/2 (fl) and j+1/2 (F)
+        T v[NQ];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          const T v = old[c] - dtdx * sub_rn(F[c], S.fl[c]);
-          if (DEFER) upd[c] = v;
-          else base[comp[c] * SLAB + (long)j * sAx] = v;
+        for (int c = 0; c < NQ; ++c) v[c] = old[c] - dtdx * sub_rn(F[c], S.fl[c]);
+        if constexpr (NQ == 6) {
+          v[5] = v[5] - (dtdx * S.w[0][4]) * sub_rn(uf, S.ufl);
+          v[5] = dual_sync(v);
+        }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+          if (DEFER) upd[c] = v[c];
+          else base[comp[c] * SLAB + (long)j * sAx] = v[c];
         }
       }
 #pragma unroll
-      for (int c = 0; c < 5; ++c) S.fl[c] = F[c];
+      for (int c = 0; c < NQ; ++c) S.fl[c] = F[c];
+      if constexpr (NQ == 6) S.ufl = uf;
     }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) S.wp[c] = Wp[c];
+    for (int c = 0; c < NQ; ++c) S.wp[c] = Wp[c];
   }
   // slide the windows
   if (RS & 2) {
@@ -352,7 +367,7 @@ __device__ __forceinline__ void stream_step(PencilWindow<T>& S, int k, const T U
     S.dr[0] = S.dr[1]; S.dr[1] = S.dm[0][0];
   }
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < NQ; ++c) {
     S.w[0][c] = S.w[1][c]; S.w[1][c] = S.w[2][c]; S.w[2][c] = S.w[3][c]; S.w[3][c] = S.w[4][c];
     S.dm[0][c] = S.dm[1][c];
     S.ai[0][c] = S.ai[1][c]; S.ai[1][c] = S.ai[2][c];
@@ -380,6 +395,7 @@ __global__ void __launch_bounds__(CT, MINB)
 sweep_stream_kernel(DevMesh m, SweepParams prm) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
+  constexpr int NQ = (RS & 4) ? 6 : 5;   // dual energy: a sixth field rho e
   const Gas<T> gs = Gas<T>::make(m.gamma);
   T* U = static_cast<T*>(prm.U);
   const int axis = prm.axis;
@@ -387,8 +403,8 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
   const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
   const long sTA = axis == 2 ? N : (long)N * N;
   const long sTB = axis == 0 ? N : 1;
-  int comp[5];
-  comp[0] = 0; comp[1] = 1 + axis; comp[4] = 4;
+  int comp[6];
+  comp[0] = 0; comp[1] = 1 + axis; comp[4] = 4; comp[5] = 5;
   comp[2] = axis == 0 ? 2 : 1;
   comp[3] = axis == 2 ? 2 : 3;
 
@@ -414,22 +430,22 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
     if (q < cA * cB) {
       const int qa = (int)prm.div_cb.div((unsigned)q);
       const int pa = prm.a0 + qa, pb = prm.b0 + q - qa * cB;
-      T* base = U + (long)leaf * 5 * SLAB + pa * sTA + pb * sTB;
+      T* base = U + (long)leaf * NQ * SLAB + pa * sTA + pb * sTB;
       const bool face_row = prm.reg && pa >= G && pa < G + NB && pb >= G && pb < G + NB;
-      PencilWindow<T> S;
-      T old[5];
+      PencilWindow<T, NQ> S;
+      T old[NQ];
       if (VEC == 3 && axis == 0) {
         // the groups of four cells are copied HBM -> shared memory by cp.async, one group
         // ahead, into three per-thread slots (current group, the group being updated, the
         // group in flight); nothing of the pencil is held in registers but the output group
         extern __shared__ __align__(16) unsigned char stream_raw[];
-        float4* my = reinterpret_cast<float4*>(stream_raw) + t;   // slot s, field c at my[(s * 5 + c) * CT]
+        float4* my = reinterpret_cast<float4*>(stream_raw) + t;   // slot s, field c at my[(s * NQ + c) * CT]
         const float4* b4 = reinterpret_cast<const float4*>(base);
         constexpr int NG = N / 4;
         auto issue = [&](int grp, int slot) {
 #pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(&my[(slot * 5 + c) * CT]);
+          for (int c = 0; c < NQ; ++c) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&my[(slot * NQ + c) * CT]);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(b4 + comp[c] * (SLAB / 4) + grp)
                          : "memory");
           }
@@ -441,75 +457,75 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           if (g + 1 < NG) issue(g + 1, (g + 1) % 3);
           asm volatile("cp.async.commit_group;\n" ::: "memory");
           asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // group g has landed
-          const float* cur = reinterpret_cast<const float*>(my + (g % 3) * 5 * CT);
-          const float* prv = reinterpret_cast<const float*>(my + ((g + 2) % 3) * 5 * CT);
-          float4 out4[5];
+          const float* cur = reinterpret_cast<const float*>(my + (g % 3) * NQ * CT);
+          const float* prv = reinterpret_cast<const float*>(my + ((g + 2) % 3) * NQ * CT);
+          float4 out4[NQ];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            T Us[5], up[5];
+            T Us[NQ], up[NQ];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
+            for (int c = 0; c < NQ; ++c) {
               Us[c] = cur[c * CT * 4 + i];
               old[c] = prv[c * CT * 4 + i];
             }
             stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
                                          face_row, pa, pb, up);
 #pragma unroll
-            for (int c = 0; c < 5; ++c) set_lane4(out4[c], i, up[c]);
+            for (int c = 0; c < NQ; ++c) set_lane4(out4[c], i, up[c]);
           }
           if (g >= 2 && g - 1 <= NG - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
             float4* w4 = reinterpret_cast<float4*>(base);
 #pragma unroll
-            for (int c = 0; c < 5; ++c) w4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
+            for (int c = 0; c < NQ; ++c) w4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
           }
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       } else if (VEC > 0 && axis == 0) {
         // rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
         float4* b4 = reinterpret_cast<float4*>(base);
-        float4 nx4[5];   // the next group of four cells
+        float4 nx4[NQ];   // the next group of four cells
 #pragma unroll
-        for (int c = 0; c < 5; ++c) nx4[c] = b4[comp[c] * (SLAB / 4)];
+        for (int c = 0; c < NQ; ++c) nx4[c] = b4[comp[c] * (SLAB / 4)];
 #pragma unroll 1
         for (int g = 0; g < N / 4; ++g) {
-          float4 cur4[5], old4[5], out4[5];
+          float4 cur4[NQ], old4[NQ], out4[NQ];
 #pragma unroll
-          for (int c = 0; c < 5; ++c) cur4[c] = nx4[c];
+          for (int c = 0; c < NQ; ++c) cur4[c] = nx4[c];
           if (g + 1 < N / 4) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) nx4[c] = b4[comp[c] * (SLAB / 4) + g + 1];
+            for (int c = 0; c < NQ; ++c) nx4[c] = b4[comp[c] * (SLAB / 4) + g + 1];
           }
           if (g >= 2) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) old4[c] = b4[comp[c] * (SLAB / 4) + g - 1];
+            for (int c = 0; c < NQ; ++c) old4[c] = b4[comp[c] * (SLAB / 4) + g - 1];
           }
           if (VEC == 1) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              T Us[5], up[5];
+              T Us[NQ], up[NQ];
 #pragma unroll
-              for (int c = 0; c < 5; ++c) {
+              for (int c = 0; c < NQ; ++c) {
                 Us[c] = lane4(cur4[c], i);
                 old[c] = lane4(old4[c], i);
               }
               stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
                                            face_row, pa, pb, up);
 #pragma unroll
-              for (int c = 0; c < 5; ++c) set_lane4(out4[c], i, up[c]);
+              for (int c = 0; c < NQ; ++c) set_lane4(out4[c], i, up[c]);
             }
           } else {   // one copy of the step body: the groups' lanes shift by one each cell
 #pragma unroll 1
             for (int i = 0; i < 4; ++i) {
-              T Us[5], up[5];
+              T Us[NQ], up[NQ];
 #pragma unroll
-              for (int c = 0; c < 5; ++c) {
+              for (int c = 0; c < NQ; ++c) {
                 Us[c] = cur4[c].x;
                 old[c] = old4[c].x;
               }
               stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
                                            face_row, pa, pb, up);
 #pragma unroll
-              for (int c = 0; c < 5; ++c) {
+              for (int c = 0; c < NQ; ++c) {
                 cur4[c].x = cur4[c].y; cur4[c].y = cur4[c].z; cur4[c].z = cur4[c].w;
                 old4[c].x = old4[c].y; old4[c].y = old4[c].z; old4[c].z = old4[c].w;
                 out4[c].x = out4[c].y; out4[c].y = out4[c].z; out4[c].z = out4[c].w; out4[c].w = up[c];
@@ -518,25 +534,25 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           }
           if (g >= 2 && g - 1 <= N / 4 - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
 #pragma unroll
-            for (int c = 0; c < 5; ++c) b4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
+            for (int c = 0; c < NQ; ++c) b4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
           }
         }
       } else {
-        T nx[5];   // cell k+1, loaded one step ahead
+        T nx[NQ];   // cell k+1, loaded one step ahead
 #pragma unroll
-        for (int c = 0; c < 5; ++c) nx[c] = base[comp[c] * SLAB];
+        for (int c = 0; c < NQ; ++c) nx[c] = base[comp[c] * SLAB];
 #pragma unroll 1
         for (int k = 0; k < N; ++k) {
-          T Us[5];
+          T Us[NQ];
 #pragma unroll
-          for (int c = 0; c < 5; ++c) Us[c] = nx[c];
+          for (int c = 0; c < NQ; ++c) Us[c] = nx[c];
           if (k + 1 < N) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) nx[c] = base[comp[c] * SLAB + (k + 1) * sAx];
+            for (int c = 0; c < NQ; ++c) nx[c] = base[comp[c] * SLAB + (k + 1) * sAx];
           }
           if (k >= 8) {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) old[c] = base[comp[c] * SLAB + (k - 4) * sAx];
+            for (int c = 0; c < NQ; ++c) old[c] = base[comp[c] * SLAB + (k - 4) * sAx];
           }
           stream_step<T, NB, RS>(S, k, Us, old, base, sAx, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb);
         }

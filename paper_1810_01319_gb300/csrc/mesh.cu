@@ -874,10 +874,6 @@ cello_status cello_set_sweep_variants(cello_mesh* M, const int* variants) {
   const int nv = M->desc.precision == 4 ? sweep_variant_count_f32() : sweep_variant_count_f64();
   for (int a = 0; a < 3; ++a)
     if (variants[a] < 0 || variants[a] >= nv) return fail(CELLO_EINVAL, "sweep variant out of range");
-  if (M->desc.dual_energy && M->desc.precision == 4)
-    for (int a = 0; a < 3; ++a)
-      if (sweep_variant_f32(variants[a]).stream)
-        return fail(CELLO_EINVAL, "the streaming sweep carries five fields: dual-energy meshes take shared-memory variants");
   for (int a = 0; a < 3; ++a) M->sweep_variant[a] = variants[a];
   for (auto& g : M->graphs) cudaGraphExecDestroy(g.exec);
   M->graphs.clear();
@@ -902,11 +898,6 @@ cello_status cello_autotune(cello_mesh* M, void* U, int* variants_out, float* ms
   float best_ms[3] = {1e30f, 1e30f, 1e30f};
   cudaError_t err = cudaSuccess;
   for (int v = 0; v < nv && err == cudaSuccess; ++v) {
-    if (d.dual_energy && d.precision == 4 && sweep_variant_f32(v).stream) {
-      for (int a = 0; a < 3; ++a)
-        if (ms_out && 3 * v + a < ms_len) ms_out[3 * v + a] = -1.0f;
-      continue;
-    }
     float vbest[3] = {1e30f, 1e30f, 1e30f};
     for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
       float axis_ms[3] = {0, 0, 0};

@@ -23,7 +23,11 @@ constexpr int kNu = 2;
 constexpr int kCoarseSweeps = 50;
 constexpr int kRedThreads = 256;
 
-__device__ __forceinline__ long gidx(int x, int y, int z, int M) { return ((long)z * M + y) * M + x; }
+// M <= 1024 (checked by cello_poisson_solve): M^3 <= 2^30 and every grid
+// offset fits 32-bit unsigned arithmetic.
+__device__ __forceinline__ unsigned gidx(int x, int y, int z, int M) {
+  return ((unsigned)z * (unsigned)M + (unsigned)y) * (unsigned)M + (unsigned)x;
+}
 __device__ __forceinline__ int wrapm(int v, int M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
 
 template <typename T>
@@ -37,8 +41,13 @@ __device__ __forceinline__ T nbsum(const T* p, int x, int y, int z, int M) {
 // The grid kernels run one thread per cell of an M^3 (or, for the
 // restriction, (M/2)^3) grid on a 3-D launch: 32 x 8 threads per CTA in
 // (x, y), one CTA row per z plane, so no division recovers the coordinates.
-constexpr int kBX = 32, kBY = 8;
+// The Jacobi sweep instead walks kZC planes per thread along z, keeping the
+// z-1, z and z+1 values of its column in registers.
+constexpr int kBX = 32, kBY = 8, kZC = 8;
 dim3 grid3(int M) { return dim3((unsigned)((M + kBX - 1) / kBX), (unsigned)((M + kBY - 1) / kBY), (unsigned)M); }
+dim3 grid_zc(int M) {
+  return dim3((unsigned)((M + kBX - 1) / kBX), (unsigned)((M + kBY - 1) / kBY), (unsigned)((M + kZC - 1) / kZC));
+}
 const dim3 kBlock3(kBX, kBY, 1);
 
 __device__ __forceinline__ bool cell3(int M, int& x, int& y, int& z) {
@@ -50,10 +59,27 @@ __device__ __forceinline__ bool cell3(int M, int& x, int& y, int& z) {
 
 template <typename T>
 __global__ void jacobi_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ f, int M, T h2) {
-  int x, y, z;
-  if (!cell3(M, x, y, z)) return;
-  const long i = gidx(x, y, z, M);
-  out[i] = T(1.0 - kOmega) * in[i] + T(kOmega) * ((nbsum(in, x, y, z, M) - h2 * f[i]) * T(1.0 / 6.0));
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= M || y >= M) return;
+  const int z0 = blockIdx.z * kZC;
+  const int z1 = z0 + kZC < M ? z0 + kZC : M;
+  const unsigned uM = (unsigned)M, P = uM * uM;
+  const unsigned xm = (unsigned)wrapm(x - 1, M), xp = (unsigned)wrapm(x + 1, M);
+  const unsigned row = (unsigned)y * uM, rym = (unsigned)wrapm(y - 1, M) * uM, ryp = (unsigned)wrapm(y + 1, M) * uM;
+  unsigned zb = (unsigned)z0 * P;
+  T cm = in[(unsigned)wrapm(z0 - 1, M) * P + row + x];   // column values at z-1 and z
+  T cc = in[zb + row + x];
+  for (int z = z0; z < z1; ++z) {
+    const T cp = in[(unsigned)wrapm(z + 1, M) * P + row + x];
+    // the neighbour sum in the order of nbsum: x-1, x+1, y-1, y+1, z-1, z+1
+    const T s = ((((in[zb + row + xm] + in[zb + row + xp]) + in[zb + rym + x]) + in[zb + ryp + x]) + cm) + cp;
+    const unsigned i = zb + row + x;
+    out[i] = T(1.0 - kOmega) * cc + T(kOmega) * ((s - h2 * f[i]) * T(1.0 / 6.0));
+    cm = cc;
+    cc = cp;
+    zb += P;
+  }
 }
 
 // Coarse right-hand side: mean of the residuals f - lap(phi) of the 8
@@ -64,14 +90,14 @@ __global__ void residual_restrict_kernel(const T* __restrict__ phi, const T* __r
   const int Mc = M / 2;
   int X, Y, Z;
   if (!cell3(Mc, X, Y, Z)) return;
-  const long i = gidx(X, Y, Z, Mc);
+  const unsigned i = gidx(X, Y, Z, Mc);
   T s = T(0);
   bool first = true;
   for (int dz = 0; dz < 2; ++dz)
     for (int dy = 0; dy < 2; ++dy)
       for (int dx = 0; dx < 2; ++dx) {
         const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
-        const long o = gidx(x, y, z, M);
+        const unsigned o = gidx(x, y, z, M);
         const T r = f[o] - (nbsum(phi, x, y, z, M) - T(6) * phi[o]) * ih2;
         s = first ? r : s + r;
         first = false;
@@ -85,7 +111,7 @@ __global__ void prolong_add_kernel(const T* __restrict__ ec, T* __restrict__ phi
   const int Mc = M / 2;
   int x, y, z;
   if (!cell3(M, x, y, z)) return;
-  const long i = gidx(x, y, z, M);
+  const unsigned i = gidx(x, y, z, M);
   const int X = x >> 1, Y = y >> 1, Z = z >> 1;
   const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
   const int X1 = wrapm(X + sx, Mc), Y1 = wrapm(Y + sy, Mc), Z1 = wrapm(Z + sz, Mc);
@@ -105,7 +131,7 @@ __global__ void residual_f32_kernel(const double* __restrict__ phi, const double
                                     float* __restrict__ r, int M, double ih2) {
   int x, y, z;
   if (!cell3(M, x, y, z)) return;
-  const long i = gidx(x, y, z, M);
+  const unsigned i = gidx(x, y, z, M);
   r[i] = (float)(f[i] - (nbsum(phi, x, y, z, M) - 6.0 * phi[i]) * ih2);
 }
 
@@ -196,7 +222,7 @@ struct Cycle {
 
   void sweeps(Level<T>& L, int count) {
     for (int k = 0; k < count; ++k) {
-      jacobi_kernel<T><<<grid3(L.M), kBlock3, 0, s>>>(L.phi, L.tmp, L.f, L.M, T(L.h * L.h));
+      jacobi_kernel<T><<<grid_zc(L.M), kBlock3, 0, s>>>(L.phi, L.tmp, L.f, L.M, T(L.h * L.h));
       std::swap(L.phi, L.tmp);
     }
   }
