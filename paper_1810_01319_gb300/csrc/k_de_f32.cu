@@ -23,10 +23,10 @@ void launch_sweep_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaS
 }
 
 // Register-streaming form: VEC = 3 stages three groups of four cells of the
-// six fields per thread in shared memory.
+// six fields per thread in shared memory, and the updated group.
 template <int NB, int CT, int MINB, int VEC>
 void launch_stream_de_f32(const DevMesh& m, const SweepParams& p, int grid, cudaStream_t s) {
-  constexpr size_t sh = VEC == 3 ? sizeof(float4) * 3 * 6 * CT : 0;
+  constexpr size_t sh = VEC == 3 ? sizeof(float4) * 4 * 6 * CT : 0;
   switch (method_code(m.riemann, m.steepen)) {
     case 0: sweep_stream_kernel<float, NB, CT, MINB, VEC, 4><<<grid, CT, sh, s>>>(m, p); break;
     case 1: sweep_stream_kernel<float, NB, CT, MINB, VEC, 5><<<grid, CT, sh, s>>>(m, p); break;

@@ -50,10 +50,10 @@ static void prepare_variant(int v, int sms) {
 }
 
 // Dynamic shared memory of the streaming form: the staged form keeps three
-// groups of four cells of five fields per thread.
+// groups of four cells of five fields per thread, and the updated group.
 template <int CT, int VEC>
 static constexpr size_t stream_smem() {
-  return VEC == 3 ? sizeof(float4) * 3 * 5 * CT : 0;
+  return VEC == 3 ? sizeof(float4) * 4 * 5 * CT : 0;
 }
 
 template <int NB, int CT, int MINB, int VEC>

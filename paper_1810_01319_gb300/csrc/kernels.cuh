@@ -437,7 +437,10 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
       if (VEC == 3 && axis == 0) {
         // the groups of four cells are copied HBM -> shared memory by cp.async, one group
         // ahead, into three per-thread slots (current group, the group being updated, the
-        // group in flight); nothing of the pencil is held in registers but the output group
+        // group in flight); the four cells of a group run through one copy of the step,
+        // each updated cell written to a fourth slot that cp.async never targets and
+        // stored from there as one vector per field, so the x sweep's code is no larger
+        // than the one-cell walk
         extern __shared__ __align__(16) unsigned char stream_raw[];
         float4* my = reinterpret_cast<float4*>(stream_raw) + t;   // slot s, field c at my[(s * NQ + c) * CT]
         const float4* b4 = reinterpret_cast<const float4*>(base);
@@ -459,8 +462,8 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // group g has landed
           const float* cur = reinterpret_cast<const float*>(my + (g % 3) * NQ * CT);
           const float* prv = reinterpret_cast<const float*>(my + ((g + 2) % 3) * NQ * CT);
-          float4 out4[NQ];
-#pragma unroll
+          float* out = reinterpret_cast<float*>(my + 3 * NQ * CT);
+#pragma unroll 1
           for (int i = 0; i < 4; ++i) {
             T Us[NQ], up[NQ];
 #pragma unroll
@@ -470,13 +473,16 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
             }
             stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
                                          face_row, pa, pb, up);
+            if (g >= 2) {   // cells k >= 8: up holds cell 4(g-1)+i
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) set_lane4(out4[c], i, up[c]);
+              for (int c = 0; c < NQ; ++c) out[c * CT * 4 + i] = up[c];
+            }
           }
           if (g >= 2 && g - 1 <= NG - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
             float4* w4 = reinterpret_cast<float4*>(base);
+            const float4* done = my + 3 * NQ * CT;
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) w4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
+            for (int c = 0; c < NQ; ++c) w4[comp[c] * (SLAB / 4) + g - 1] = done[c * CT];
           }
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
