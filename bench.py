@@ -38,8 +38,8 @@ WORKLOAD = dict(workload="blob-amr-large", root=[16, 16, 16], n=32, max_level=2,
 # ncu on the 4^3-root blob box (3,970 leaves) for the same kernel form and
 # position in the sweep order, keyed "axis-form-position"; the roofline's
 # traffic is this times the leaves of the launch.
-SWEEP_DRAM_BYTES_PER_LEAF = {"x-streaming-vec4-sweep_1": 2.548e6, "y-streaming-sweep_2": 2.291e6,
-                             "z-streaming-sweep_3": 1.831e6}
+SWEEP_DRAM_BYTES_PER_LEAF = {"x-streaming-staged-sweep_1": 2.578e6, "y-streaming-staged-sweep_2": 2.291e6,
+                             "z-streaming-staged-sweep_3": 1.831e6}
 
 # FP32 lane operations per second of the whole GPU at the maximum SM clock:
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (one operation per lane per clock)
@@ -530,7 +530,8 @@ def main():
         v = variant[order[k]]
         sweeps[f"sweep_{k + 1}"] = {
             "axis": "xyz"[order[k]], "variant": v,
-            "form": ("streaming-vec4" if v % 12 >= 10 else "streaming") if v % 12 >= 6 else "shared-memory",
+            "form": {10: "streaming-staged", 11: "streaming-vec4"}.get(v % 12, "streaming") if v % 12 >= 6
+            else "shared-memory",
             "ms": prof[1 + k], "hbm_gbs_algorithmic": alg_bytes[f"sweep_{k + 1}"] / t / 1e9}
         if ops is not None:
             ops_launch = float(ops[k].sum()) * scale
