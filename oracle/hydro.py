@@ -9,8 +9,8 @@ Blocks before a Method runs (Sec. II.B, Fig. 4); Refine / Restrict / Prolong
 plug-ins move data between levels (Sec. II.B); the hydro Method is a modified
 piecewise parabolic method (PPM, Colella & Woodward 1984; Bryan et al. 1995)
 (Sec. II.C).  The paper prints none of the formulas, so every formula below is
-a reading of the named published method, stated in the docstrings and listed
-in the design doc.  The code is vectorised torch float64 on the CPU: every
+a reading of the named published method, stated in the docstrings.  The
+code is vectorised torch float64 on the CPU: every
 elementwise operation is written out in the stated order (no fused
 multiply-add, no reassociation), so a reader can check it term by term.
 
