@@ -36,3 +36,27 @@ def test_product_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(_lib.CelloError):
         _lib.lib()
+
+
+def test_mesh_desc_layout_matches_the_header(tmp_path):
+    """The binding's ctypes view of cello_mesh_desc has the size and field
+    offsets the C compiler gives the header's struct."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1810_01319_gb300 import _lib
+    fields = [f for f, _ in _lib.MeshDesc._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("{f} %zu\\n", offsetof(cello_mesh_desc, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "cello.h"\nint main(void) {\n'
+                   '  printf("sizeof %zu\\n", sizeof(cello_mesh_desc));\n' + body + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert int(out["sizeof"]) == ctypes.sizeof(_lib.MeshDesc)
+    for f in fields:
+        assert int(out[f]) == getattr(_lib.MeshDesc, f).offset, f
