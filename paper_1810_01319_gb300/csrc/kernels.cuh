@@ -387,9 +387,10 @@ __device__ __forceinline__ void set_lane4(float4& v, int i, float x) {
 // contiguous axis): cells are read and written four at a time as 16-byte
 // vectors (a group is read one group ahead; the group updated during group
 // g is g-1, written back at its end) instead of 4-byte accesses 160 bytes
-// apart across the warp; VEC = 1 unrolls the four cells of a group, VEC = 2
-// keeps one copy of the step, VEC = 3 stages the groups in shared memory by
-// asynchronous copies; other axes take the one-cell path.
+// apart across the warp; VEC = 1 unrolls the four cells of a group in
+// registers, VEC = 3 stages the groups in shared memory by asynchronous
+// copies and runs them through one copy of the step; other axes take the
+// one-cell path.
 template <typename T, int NB, int CT, int MINB, int VEC, int RS>
 __global__ void __launch_bounds__(CT, MINB)
 sweep_stream_kernel(DevMesh m, SweepParams prm) {
@@ -487,7 +488,7 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       } else if (VEC > 0 && axis == 0) {
-        // rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
+        // VEC == 1; rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
         float4* b4 = reinterpret_cast<float4*>(base);
         float4 nx4[NQ];   // the next group of four cells
 #pragma unroll
@@ -505,38 +506,18 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
 #pragma unroll
             for (int c = 0; c < NQ; ++c) old4[c] = b4[comp[c] * (SLAB / 4) + g - 1];
           }
-          if (VEC == 1) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              T Us[NQ], up[NQ];
+          for (int i = 0; i < 4; ++i) {
+            T Us[NQ], up[NQ];
 #pragma unroll
-              for (int c = 0; c < NQ; ++c) {
-                Us[c] = lane4(cur4[c], i);
-                old[c] = lane4(old4[c], i);
-              }
-              stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
-                                           face_row, pa, pb, up);
-#pragma unroll
-              for (int c = 0; c < NQ; ++c) set_lane4(out4[c], i, up[c]);
+            for (int c = 0; c < NQ; ++c) {
+              Us[c] = lane4(cur4[c], i);
+              old[c] = lane4(old4[c], i);
             }
-          } else {   // one copy of the step body: the groups' lanes shift by one each cell
-#pragma unroll 1
-            for (int i = 0; i < 4; ++i) {
-              T Us[NQ], up[NQ];
+            stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
+                                         face_row, pa, pb, up);
 #pragma unroll
-              for (int c = 0; c < NQ; ++c) {
-                Us[c] = cur4[c].x;
-                old[c] = old4[c].x;
-              }
-              stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
-                                           face_row, pa, pb, up);
-#pragma unroll
-              for (int c = 0; c < NQ; ++c) {
-                cur4[c].x = cur4[c].y; cur4[c].y = cur4[c].z; cur4[c].z = cur4[c].w;
-                old4[c].x = old4[c].y; old4[c].y = old4[c].z; old4[c].z = old4[c].w;
-                out4[c].x = out4[c].y; out4[c].y = out4[c].z; out4[c].z = out4[c].w; out4[c].w = up[c];
-              }
-            }
+            for (int c = 0; c < NQ; ++c) set_lane4(out4[c], i, up[c]);
           }
           if (g >= 2 && g - 1 <= N / 4 - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
 #pragma unroll
