@@ -5,8 +5,8 @@ interiors its ghost refresh reads and the fine face fluxes its coarse-fine
 faces need, packed into flat buffers, and reduces the CFL step (min) and the
 totals (sum) with the other ranks.  Its leaves must come out bit-identical
 to the unpartitioned step, the step size identical, the totals equal to
-rounding.  World size 2 over gloo in separate processes; three ranks in one
-process with the buffers handed over directly."""
+rounding.  World size 2 over gloo in separate processes; three to five ranks
+in one process with the buffers handed over directly."""
 import os
 import socket
 
@@ -19,10 +19,11 @@ import torch.multiprocessing as mp
 DT, CYCLE, CFL = 2e-3, 1, 0.4
 
 
-def _setup():
+def _setup(bc=None, dual=False):
     import helpers as H
     from oracle import mesh as OM
-    od = H.oracle_desc(root=(2, 2, 2), n=8, lmax=2, dual_energy=False)
+    od = H.oracle_desc(root=(2, 2, 2), n=8, lmax=2, dual_energy=dual,
+                       **({} if bc is None else {"bc": bc}))
     rng = np.random.default_rng(11)
     mesh = OM.root_mesh(od)
     for _ in range(2):
@@ -106,9 +107,9 @@ class Rank:
         return len(self.need[self.r][peer]) * n3, len(self.flux[self.r][peer]) * face
 
 
-def _reference():
+def _reference(bc=None, dual=False):
     from oracle import hydro as OH
-    mesh, U0 = _setup()
+    mesh, U0 = _setup(bc, dual)
     U = OH.step(U0, mesh, DT, CYCLE)
     dt, totals = OH.reduce_dt_totals(U, mesh, CFL)
     return mesh, U, dt, totals
@@ -203,19 +204,24 @@ def test_sharded_step_gloo_world2():
         assert torch.allclose(totals, totref, rtol=1e-14, atol=0)
 
 
-def test_sharded_step_three_ranks_in_process():
-    mesh, Uref, dtref, totref = _reference()
-    _, U0 = _setup()
-    owner, need, flux = _plans(mesh, 3)
-    ranks = [Rank(r, mesh, U0, owner, need, flux) for r in range(3)]
+@pytest.mark.parametrize("nranks,bc,dual", [(3, None, False), (4, (1, 0, 1), False), (5, None, True)],
+                         ids=["3-periodic", "4-outflow-xz", "5-dual-energy"])
+def test_sharded_step_in_process(nranks, bc, dual):
+    """Several ranks in one process, buffers handed over directly; with
+    outflow faces (no neighbour behind them) and with the sixth field of
+    the dual-energy formalism."""
+    mesh, Uref, dtref, totref = _reference(bc, dual)
+    _, U0 = _setup(bc, dual)
+    owner, need, flux = _plans(mesh, nranks)
+    ranks = [Rank(r, mesh, U0, owner, need, flux) for r in range(nranks)]
     for me in ranks:
-        for peer in range(3):
+        for peer in range(nranks):
             if peer != me.r:
                 me.unpack_interiors(peer, ranks[peer].pack_interiors(me.r))
     for me in ranks:
         me.sweeps()
     for me in ranks:
-        for peer in range(3):
+        for peer in range(nranks):
             if peer != me.r:
                 me.unpack_fluxes(peer, ranks[peer].pack_fluxes(me.r))
     res = [me.finish() for me in ranks]
