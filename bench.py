@@ -378,8 +378,7 @@ def main():
     ap.add_argument("--max-wall", type=float, default=300.0, help="wall-time bound of the sedov-deep run (s)")
     ap.add_argument("--riemann", default="two-shock", choices=["two-shock", "hllc"])
     ap.add_argument("--steepening", action="store_true", help="contact steepening of the density edge values")
-    ap.add_argument("--dual-energy", action="store_true",
-                    help="dual-energy formalism (sixth field rho e; shared-memory sweep variants, no operation counts)")
+    ap.add_argument("--dual-energy", action="store_true", help="dual-energy formalism (a sixth field rho e)")
     ap.add_argument("--variants", default="", help="sweep variants x,y,z instead of autotuning (profiling)")
     ap.add_argument("--abc", type=float, default=0.0,
                     help="amplitude of an ABC flow added to every cell (0: blobs in a medium at rest)")
@@ -501,10 +500,8 @@ def main():
     sample_ids = np.unique(np.linspace(0, mesh.n_leaves - 1, 32).round().astype(np.int64))
     mesh.ghost_refresh(U)
     t_ops = time.time()
-    ops = None   # operation counts cover the five-field sweep
-    if mesh.nf == 5:
-        ops, pencils, swept_cells, _ = mesh.sweep_opcount(U, sample_ids, float(dt.item()), cycle)
-        log(f"[bench] operation count on {len(sample_ids)} leaves in {time.time() - t_ops:.1f}s")
+    ops, pencils, swept_cells, _ = mesh.sweep_opcount(U, sample_ids, float(dt.item()), cycle)
+    log(f"[bench] operation count on {len(sample_ids)} leaves in {time.time() - t_ops:.1f}s")
     scale = mesh.n_leaves / len(sample_ids)
     prof = mesh.profile_step(U, dt, cycle, cfg["cfl"])
     names = ["ghost_refresh", "sweep_1", "sweep_2", "sweep_3", "flux_correct", "reduce"]

@@ -70,7 +70,7 @@ typedef struct {
                        * that exceeds 1e-3 E, else from rho*e; rho*e is advected with the mass flux,
                        * takes the compression term -(dt/dx) p (u+ - u-) with the interface-state
                        * velocities, and is reset to E - ke after each sweep where that exceeds 0.1 E.
-                       * No adjoint or operation counts.  0: off */
+                       * No adjoint.  0: off */
 } cello_mesh_desc;
 
 /* Riemann solvers of the sweep (Sec. II.C, PPM): the Colella-Woodward
@@ -272,7 +272,8 @@ cello_status cello_poisson_solve(cello_mesh* mesh, const double* f_dev, double* 
  * scalar (one operation per add, subtract, multiply, divide, square root,
  * comparison, absolute value or copysign) over the pencils the sweep kernel
  * covers, on `count` leaves whose slabs the caller copied (ghosts refreshed)
- * into U_host (float32, [count][5][(n+2g)^3], overwritten with the swept
+ * into U_host (float32, [count][fields][(n+2g)^3] with 5 or, with dual
+ * energy, 6 fields, overwritten with the swept
  * state); leaf_ids are those leaves' indices in the mesh; dt and cycle as in
  * cello_hydro_step.  out[24]: for the k-th sweep of the step, out[8k+0..5]
  * are the operations of its six phases (primitives, slopes and shock

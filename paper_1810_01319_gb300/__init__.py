@@ -169,7 +169,7 @@ class Mesh:
         """Counted operations of the step's three sweeps on the given leaves
         (their slabs are copied to the host; the ghosts must be refreshed).
         Returns (ops [3, 6] per sweep and phase, pencils [3], cells [3], swept
-        host copy [count, 5, N, N, N]; five-field meshes only)."""
+        host copy [count, fields, N, N, N])."""
         ids = np.ascontiguousarray(np.asarray(leaf_ids, dtype=np.int32))
         host = U[torch.as_tensor(ids, dtype=torch.int64, device=U.device)].detach().to("cpu").contiguous()
         out = np.zeros(24, dtype=np.float64)

@@ -93,10 +93,10 @@ def build_hostcheck() -> str:
     (csrc/hostcheck.cu), used only by the CPU unit tests."""
     os.makedirs(BUILD, exist_ok=True)
     src = os.path.join(CSRC, "hostcheck.cu")
-    deps = [src] + [os.path.join(CSRC, f) for f in ("ppm.cuh", "adjoint.cuh")]
+    deps = [src] + [os.path.join(CSRC, f) for f in ("ppm.cuh", "adjoint.cuh", "opcount.cu", "cello_internal.h")]
     if _stale(HOSTCHECK, deps):
         cmd = [nvcc(), *ARCH, "-O2", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", CSRC,
-               "-shared", src, "-o", HOSTCHECK]
+               "-I", INCLUDE, "-shared", src, "-o", HOSTCHECK]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on hostcheck.cu:\n{r.stderr}")

@@ -184,6 +184,6 @@ void launch_particles_push(const DevMesh& m, const unsigned long long* keys, con
                            cudaStream_t s);
 // Host: counted operations of one leaf's sweep (opcount.cu), update applied.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
-                  int riemann, int steepen, unsigned long long counts[6]);
+                  int riemann, int steepen, int dual, unsigned long long counts[6]);
 
 }  // namespace cello

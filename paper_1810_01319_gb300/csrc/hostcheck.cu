@@ -1,8 +1,10 @@
 // Host-compiled entry points of the per-interface PPM arithmetic and its
-// hand-written adjoint, for CPU unit tests of the device math (the same
-// CELLO_HD functions the kernels run).  Built into a separate test library;
-// the product library does not contain it.
+// hand-written adjoint, and of the host operation count of a leaf's sweep,
+// for CPU unit tests of the device math (the same CELLO_HD functions the
+// kernels run).  Built into a separate test library; the product library
+// does not contain it.
 #include "adjoint.cuh"
+#include "opcount.cu"
 
 using namespace cello;
 
@@ -38,5 +40,11 @@ void cello_hc_window_flux_vjp(const double* U, double dtdx, double gamma, int pr
                               double* Ub) {
   if (precision == 4) vjp_t<float>(U, dtdx, gamma, Fb, Ub);
   else vjp_t<double>(U, dtdx, gamma, Fb, Ub);
+}
+// One leaf's sweep through the counting scalar (float32 arithmetic), its
+// update written back into slab [fields][N^3]; counts[6] per phase.
+void cello_hc_opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx,
+                           double gamma, int riemann, int steepen, int dual, unsigned long long* counts) {
+  opcount_leaf(slab, n, g, axis, a0, a1, b0, b1, dtdx, gamma, riemann, steepen, dual, counts);
 }
 }

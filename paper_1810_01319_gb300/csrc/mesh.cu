@@ -1005,11 +1005,10 @@ cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32
                                  double dt, int cycle, double* out) {
   if (!M || !U_host || !leaf_ids || !out || count <= 0) return fail(CELLO_EINVAL, "NULL argument or empty sample");
   if (M->desc.precision != 4) return fail(CELLO_EINVAL, "operation counts are taken on float32 meshes");
-  if (M->desc.dual_energy) return fail(CELLO_EINVAL, "operation counts cover the five-field sweep");
   for (int64_t i = 0; i < count; ++i)
     if (leaf_ids[i] < 0 || leaf_ids[i] >= M->B) return fail(CELLO_EINVAL, "leaf id out of range");
   const cello_mesh_desc& d = M->desc;
-  const long slab = 5L * M->N * M->N * M->N;
+  const long slab = (long)nfields(d) * M->N * M->N * M->N;
   const double dx0 = (d.hi[0] - d.lo[0]) / (d.root[0] * d.n);
   for (int k = 0; k < 3 * 8; ++k) out[k] = 0.0;
   const int order[3] = {cycle % 2 == 0 ? 0 : 2, 1, cycle % 2 == 0 ? 2 : 0};
@@ -1022,7 +1021,7 @@ cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32
     for (int64_t i = 0; i < count; ++i) {
       const double dtdx = dt / std::ldexp(dx0, -M->leaves[leaf_ids[i]].x);
       opcount_leaf(U_host + i * slab, d.n, d.ghosts, axis, a0, a1, b0, b1, dtdx, d.gamma, d.riemann, d.steepening,
-                   c);
+                   d.dual_energy, c);
     }
     for (int k = 0; k < 6; ++k) out[oi * 8 + k] = (double)c[k];
     out[oi * 8 + 6] = (double)count * (a1 - a0) * (b1 - b0);
