@@ -154,12 +154,26 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def test_halo_and_flux_plans_cover_the_refresh():
+def _random_mesh(seed, bc):
+    import helpers as H
+    from oracle import mesh as OM
+    od = H.oracle_desc(root=(2, 3, 2), n=8, lmax=2, bc=bc)
+    rng = np.random.default_rng(seed)
+    mesh = OM.root_mesh(od)
+    for _ in range(2):
+        mesh = OM.build(od, mesh, rng.choice([-1, 0, 1], size=mesh.n_leaves, p=[0.2, 0.4, 0.4]))
+    return mesh
+
+
+@pytest.mark.parametrize("seed,ranks,bc", [(0, 2, (0, 0, 0)), (1, 3, (1, 0, 0)), (2, 5, (0, 1, 1)),
+                                           (3, 7, (0, 0, 0))])
+def test_halo_and_flux_plans_cover_the_refresh(seed, ranks, bc):
     """Every ghost source of a leaf is itself or in its rank's receive list
-    (checked against the oracle's own refresh plan, source by source)."""
+    (checked against the oracle's own refresh plan, source by source), on
+    seeded random meshes of non-cubic root arrays split over 2 to 7 ranks."""
     from oracle import hydro as OH
-    mesh, _ = _setup()
-    owner, need, flux = _plans(mesh, 3)
+    mesh = _random_mesh(seed, bc)
+    owner, need, flux = _plans(mesh, ranks)
     plan = OH.RefreshPlan(mesh)
     N3 = plan.N3
     per_leaf = plan.nf * N3
