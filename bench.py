@@ -542,7 +542,7 @@ def main():
         sw = sweeps[kname]
         traffic, tsrc = None, None
         key = f"{sw['axis']}-{sw['form']}-{kname}"
-        if key in SWEEP_DRAM_BYTES_PER_LEAF and cfg["n"] == 32:
+        if key in SWEEP_DRAM_BYTES_PER_LEAF and cfg["n"] == 32 and mesh.nf == 5:   # measured on five fields
             traffic = SWEEP_DRAM_BYTES_PER_LEAF[key] * mesh.n_leaves
             tsrc = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per leaf of the same kernel and sweep "
                     "position on the 4^3-root blob box, times the leaves of this launch")
