@@ -622,12 +622,12 @@ def main():
             timing[inner] = a.elapsed_time(b) / 5
         vms = timing[4]
         _, res = pm.poisson_solve(fsrc, 5, phi=phi, residuals=True, inner=4)
-        cells = 512 ** 3
+        pcells = 512 ** 3
         # algorithmic bytes per V-cycle: on each level four Jacobi sweeps (read
         # phi and f, write phi: 24 B per cell), the residual restriction (read
         # phi and f: 16 B) and the prolongation (read and write phi: 16 B);
         # the levels add 1/7 to the finest
-        alg = 128.0 * cells * 8.0 / 7.0
+        alg = 128.0 * pcells * 8.0 / 7.0
         poisson = {"grid": "512^3 (16^3 roots x 32^3, uniform, periodic)",
                    "vcycle_ms_mixed": vms, "vcycle_ms_float64": timing[8],
                    "residual_reduction_per_cycle": (res[-1] / res[0]) ** (1.0 / (len(res) - 1)),

@@ -13,14 +13,11 @@ formulas; the readings taken here are:
   width at max_level (clamped into the root array), whose Morton key (the
   key of mesh.py) lies in [key(leaf), key(leaf) + 8^(max_level - L)) for
   exactly one leaf: the last leaf in key order whose key does not exceed it.
-* The tracer velocity is the fluid velocity (momentum times the reciprocal
-  of the density, density floored at 1e-10 as in the primitives of the
-  sweep) interpolated trilinearly between the cell centres of the
-  containing leaf's padded block (its ghost layer refreshed), linear along
-  x, then y, then z.  The reciprocal 1/rho is the correctly rounded float32
-  reciprocal of float32(rho), refined by two Newton steps r <- r (2 - rho r)
-  in float64 (each step doubles the correct bits; within 2 ulp for densities
-  in the float32 range), one per cell for the three components.
+* The tracer velocity is the fluid velocity, momentum divided by density
+  (the density floored at 1e-10 as in the primitives of the sweep), one
+  float64 division per cell and component, interpolated trilinearly
+  between the cell centres of the containing leaf's padded block (its ghost
+  layer refreshed), linear along x, then y, then z.
 * One step moves every live tracer by dt times that velocity (forward
   Euler), wraps it into the box along periodic axes and marks it lost
   (leaf -1; a lost tracer is not moved again) when it leaves through an
@@ -37,13 +34,6 @@ import torch
 from .mesh import PERIODIC, Mesh, morton_key
 
 RHO_FLOOR = 1e-10
-
-
-def reciprocal(rho: float) -> float:
-    """1/rho: IEEE float32 reciprocal of float32(rho), two float64 Newton steps."""
-    r = float(np.float32(1.0) / np.float32(rho))
-    r = r * (2.0 - rho * r)
-    return r * (2.0 - rho * r)
 
 
 def block_width(mesh: Mesh):
@@ -88,7 +78,7 @@ def velocity(U, mesh: Mesh, pos, leaf):
         for comp in range(3):
             def vel(z, y, x):
                 rho = max(float(U[b, 0, z, y, x]), RHO_FLOOR)
-                return float(U[b, 1 + comp, z, y, x]) * reciprocal(rho)
+                return float(U[b, 1 + comp, z, y, x]) / rho
             x0, y0, z0 = i0
             fx, fy, fz = f
             c00 = vel(z0, y0, x0) * (1.0 - fx) + vel(z0, y0, x0 + 1) * fx

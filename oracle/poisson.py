@@ -10,15 +10,13 @@ paper prints no formulas; the readings taken here are:
 * Problem: lap(phi) = f on the cell centres of a uniform mesh (every leaf
   at one level, periodic on every axis), the 7-point Laplacian
   lap(phi)_c = (((((phi_{x-1} + phi_{x+1}) + phi_{y-1}) + phi_{y+1})
-  + phi_{z-1}) + phi_{z+1} - 6 phi_c) * (1 / h^2), with 1 / h^2 computed
-  once per grid (multiplications by precomputed reciprocals, here and in
-  the Jacobi sweep, instead of divisions per cell).  The mean of f is removed
+  + phi_{z-1}) + phi_{z+1} - 6 phi_c) / h^2.  The mean of f is removed
   first (a periodic problem is solvable only for zero-mean f) and the mean
   of phi is removed at the end (phi is defined up to a constant).
 * Grids: the mesh's cells as one M^3 grid (M = root * 2^L * n per axis,
   cubic root arrays), coarsened by 2 while M is even and above 1.
 * V-cycle on a grid of spacing h: two damped Jacobi sweeps (weight 6/7),
-  phi <- (1 - w) phi + w (((sum of the 6 neighbours) - h^2 f) * (1/6)); the
+  phi <- (1 - w) phi + w ((sum of the 6 neighbours) - h^2 f) / 6; the
   residual r = f - lap(phi); restriction by the mean of the 8 children
   (summed in (dz, dy, dx) order, times 0.125); the coarse error from a
   V-cycle started at zero with spacing 2h; trilinear prolongation of the
@@ -47,15 +45,12 @@ def _nbsum(phi):
     return ((((xm + xp) + ym) + yp) + zm) + zp
 
 
-SIXTH = 1.0 / 6.0
-
-
 def laplacian(phi, h):
-    return (_nbsum(phi) - 6.0 * phi) * (1.0 / (h * h))
+    return (_nbsum(phi) - 6.0 * phi) / (h * h)
 
 
 def jacobi(phi, f, h):
-    return (1.0 - OMEGA) * phi + OMEGA * ((_nbsum(phi) - (h * h) * f) * SIXTH)
+    return (1.0 - OMEGA) * phi + OMEGA * ((_nbsum(phi) - (h * h) * f) / 6.0)
 
 
 def residual(phi, f, h):

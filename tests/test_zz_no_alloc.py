@@ -3,7 +3,8 @@ that cannot let the library allocate device memory at the point of use
 (allocation-free stream captures, fixed up-front device budgets, runtimes
 that own the device allocator).  Its scratch is a fixed array inside the
 library.  Checked through the C ABI against cello_reduce on two calls in a
-row, on different states, in both precisions.  Collected last on purpose."""
+row, on different states, in both precisions: bit for bit, since both run
+the same kernels in the same launch shape.  Collected last on purpose."""
 import numpy as np
 import pytest
 import torch
@@ -30,8 +31,10 @@ def test_noalloc_matches_reduce_on_two_calls(precision):
         gm.reduce_noalloc(U, 0.4, dt_next=na_dt, totals=na_tot)
         torch.cuda.synchronize()
         assert float(ref_dt) > 0
-        assert torch.allclose(na_dt, ref_dt, rtol=1e-12, atol=0)
-        assert torch.allclose(na_tot, ref_tot, rtol=1e-12, atol=1e-12 * float(ref_tot.abs().max()))
+        # the same kernels in the same launch shape, only the scratch differs:
+        # the results are bit-identical
+        assert torch.equal(na_dt, ref_dt)
+        assert torch.equal(na_tot, ref_tot)
         # advance the state so that the second call sees different data
         dt.copy_(ref_dt)
         gm.hydro_step(U, dt, call)
