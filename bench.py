@@ -41,9 +41,24 @@ WORKLOAD = dict(workload="blob-amr-large", root=[16, 16, 16], n=32, max_level=2,
 SWEEP_DRAM_BYTES_PER_LEAF = {"x-streaming-staged-sweep_1": 2.578e6, "y-streaming-staged-sweep_2": 2.291e6,
                              "z-streaming-staged-sweep_3": 1.831e6}
 
-# FP32 lane operations per second of the whole GPU at the maximum SM clock:
-# 152 SMs x 128 FP32 lanes x 2.07 GHz (one operation per lane per clock)
-ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+def alu_peak(log=print):
+    """The FP32 ALU roofline's denominator: measured FFMA lane instructions
+    per second (cello_fp32_ffma_rate), and the nominal figure from the
+    device's SM count x 128 FP32 lanes x the maximum SM clock."""
+    from paper_1810_01319_gb300 import fp32_ffma_rate
+    rate, ms = fp32_ffma_rate()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    try:
+        mhz = float(subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()), "--query-gpu=clocks.max.sm",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                   timeout=20).stdout.split()[0])
+    except Exception:
+        mhz = None
+    nominal = sms * 128 * mhz * 1e6 / 1e12 if mhz else None
+    log(f"[bench] FP32 FFMA rate {rate / 1e12:.2f} T lane-instr/s measured ({ms:.2f} ms launch); "
+        f"nominal {sms} SMs x 128 x {mhz} MHz = {nominal} T")
+    return rate / 1e12, sms, mhz, nominal
 
 
 def peaks():
@@ -213,6 +228,31 @@ SEDOV = dict(workload="sedov-deep", root=[4, 4, 4], n=16, max_level=5, E=1.0, rh
              tau=0.3, cfl=0.4, t_end=0.05, adapt_every=4, bc="periodic")
 
 
+def _cfl_limiter(U, leaves, cfg, n):
+    """Level, radius, density and pressure of the cell that sets the CFL
+    step (diagnostic of the deep Sedov run; torch on the device state)."""
+    from workloads import ics
+    g = 4
+    sl = (slice(None), slice(g, g + n), slice(g, g + n), slice(g, g + n))
+    I = U[(slice(None), slice(None)) + sl[1:]].double()
+    rho = I[:, 0].clamp_min(1e-10)
+    vel = I[:, 1:4] / rho[:, None]
+    ke = 0.5 * rho * (vel ** 2).sum(1)
+    p = ((cfg["gamma"] - 1.0) * (I[:, 4] - ke)).clamp_min(1e-20)
+    s = vel.abs().amax(1) + torch.sqrt(cfg["gamma"] * p / rho)
+    lvl = torch.as_tensor(leaves[:, 0], device=U.device)
+    dx = (1.0 / (cfg["root"][0] * n)) / (2.0 ** lvl.double())
+    cand = dx.view(-1, 1, 1, 1) / s
+    k = int(torch.argmin(cand))
+    b = k // n ** 3
+    x, y, z = ics.cell_centres(leaves[b:b + 1].astype(np.int64), cfg["root"], n, g, (0, 0, 0), (1, 1, 1),
+                               device=U.device)
+    c = k % n ** 3
+    zi, yi, xi = c // (n * n) + g, (c // n) % n + g, c % n + g
+    r = float(torch.sqrt((x[0, zi, yi, xi] - 0.5) ** 2 + (y[0, zi, yi, xi] - 0.5) ** 2 + (z[0, zi, yi, xi] - 0.5) ** 2))
+    return int(leaves[b, 0]), r, float(rho.reshape(-1)[k]), float(p.reshape(-1)[k])
+
+
 def sedov_run(cfg, precision, log=print, max_wall=300.0):
     """The deep-AMR Sedov-Taylor blast toward t_end with pressure-slope
     adaptation every few steps; stops at t_end or after max_wall seconds of
@@ -264,8 +304,12 @@ def sedov_run(cfg, precision, log=print, max_wall=300.0):
         cell_updates += mesh.n_leaves * n ** 3
         t += d
         steps += 1
-        if steps % 200 == 0:
-            log(f"[sedov] step {steps} t={t:.3e} dt={d:.2e} leaves={mesh.n_leaves} "
+        if steps % 500 == 0:
+            lv = mesh.leaves
+            hist = np.bincount(lv[:, 0], minlength=cfg["max_level"] + 1).tolist()
+            where = _cfl_limiter(U, lv, cfg, n)
+            log(f"[sedov] step {steps} t={t:.3e} dt={d:.2e} leaves={mesh.n_leaves} levels={hist} "
+                f"cfl-limiting cell: level {where[0]}, r={where[1]:.4f}, rho={where[2]:.3e}, p={where[3]:.3e} "
                 f"step_ms={step_ms:.0f} adapt_s={adapt_s:.1f} wall={time.time() - wall:.0f}s")
     wall = time.time() - wall
     # shock radius: density-weighted mean radius of cells within 10 % of the peak density
@@ -326,18 +370,50 @@ def e2e_host_buffers(cfg, steps, stream, log):
     m2 = mesh
     cells = mesh.n_leaves * cfg["n"] ** 3
     state_bytes = U.numel() * U.element_size()
-    # page-locked in place (the caching pinned allocator would round the
-    # size up to a power of two)
-    host = torch.empty(U.shape, dtype=U.dtype)
     cudart = torch.cuda.cudart()
-    if int(cudart.cudaHostRegister(host.data_ptr(), state_bytes, 0)) != 0:
-        return {"value": None, "unit": UNIT, "skipped": "cudaHostRegister failed"}
+
+    def timed(fn, reps=3):
+        """Median milliseconds of fn() on the stream, CUDA events."""
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    # the host link for the two ways of page-locking a host buffer: pageable
+    # memory registered in place (cudaHostRegister) and memory allocated
+    # page-locked (cudaHostAlloc, torch's pinned allocator)
+    links = {}
+    reg = torch.empty(U.shape, dtype=U.dtype)
+    if int(cudart.cudaHostRegister(reg.data_ptr(), state_bytes, 0)) == 0:
+        reg.copy_(U)
+        with torch.cuda.stream(stream):
+            links["registered"] = (timed(lambda: U.copy_(reg, non_blocking=True)),
+                                   timed(lambda: reg.copy_(U, non_blocking=True)))
+        cudart.cudaHostUnregister(reg.data_ptr())
+    del reg
+    host = torch.empty(U.shape, dtype=U.dtype, pin_memory=True)
     host.copy_(U)
     torch.cuda.synchronize()
     dt_next = torch.zeros(1, dtype=torch.float64, device="cuda")
     mesh.reduce(U, cfg["cfl"], dt_next=dt_next)
     dt_host = float(dt_next.item())
     h2d_extra, d2h_extra = 8, 48
+
+    # the host link and the step alone, in the same run: the per-call time
+    # should be their sum
+    with torch.cuda.stream(stream):
+        h2d_ms = timed(lambda: U.copy_(host, non_blocking=True))
+        d2h_ms = timed(lambda: host.copy_(U, non_blocking=True))
+    links["allocated"] = (h2d_ms, d2h_ms)
+    dt_dev = torch.full((1,), dt_host, dtype=torch.float64, device="cuda")
+    step_ms = timed(lambda: mesh.hydro_step(U, dt_dev, 0, cfg["cfl"], stream=stream))
+    host.copy_(U)
     for c in range(2):
         dt_host, _ = mesh.hydro_step_host(host, U, dt_host, c, cfg["cfl"], stream=stream)
     calls = []
@@ -349,11 +425,18 @@ def e2e_host_buffers(cfg, steps, stream, log):
     el = time.perf_counter() - t0
     res = {"value": cells * steps / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes + h2d_extra,
            "d2h_bytes_per_step": state_bytes + d2h_extra, "workload": workload, "leaves": mesh.n_leaves,
-           "call": "cello_hydro_step_host (state in page-locked host memory, copied in and out every step)",
+           "call": "cello_hydro_step_host (state in page-locked host memory from cudaHostAlloc, copied in and "
+                   "out every step)",
            "call_ms": {"min": min(calls) * 1e3, "median": statistics.median(calls) * 1e3, "max": max(calls) * 1e3},
-           "timer": "host wall clock around each call, which waits for its stream"}
+           "timer": "host wall clock around each call, which waits for its stream",
+           "link": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms, "h2d_gbs": state_bytes / h2d_ms / 1e6,
+                    "d2h_gbs": state_bytes / d2h_ms / 1e6, "step_ms": step_ms,
+                    "expected_call_ms": h2d_ms + d2h_ms + step_ms,
+                    "how": "plain copies of the same page-locked buffer and one device step, CUDA events, "
+                           "median of 3, in the same run just before the timed calls",
+                    "by_allocation": {k: {"h2d_gbs": state_bytes / v[0] / 1e6, "d2h_gbs": state_bytes / v[1] / 1e6}
+                                      for k, v in links.items()}}}
     torch.cuda.synchronize()
-    cudart.cudaHostUnregister(host.data_ptr())
     del host
     if m2 is not None:
         del U, m2
@@ -461,6 +544,7 @@ def main():
         log(f"[bench] autotuned sweep variants (x, y, z) {variant}: "
             f"{[['%.2f' % t for t in axes] for axes in variant_ms]} ms")
     mesh.set_exec(EXEC_GRAPH)
+    alu_tops, alu_sms, alu_mhz, alu_nominal = alu_peak(log)
     cells = mesh.n_leaves * cfg["n"] ** 3
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
     dt_next = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -546,9 +630,17 @@ def main():
             traffic = SWEEP_DRAM_BYTES_PER_LEAF[key] * mesh.n_leaves
             tsrc = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per leaf of the same kernel and sweep "
                     "position on the 4^3-root blob box, times the leaves of this launch")
-        roofline = {"bound": "alu", "kernel": kname, "achieved": sw["achieved_tops"], "peak": ALU_PEAK_TOPS,
-                    "unit": "T FP32 lane-op/s", "frac": sw["achieved_tops"] / ALU_PEAK_TOPS,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per lane per clock",
+        roofline = {"bound": "alu", "kernel": kname, "achieved": sw["achieved_tops"], "peak": alu_tops,
+                    "unit": "T FP32 lane-op/s", "frac": sw["achieved_tops"] / alu_tops,
+                    "peak_source": "measured: cello_fp32_ffma_rate, FP32 fused multiply-add lane instructions "
+                                   "per second, 8 CTAs x 256 threads per SM, 16 independent chains each",
+                    "peak_nominal": {"value": alu_nominal, "sms": alu_sms, "sm_max_mhz": alu_mhz,
+                                     "formula": "SMs x 128 FP32 lanes x max SM clock"},
+                    "convention": "operation-count ratio: the numerator counts every add, multiply, divide, "
+                                  "square root, comparison, abs and copysign of the sweep's formulas as one "
+                                  "operation, so a fused multiply-add counts two, while the peak counts one "
+                                  "FFMA instruction per lane per clock; against the flop convention (an FFMA = "
+                                  "2 flops, peak x 2) the same count gives half this frac",
                     "traffic": traffic, "traffic_source": tsrc,
                     "algorithmic_ops_per_launch": sw["ops_per_launch"],
                     "ops_sample": f"{len(sample_ids)} leaves evenly spaced in Morton order, scaled by "

@@ -248,7 +248,10 @@ cello_status cello_particles_push(cello_mesh* mesh, const void* U, double* pos_d
 /* Poisson solve, lap(phi) = f (Sec. II.C: Enzo-P's mg0 geometric multigrid
  * V-cycle, the self-gravity solver of the paper's uniform-grid runs), on a
  * uniform mesh (every leaf at one level), periodic on every axis, cubic
- * root array, at most 1024 cells per axis.  f_dev and phi_dev: device
+ * root array, at most 512 blocks per axis.  The V-cycle runs on the leaf
+ * blocks while they have at least 4 cells per edge, each block with a
+ * one-cell ghost layer refreshed from its neighbours through the mesh's
+ * neighbour table, and on single arrays below that.  f_dev and phi_dev: device
  * float64 leaf interiors [B][n^3] (no ghosts; x fastest) in leaf order.
  * The 7-point cell-centred Laplacian; the mean of f is removed first and
  * the mean of phi last.  cycles V-cycles from phi = 0, each two damped
@@ -261,8 +264,9 @@ cello_status cello_particles_push(cello_mesh* mesh, const void* U, double* pos_d
  * cost).  resid_host (nullable, host,
  * `cycles` doubles) receives the max-norm of the residual after each cycle,
  * and then the call waits for the stream.  The first solve on a mesh
- * allocates the level arrays (about 4/7 x 3 x 8 bytes per cell), freed with
- * the mesh.  CELLO_EINVAL on a mesh it does not support. */
+ * allocates the level arrays (padded blocks: about 3 x 8 x 1.3 bytes per
+ * cell for n = 32, more for smaller blocks), freed with the mesh.
+ * CELLO_EINVAL on a mesh it does not support. */
 cello_status cello_poisson_solve(cello_mesh* mesh, const double* f_dev, double* phi_dev, int cycles, int inner,
                                  double* resid_host, void* stream);
 
@@ -317,6 +321,16 @@ cello_status cello_profile_step(cello_mesh* mesh, void* U, const double* dt_dev,
  * has to start at zero; calls that overlap on the GPU race on it. */
 cello_status cello_reduce_noalloc(cello_mesh* mesh, const void* U, double cfl, double* dt_next_dev,
                                   double* totals_dev, void* stream);
+
+/* Measured FP32 issue rate of the current device, the denominator of the
+ * sweep's ALU roofline (not a step of the method; the paper has no
+ * counterpart).  Launches 8 CTAs of 256 threads per SM, each thread running
+ * 16 independent fused multiply-add chains, times the launch with CUDA
+ * events on `stream` (best of three after one warm-up) and writes the FP32
+ * fused multiply-adds per second (lane instructions: one per lane per
+ * clock at the pipes' peak; twice that in flop/s) to *ffma_per_s and the
+ * launch's milliseconds to *ms_out (nullable).  Blocks until done. */
+cello_status cello_fp32_ffma_rate(double* ffma_per_s, double* ms_out, void* stream);
 
 /* Text of the calling thread's last error ("" if none). */
 const char* cello_last_error(void);

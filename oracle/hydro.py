@@ -515,9 +515,12 @@ class RefreshPlan:
         the level-L-1 neighbours C+-e_d (boundary rule at level L-1) are copied
         from a level-L-1 leaf, restricted from level-L leaves or injected from
         the level-L-2 leaf that covers them.
-    The sources are always leaf interiors, so the refresh has no ordering."""
+    The sources are always leaf interiors, so the refresh has no ordering.
 
-    def __init__(self, mesh: Mesh):
+    dest: optional list of leaf indices whose ghosts the plan fills (all
+    leaves by default); sources may still be any leaf of the mesh."""
+
+    def __init__(self, mesh: Mesh, dest=None):
         d = mesh.desc
         n, g = d.n, d.ghosts
         N = n + 2 * g
@@ -572,8 +575,8 @@ class RefreshPlan:
                 idx[c, 0] = flat(cc, Zc % n + g, Yc % n + g, Xc % n + g)
             return idx, mode
 
-        for b, (L, bi, bj, bk) in enumerate(mesh.leaves):
-            L, bi, bj, bk = int(L), int(bi), int(bj), int(bk)
+        for b in (range(mesh.n_leaves) if dest is None else dest):
+            L, bi, bj, bk = (int(v) for v in mesh.leaves[b])
             X = _bc(mesh, L, 0, bi * n + gx - g)
             Y = _bc(mesh, L, 1, bj * n + gy - g)
             Z = _bc(mesh, L, 2, bk * n + gz - g)
@@ -616,6 +619,30 @@ class RefreshPlan:
         self.pro_sg = (torch.from_numpy(np.concatenate(pro_sg)) if pro_sg
                        else torch.zeros((0, 3), dtype=torch.float64))
         self.pro_nb, self.pro_mode = cat(pro_nb, (0, 6, 8)), cat(pro_mode, (0, 6))
+
+    def leaves_read(self):
+        """Sorted indices of the leaves the plan reads or writes."""
+        per = self.nf * self.N3
+        ids = [t.reshape(-1) // per for t in (self.copy_d, self.copy_s, self.rst_d, self.rst_s, self.pro_d,
+                                              self.pro_c, self.pro_nb) if t.numel()]
+        return np.unique(torch.cat(ids).numpy()) if ids else np.zeros(0, dtype=np.int64)
+
+    def compact(self, leaves):
+        """The same plan over a pool that holds only `leaves` (sorted, a
+        superset of leaves_read()), leaf leaves[k] at slot k."""
+        per = self.nf * self.N3
+        pos = torch.full((int(max(leaves)) + 1,), -1, dtype=torch.int64)
+        pos[torch.as_tensor(leaves, dtype=torch.int64)] = torch.arange(len(leaves), dtype=torch.int64)
+        out = RefreshPlan.__new__(RefreshPlan)
+        out.__dict__.update(self.__dict__)
+        for name in ("copy_d", "copy_s", "rst_d", "rst_s", "pro_d", "pro_c", "pro_nb"):
+            t = getattr(self, name)
+            if t.numel():
+                slot = pos[t // per]
+                assert bool((slot >= 0).all()), "a leaf the plan reads is missing from the pool"
+                t = slot * per + t % per
+            setattr(out, name, t)
+        return out
 
     def apply(self, U):
         shape = U.shape

@@ -46,6 +46,16 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def fp32_ffma_rate(stream=None):
+    """Measured FP32 fused multiply-adds per second of the current device
+    (lane instructions) and the timed launch's milliseconds: the ALU
+    roofline's denominator (cello_fp32_ffma_rate)."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _lib.check(_lib.lib().cello_fp32_ffma_rate(ctypes.byref(rate), ctypes.byref(ms), _stream(stream)),
+               "cello_fp32_ffma_rate")
+    return rate.value, ms.value
+
+
 class Mesh:
     """A leaf table built by cello_octree_build; owns the C handle."""
 

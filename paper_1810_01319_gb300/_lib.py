@@ -53,6 +53,7 @@ SIGNATURES = {
     "cello_hydro_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    "cello_fp32_ffma_rate": (ctypes.c_int, [_vp, _vp, _vp]),
     "cello_set_exec": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cello_set_sweep_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cello_set_sweep_variants": (ctypes.c_int, [_vp, _vp]),

@@ -133,14 +133,18 @@ void prepare_kernels_f64();
 // Launchers (defined in the kernel translation units).
 void launch_neighbour_table(const DevMesh& m, const unsigned long long* keys, int8_t* kind, int* idx,
                             int* fine8, cudaStream_t s);
-// Ghost refresh of leaves [leaf0, leaf0+nleaf): vector copies of same-level
-// runs, then the listed slow runs (leaf * runs_per_leaf + run) cell by cell.
-void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const long long* slow, int nslow,
-                        cudaStream_t s);
-void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const long long* slow, int nslow,
-                        cudaStream_t s);
-int ghost_run_count(int n);
-void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsigned char* out, cudaStream_t s);
+// Ghost refresh of leaves [leaf0, leaf0+nleaf) in phases, in this order: the
+// listed slow faces (leaf * 6 + face of the faces of these leaves whose
+// neighbour is not a same-level leaf: their phase regions computed from leaf
+// interiors), then the same-level face copies along x, y and z (each phase
+// reads the margins the earlier ones filled in the face neighbours).
+// `phases` selects a subset; a phase must have run on every leaf before the
+// next one starts.
+enum RefreshPhase : int { kRefreshSlow = 1, kRefreshX = 2, kRefreshY = 4, kRefreshZ = 8, kRefreshAll = 15 };
+void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const int* slow, int nslow,
+                        int phases, cudaStream_t s);
+void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const int* slow, int nslow,
+                        int phases, cudaStream_t s);
 void launch_sweep_f32(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 void launch_sweep_f64(const DevMesh& m, const SweepParams& p, int pencils, cudaStream_t s);
 // Dual-energy sweeps (both float32 forms, k_de_f32.cu; float64, k_de_f64.cu),

@@ -113,50 +113,48 @@ void prepare_kernels_f64() {
   prepare_adj<32>();
 }
 
+template <typename T, int NB, int NF>
+static void refresh_nf(const DevMesh& m, T* U, int leaf0, int nleaf, const int* slow, int nslow, int phases,
+                       cudaStream_t s) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  auto blocks = [](long threads, int per) { return (unsigned)((threads + per - 1) / per); };
+  if ((phases & kRefreshSlow) && nslow > 0) refresh_slow_kernel<T, NB, NF><<<nslow, 128, 0, s>>>(m, U, slow, nslow);
+  if (nleaf <= 0) return;
+  if (phases & kRefreshX)
+    refresh_x_kernel<T, NB, NF><<<blocks((long)nleaf * NB * NB, 256), 256, 0, s>>>(m, U, leaf0, nleaf);
+  constexpr int S = Sector<T>::kCells;
+  if (phases & kRefreshY)
+    refresh_y_kernel<T, NB, NF><<<blocks((long)nleaf * 2 * NF * NB * (G * N / S), 256), 256, 0, s>>>(m, U, leaf0,
+                                                                                                   nleaf);
+  if (phases & kRefreshZ)
+    refresh_z_kernel<T, NB, NF><<<blocks((long)nleaf * 2 * NF * (G * N * N / S), 256), 256, 0, s>>>(m, U, leaf0,
+                                                                                                    nleaf);
+}
+
 template <typename T, int NB>
-static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, const long long* slow, int nslow,
+static void refresh_n(const DevMesh& m, T* U, int leaf0, int nleaf, const int* slow, int nslow, int phases,
                       cudaStream_t s) {
-  const long threads = (long)ghost_runs<NB>() * nleaf;
-  const unsigned grid = (unsigned)((threads + 255) / 256), sgrid = (unsigned)((nslow + 127) / 128);
-  if (m.nf == 6) {
-    if (threads > 0) refresh_kernel<T, NB, 6><<<grid, 256, 0, s>>>(m, U, leaf0, nleaf);
-    if (nslow > 0) refresh_slow_kernel<T, NB, 6><<<sgrid, 128, 0, s>>>(m, U, slow, nslow);
-    return;
-  }
-  if (threads > 0) refresh_kernel<T, NB><<<grid, 256, 0, s>>>(m, U, leaf0, nleaf);
-  if (nslow > 0) refresh_slow_kernel<T, NB><<<sgrid, 128, 0, s>>>(m, U, slow, nslow);
+  if (m.nf == 6) refresh_nf<T, NB, 6>(m, U, leaf0, nleaf, slow, nslow, phases, s);
+  else refresh_nf<T, NB, 5>(m, U, leaf0, nleaf, slow, nslow, phases, s);
 }
 
 template <typename T>
-static void refresh_t(const DevMesh& m, T* U, int leaf0, int nleaf, const long long* slow, int nslow,
+static void refresh_t(const DevMesh& m, T* U, int leaf0, int nleaf, const int* slow, int nslow, int phases,
                       cudaStream_t s) {
   switch (m.n) {
-    case 8: refresh_n<T, 8>(m, U, leaf0, nleaf, slow, nslow, s); break;
-    case 16: refresh_n<T, 16>(m, U, leaf0, nleaf, slow, nslow, s); break;
-    case 32: refresh_n<T, 32>(m, U, leaf0, nleaf, slow, nslow, s); break;
+    case 8: refresh_n<T, 8>(m, U, leaf0, nleaf, slow, nslow, phases, s); break;
+    case 16: refresh_n<T, 16>(m, U, leaf0, nleaf, slow, nslow, phases, s); break;
+    case 32: refresh_n<T, 32>(m, U, leaf0, nleaf, slow, nslow, phases, s); break;
   }
 }
 
-void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const long long* slow, int nslow,
-                        cudaStream_t s) {
-  refresh_t<float>(m, U, leaf0, nleaf, slow, nslow, s);
+void launch_refresh_f32(const DevMesh& m, float* U, int leaf0, int nleaf, const int* slow, int nslow,
+                        int phases, cudaStream_t s) {
+  refresh_t<float>(m, U, leaf0, nleaf, slow, nslow, phases, s);
 }
-void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const long long* slow, int nslow,
-                        cudaStream_t s) {
-  refresh_t<double>(m, U, leaf0, nleaf, slow, nslow, s);
-}
-
-int ghost_run_count(int n) { return n == 8 ? ghost_runs<8>() : (n == 16 ? ghost_runs<16>() : ghost_runs<32>()); }
-
-void launch_classify_runs(const DevMesh& m, const int* leaves, int nleaf, unsigned char* out, cudaStream_t s) {
-  const long threads = (long)ghost_run_count(m.n) * nleaf;
-  if (threads <= 0) return;
-  const unsigned grid = (unsigned)((threads + 255) / 256);
-  switch (m.n) {
-    case 8: classify_runs_kernel<8><<<grid, 256, 0, s>>>(m, leaves, nleaf, out); break;
-    case 16: classify_runs_kernel<16><<<grid, 256, 0, s>>>(m, leaves, nleaf, out); break;
-    case 32: classify_runs_kernel<32><<<grid, 256, 0, s>>>(m, leaves, nleaf, out); break;
-  }
+void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const int* slow, int nslow,
+                        int phases, cudaStream_t s) {
+  refresh_t<double>(m, U, leaf0, nleaf, slow, nslow, phases, s);
 }
 
 template <typename T, int NB>

@@ -731,71 +731,200 @@ template <> struct Vec4<double> {
     reinterpret_cast<double2*>(p)[1] = b;
   }
 };
-
-// Ghost runs: four consecutive ghost cells along x.  Every run starts at a
-// multiple of four cells, so source and destination are 16-byte aligned.
-template <int NB>
-__host__ __device__ constexpr int ghost_runs() {
-  return ((NB + 8) * (NB + 8) * (NB + 8) - NB * NB * NB) / 4;
+__device__ __forceinline__ void store_lanes(const Vec4<float>& v, float* o) {
+  o[0] = v.a.x; o[1] = v.a.y; o[2] = v.a.z; o[3] = v.a.w;
+}
+__device__ __forceinline__ void store_lanes(const Vec4<double>& v, double* o) {
+  o[0] = v.a.x; o[1] = v.a.y; o[2] = v.b.x; o[3] = v.b.y;
+}
+__device__ __forceinline__ void load_lanes(Vec4<float>& v, const float* o) {
+  v.a = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void load_lanes(Vec4<double>& v, const double* o) {
+  v.a = make_double2(o[0], o[1]);
+  v.b = make_double2(o[2], o[3]);
 }
 
-// Direction of a run after the outflow clamp on y and z; false if the run
-// is not a plain same-level copy (coarser or finer neighbour, or clamped
-// along x).
-template <int NB>
-__device__ __forceinline__ bool run_is_copy(const DevMesh& m, int leaf, int x0, int y, int z, int c[3], int d[3],
-                                            int& e) {
-  constexpr int G = kGhosts;
-  d[0] = x0 < G ? -1 : (x0 >= G + NB ? 1 : 0);
-  d[1] = y < G ? -1 : (y >= G + NB ? 1 : 0);
-  d[2] = z < G ? -1 : (z >= G + NB ? 1 : 0);
-  c[0] = x0; c[1] = y; c[2] = z;
-  if (d[0] != 0 && m.kind[leaf * 27 + face_dir(0, d[0])] == kBoundary) return false;
-  for (int a = 1; a < 3; ++a)
-    if (d[a] != 0 && m.kind[leaf * 27 + face_dir(a, d[a])] == kBoundary) {
-      c[a] = d[a] < 0 ? G : G + NB - 1;
-      d[a] = 0;
-    }
-  e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
-  return m.kind[e] == kSame;
-}
+// One 32-byte DRAM sector of consecutive cells (8 floats or 4 doubles),
+// moved by a single 256-bit access: a sector written whole by one store is
+// not read from DRAM first, which a store of half a sector would cause.
+// The address must be 32-byte aligned.
+template <typename T> struct Sector;
+template <> struct Sector<float> {
+  static constexpr int kCells = 8;
+  float v[8];
+  __device__ __forceinline__ void load(const float* p) {
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+  }
+  __device__ __forceinline__ void store(float* p) const {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+  }
+};
+template <> struct Sector<double> {
+  static constexpr int kCells = 4;
+  double v[4];
+  __device__ __forceinline__ void load(const double* p) {
+    asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+  }
+  __device__ __forceinline__ void store(double* p) const {
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
+                 : "memory");
+  }
+};
 
-// Same-level copies: one thread per run, one 16-byte vector per field.  Runs
-// that are not plain copies are left to refresh_slow_kernel.
+// The refresh runs in three phases, one per axis, each a copy across the
+// faces of that axis from same-level face neighbours:
+//   X: the x margins of interior rows (y and z interior);
+//   Y: the y-ghost rows of interior z planes, all N cells of each row;
+//   Z: the z-ghost planes, all N x N cells of each.
+// A ghost cell's value depends only on its position and level (the level-L
+// cell there after the boundary rule), so the margins of a face neighbour's
+// rows, filled by an earlier phase, are exactly the edge and corner ghosts
+// of this leaf: Y copies whole rows (x margins included) and Z whole planes.
+// A face whose neighbour is not a same-level leaf (coarser, finer, outflow
+// boundary) has its phase region listed as slow work, computed from leaf
+// interiors.
+//
+// Phase X: one thread per (leaf A, interior row).  If A's -x face neighbour
+// B is a same-level leaf the thread fills both margins of that face: A's -x
+// margin from B's last four interior cells and B's +x margin from A's first
+// four.  Every access is one whole 32-byte sector: in float32 a 4-cell
+// margin is half of the sector it shares with the adjacent interior run, so
+// the thread loads A's first sector (ghost, interior) and B's last (interior,
+// ghost) and stores both back whole, each as (B's run, A's run); in float64 a
+// margin is a sector of its own.  A's +x margin is filled by the thread of
+// A's +x neighbour, or is slow work.
 template <typename T, int NB, int NF = 5>
-__global__ void __launch_bounds__(256) refresh_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
-  constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
+__global__ void __launch_bounds__(256) refresh_x_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long)nleaf * NS) return;
-  const int leaf = leaf0 + (int)(gid / NS);
-  int x0, y, z, c[3], d[3], e;
-  ghost_coord<NB>((int)(gid % NS) * 4, x0, y, z);
-  if (!run_is_copy<NB>(m, leaf, x0, y, z, c, d, e)) return;
-  const long dst = (long)leaf * NF * SLAB + ((long)z * N + y) * N + x0;
-  const long src = (long)m.idx[e] * NF * SLAB + ((long)(c[2] - d[2] * NB) * N + (c[1] - d[1] * NB)) * N +
-                   (c[0] - d[0] * NB);
-  Vec4<T> v[NF];
+  if (gid >= (long)nleaf * NB * NB) return;
+  const int A = leaf0 + (int)(gid / (NB * NB));
+  const int r = (int)(gid % (NB * NB));
+  const int e = A * 27 + face_dir(0, -1);
+  if (m.kind[e] != kSame) return;
+  const int Bn = m.idx[e];
+  const long row = ((long)(G + r / NB) * N + (G + r % NB)) * N;
+  T* a = U + (long)A * NF * SLAB + row;
+  T* b = U + (long)Bn * NF * SLAB + row;
+  if constexpr (sizeof(T) == 4) {
+    Sector<T> sa[NF], sb[NF];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) v[f].load(U + src + f * SLAB);
+    for (int f = 0; f < NF; ++f) {
+      sa[f].load(a + f * SLAB);        // A: cells 0..7 (ghost 0..3, interior 4..7)
+      sb[f].load(b + f * SLAB + NB);   // B: cells NB..NB+7 (interior NB..NB+3, ghost)
+    }
 #pragma unroll
-  for (int f = 0; f < NF; ++f) v[f].store(U + dst + f * SLAB);
+    for (int f = 0; f < NF; ++f) {
+      Sector<T> o;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o.v[i] = sb[f].v[i];
+        o.v[4 + i] = sa[f].v[4 + i];
+      }
+      o.store(a + f * SLAB);
+      o.store(b + f * SLAB + NB);
+    }
+  } else {
+    Sector<T> sa[NF], sb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sa[f].load(a + f * SLAB + G);    // A's first interior run
+      sb[f].load(b + f * SLAB + NB);   // B's last interior run
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sb[f].store(a + f * SLAB);          // A's -x margin
+      sa[f].store(b + f * SLAB + G + NB); // B's +x margin
+    }
+  }
 }
 
-// The remaining runs (listed per mesh as leaf * runs + run), one run of four
-// cells per thread: a run clamped along x repeats one value; a run inside a
-// finer neighbour restricts cell by cell; a run inside a coarser neighbour
-// covers two parent cells, each prolonged once for its two children.
+// Phase Y: one thread per (leaf, side, field, interior z, sector of the G
+// rows of that side), copying from the same-level y neighbour C's G interior
+// rows next to the face; the G rows of one z plane are contiguous (G N
+// cells, whole sectors).
 template <typename T, int NB, int NF = 5>
-__global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, const long long* runs, int nruns) {
-  constexpr int G = kGhosts, N = NB + 2 * G, NS = ghost_runs<NB>();
+__global__ void __launch_bounds__(256) refresh_y_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
+  constexpr int G = kGhosts, N = NB + 2 * G, S = Sector<T>::kCells, RUNS = G * N / S;
   constexpr long SLAB = (long)N * N * N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nruns) return;
-  const long long r = runs[i];
-  const int leaf = (int)(r / NS);
-  int x0, y, z;
-  ghost_coord<NB>((int)(r % NS) * 4, x0, y, z);
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)nleaf * 2 * NF * NB * RUNS) return;
+  long q = gid;
+  const int v = (int)(q % RUNS); q /= RUNS;
+  const int z = G + (int)(q % NB); q /= NB;
+  const int f = (int)(q % NF); q /= NF;
+  const int side = (int)(q % 2) ? 1 : -1;
+  const int leaf = leaf0 + (int)(q / 2);
+  const int e = leaf * 27 + face_dir(1, side);
+  if (m.kind[e] != kSame) return;
+  const int C = m.idx[e];
+  const int yd = side < 0 ? 0 : G + NB, ys = side < 0 ? NB : G;
+  Sector<T> t;
+  t.load(U + (long)C * NF * SLAB + f * SLAB + ((long)z * N + ys) * N + S * v);
+  t.store(U + (long)leaf * NF * SLAB + f * SLAB + ((long)z * N + yd) * N + S * v);
+}
+
+// Phase Z: one thread per (leaf, side, field, sector of the G planes of that
+// side), copying from the same-level z neighbour's G interior planes next to
+// the face (G N N contiguous cells).
+template <typename T, int NB, int NF = 5>
+__global__ void __launch_bounds__(256) refresh_z_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
+  constexpr int G = kGhosts, N = NB + 2 * G, S = Sector<T>::kCells, RUNS = G * N * N / S;
+  constexpr long SLAB = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long)nleaf * 2 * NF * RUNS) return;
+  long q = gid;
+  const int v = (int)(q % RUNS); q /= RUNS;
+  const int f = (int)(q % NF); q /= NF;
+  const int side = (int)(q % 2) ? 1 : -1;
+  const int leaf = leaf0 + (int)(q / 2);
+  const int e = leaf * 27 + face_dir(2, side);
+  if (m.kind[e] != kSame) return;
+  const int C = m.idx[e];
+  const int zd = side < 0 ? 0 : G + NB, zs = side < 0 ? NB : G;
+  Sector<T> t;
+  t.load(U + (long)C * NF * SLAB + f * SLAB + (long)zs * N * N + S * v);
+  t.store(U + (long)leaf * NF * SLAB + f * SLAB + (long)zd * N * N + S * v);
+}
+
+// Runs of four cells (x0 .. x0+3, y, z) in the phase region of one face
+// (axis, side) of a leaf: the x margin of the interior rows (X), the G ghost
+// rows of the interior z planes (Y), the G ghost planes (Z).
+template <int NB>
+__host__ __device__ constexpr int face_region_runs(int axis) {
+  return axis == 0 ? NB * NB
+                   : (axis == 1 ? NB * kGhosts * ((NB + 2 * kGhosts) / 4)
+                                : kGhosts * (NB + 2 * kGhosts) * ((NB + 2 * kGhosts) / 4));
+}
+
+template <int NB>
+__device__ __forceinline__ void face_region_run(int axis, int side, int r, int& x0, int& y, int& z) {
+  constexpr int G = kGhosts, N = NB + 2 * G, R = N / 4;
+  const int lo = side < 0 ? 0 : G + NB;
+  if (axis == 0) {
+    x0 = lo; y = G + r % NB; z = G + r / NB;
+  } else if (axis == 1) {
+    x0 = 4 * (r % R); y = lo + (r / R) % G; z = G + r / (R * G);
+  } else {
+    x0 = 4 * (r % R); y = (r / R) % N; z = lo + r / (R * N);
+  }
+}
+
+// One run that is not a phase copy: a run clamped along x repeats one value;
+// a run inside a coarser neighbour covers two parent cells, each prolonged
+// once for its two children; any other run (restriction from finer leaves,
+// or a same-level diagonal source seen through a face that is not
+// same-level) is evaluated cell by cell.  Sources are leaf interiors only.
+template <typename T, int NB, int NF>
+__device__ void refresh_slow_run(const DevMesh& m, T* U, int leaf, int x0, int y, int z) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
   const long dst = (long)leaf * NF * SLAB + ((long)z * N + y) * N + x0;
   int d[3] = {x0 < G ? -1 : (x0 >= G + NB ? 1 : 0), y < G ? -1 : (y >= G + NB ? 1 : 0),
               z < G ? -1 : (z >= G + NB ? 1 : 0)};
@@ -873,19 +1002,158 @@ __global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, cons
   }
 }
 
-// Classification of every run of the listed leaves, for the host's slow-run
-// list: out[k * runs + run] = 1 if that run of leaf leaves[k] is not a plain
-// copy.
+// Quads of runs: runs (x0, y + jy, z + jz), jy, jz in {0, 1}, y and z even,
+// so that in each axis the two rows are the two children of one parent row.
+// The quads tile the phase region of a face (its extents in y and z are even).
 template <int NB>
-__global__ void __launch_bounds__(256) classify_runs_kernel(DevMesh m, const int* leaves, int nleaf,
-                                                            unsigned char* out) {
-  constexpr int NS = ghost_runs<NB>();
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long)nleaf * NS) return;
-  const int leaf = leaves[gid / NS];
-  int x0, y, z, c[3], d[3], e;
-  ghost_coord<NB>((int)(gid % NS) * 4, x0, y, z);
-  out[gid] = run_is_copy<NB>(m, leaf, x0, y, z, c, d, e) ? 0 : 1;
+__host__ __device__ constexpr int face_region_quads(int axis) {
+  return face_region_runs<NB>(axis) / 4;
+}
+
+template <int NB>
+__device__ __forceinline__ void face_region_quad(int axis, int side, int r, int& x0, int& y, int& z) {
+  constexpr int G = kGhosts, N = NB + 2 * G, R = N / 4;
+  const int lo = side < 0 ? 0 : G + NB;
+  if (axis == 0) {
+    x0 = lo; y = G + 2 * (r % (NB / 2)); z = G + 2 * (r / (NB / 2));
+  } else if (axis == 1) {
+    x0 = 4 * (r % R); y = lo + 2 * ((r / R) % (G / 2)); z = G + 2 * (r / (R * (G / 2)));
+  } else {
+    x0 = 4 * (r % R); y = 2 * ((r / R) % (N / 2)); z = lo + 2 * (r / (R * (N / 2)));
+  }
+}
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// One quad of a slow face: all 16 cells lie in one neighbour direction.
+// Coarser neighbour: each of the two parents along x is prolonged once for
+// its eight children (the per-run path would take its slopes four times);
+// finer neighbour: each coarse ghost cell restricts its eight children with
+// vector loads of the children's rows.  Outflow clamps and same-level
+// diagonal sources take the per-run path.  The arithmetic of every value is
+// that of ghost_value (same operations, same order).
+template <typename T, int NB, int NF>
+__device__ void refresh_slow_quad(const DevMesh& m, T* U, int leaf, int x0, int y, int z) {
+  constexpr int G = kGhosts, N = NB + 2 * G, H = NB / 2;
+  constexpr long SLAB = (long)N * N * N;
+  const int c[3] = {x0, y, z};
+  int d[3];
+  bool clamp = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    d[a] = c[a] < G ? -1 : (c[a] >= G + NB ? 1 : 0);
+    if (d[a] != 0 && m.kind[leaf * 27 + face_dir(a, d[a])] == kBoundary) clamp = true;
+  }
+  const int e = leaf * 27 + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
+  const int8_t k = m.kind[e];
+  if (clamp || k == kSame) {
+    for (int j = 0; j < 4; ++j) refresh_slow_run<T, NB, NF>(m, U, leaf, x0, y + (j & 1), z + (j >> 1));
+    return;
+  }
+  T* const dst = U + (long)leaf * NF * SLAB;
+  if (k == kFine) {
+    for (int j = 0; j < 4; ++j) {
+      const int cy = y + (j & 1), cz = z + (j >> 1);
+      const int r[3] = {x0 - G - d[0] * NB, cy - G - d[1] * NB, cz - G - d[2] * NB};
+      const int o[3] = {r[0] / H, r[1] / H, r[2] / H};
+      const int child = m.fine8[e * 8 + o[2] * 4 + o[1] * 2 + o[0]];
+      const int f0 = 2 * r[0] - o[0] * NB + G, f1 = 2 * r[1] - o[1] * NB + G, f2 = 2 * r[2] - o[2] * NB + G;
+      const T* src = U + (long)child * NF * SLAB + ((long)f2 * N + f1) * N + f0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        // the children's rows (dz, dy) = (0,0), (0,1), (1,0), (1,1), eight cells each
+        T v[4][8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T* row = src + f * SLAB + (q >> 1) * (long)N * N + (q & 1) * N;
+          Vec4<T> lo4, hi4;
+          lo4.load(row);
+          hi4.load(row + 4);
+          store_lanes(lo4, v[q]);
+          store_lanes(hi4, v[q] + 4);
+        }
+        T out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          T a = v[0][2 * i];
+          a = a + v[0][2 * i + 1];
+          a = a + v[1][2 * i];
+          a = a + v[1][2 * i + 1];
+          a = a + v[2][2 * i];
+          a = a + v[2][2 * i + 1];
+          a = a + v[3][2 * i];
+          a = a + v[3][2 * i + 1];
+          out[i] = a * T(0.125);
+        }
+        Vec4<T> w;
+        load_lanes(w, out);
+        w.store(dst + f * SLAB + ((long)cz * N + cy) * N + x0);
+      }
+    }
+    return;
+  }
+  // coarser neighbour C: parents (x0, x0 + 1) and (x0 + 2, x0 + 3) along x;
+  // rows y, y + 1 and z, z + 1 are the lower and upper children in y and z
+  const int4 lf = m.leaf[leaf];
+  const int C = m.idx[e];
+  const int4 cl = m.leaf[C];
+  const int L = lf.x;
+  const int lij[3] = {lf.y, lf.z, lf.w}, cij[3] = {cl.y, cl.z, cl.w};
+  int rc[3];
+#pragma unroll
+  for (int a = 1; a < 3; ++a)
+    rc[a] = (wrap_mod(lij[a] * NB + (c[a] - G), (m.root[a] << L) * NB) >> 1) - cij[a] * NB;
+  const int ncx = (m.root[0] << L) * NB;
+  using V2 = typename Vec2<T>::type;
+  for (int h = 0; h < 2; ++h) {
+    rc[0] = (wrap_mod(lij[0] * NB + (x0 + 2 * h - G), ncx) >> 1) - cij[0] * NB;
+    T Uc[NF], D[3][NF];
+    load5<T, NB, NF>(U, C, rc[0] + G, rc[1] + G, rc[2] + G, Uc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T Um[NF], Up[NF];
+      int rm[3] = {rc[0], rc[1], rc[2]}, rp[3] = {rc[0], rc[1], rc[2]};
+      rm[a] -= 1;
+      rp[a] += 1;
+      if (rm[a] >= 0) load5<T, NB, NF>(U, C, rm[0] + G, rm[1] + G, rm[2] + G, Um);
+      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, -1, Uc, Um);
+      if (rp[a] < NB) load5<T, NB, NF>(U, C, rp[0] + G, rp[1] + G, rp[2] + G, Up);
+      else slope_neighbour<T, NB, NF>(m, U, C, rc, a, 1, Uc, Up);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) D[a][f] = minmod(Uc[f] - Um[f], Up[f] - Uc[f]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T sy = (j & 1) ? T(1) : T(-1), sz = (j >> 1) ? T(1) : T(-1);
+      T* row = dst + ((long)(z + (j >> 1)) * N + (y + (j & 1))) * N + x0 + 2 * h;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        V2 w;
+        w.x = Uc[f] + T(0.25) * ((T(-1) * D[0][f] + sy * D[1][f]) + sz * D[2][f]);
+        w.y = Uc[f] + T(0.25) * ((T(1) * D[0][f] + sy * D[1][f]) + sz * D[2][f]);
+        *reinterpret_cast<V2*>(row + f * SLAB) = w;
+      }
+    }
+  }
+}
+
+// The slow work, listed per mesh as faces (leaf * 6 + face, faces in the
+// order -x, +x, -y, +y, -z, +z) whose neighbour is not a same-level leaf: one
+// CTA per listed face, its threads over the quads of that face's phase region.
+template <typename T, int NB, int NF = 5>
+__global__ void __launch_bounds__(128) refresh_slow_kernel(DevMesh m, T* U, const int* faces, int nfaces) {
+  const int i = blockIdx.x;
+  if (i >= nfaces) return;
+  const int leaf = faces[i] / 6, face = faces[i] % 6;
+  const int axis = face >> 1, side = (face & 1) ? 1 : -1;
+  const int nq = face_region_quads<NB>(axis);
+  for (int r = threadIdx.x; r < nq; r += blockDim.x) {
+    int x0, y, z;
+    face_region_quad<NB>(axis, side, r, x0, y, z);
+    refresh_slow_quad<T, NB, NF>(m, U, leaf, x0, y, z);
+  }
 }
 
 // =====================================================================
@@ -1041,26 +1309,36 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
   const float* b = U + (long)leaf * NF * SLAB;
   float mn = INFINITY, hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
   int bad = 0;
-  for (int i = threadIdx.x; i < NB * NB * NB; i += blockDim.x) {
-    const int x = i % NB + G, y = (i / NB) % NB + G, z = i / (NB * NB) + G;
-    const long o = ((long)z * N + y) * N + x;
-    const float r0 = b[o], m1 = b[SLAB + o], m2 = b[2 * SLAB + o], m3 = b[3 * SLAB + o], E = b[4 * SLAB + o];
-    const float rho = vmax(r0, float(kRhoFloor));
-    const float u = m1 / rho, vv = m2 / rho, w = m3 / rho;
-    const float ke = (0.5f * rho) * (u * u + (vv * vv + w * w));
-    float src = E - ke;
-    if constexpr (NF == 6) src = (src > float(kDualEta1) * E) ? src : b[5 * SLAB + o];
-    const float praw = gm1 * src;
-    bad |= !(r0 > 0.0f) || !(praw > 0.0f) || !isfinite(praw + (m1 + m2 + m3));
-    const float p = vmax(praw, float(kPFloor));
-    const float c = sqrtf((gamma * p) / rho);
-    const float s = vmax(fabsf(u), vmax(fabsf(vv), fabsf(w))) + c;
-    mn = fminf(mn, dx / s);
-    two_sum_acc(hi[0], lo[0], r0);
-    two_sum_acc(hi[1], lo[1], m1);
-    two_sum_acc(hi[2], lo[2], m2);
-    two_sum_acc(hi[3], lo[3], m3);
-    two_sum_acc(hi[4], lo[4], E);
+  // four cells along x per 16-byte load (interior rows start at x = G, a
+  // multiple of four cells)
+  constexpr int Q = NB / 4;
+  for (int i = threadIdx.x; i < NB * NB * Q; i += blockDim.x) {
+    const int qx = i % Q, row = i / Q;
+    const long o = ((long)(row / NB + G) * N + (row % NB + G)) * N + G + 4 * qx;
+    float4 v[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) v[f] = *reinterpret_cast<const float4*>(b + f * SLAB + o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float r0 = lane4(v[0], k), m1 = lane4(v[1], k), m2 = lane4(v[2], k), m3 = lane4(v[3], k),
+                  E = lane4(v[4], k);
+      const float rho = vmax(r0, float(kRhoFloor));
+      const float u = m1 / rho, vv = m2 / rho, w = m3 / rho;
+      const float ke = (0.5f * rho) * (u * u + (vv * vv + w * w));
+      float src = E - ke;
+      if constexpr (NF == 6) src = (src > float(kDualEta1) * E) ? src : lane4(v[NF - 1], k);
+      const float praw = gm1 * src;
+      bad |= !(r0 > 0.0f) || !(praw > 0.0f) || !isfinite(praw + (m1 + m2 + m3));
+      const float p = vmax(praw, float(kPFloor));
+      const float c = sqrtf((gamma * p) / rho);
+      const float s = vmax(fabsf(u), vmax(fabsf(vv), fabsf(w))) + c;
+      mn = fminf(mn, dx / s);
+      two_sum_acc(hi[0], lo[0], r0);
+      two_sum_acc(hi[1], lo[1], m1);
+      two_sum_acc(hi[2], lo[2], m2);
+      two_sum_acc(hi[3], lo[3], m3);
+      two_sum_acc(hi[4], lo[4], E);
+    }
   }
   double v[6];
   v[0] = double(mn);

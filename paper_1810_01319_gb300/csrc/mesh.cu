@@ -29,6 +29,13 @@ cello_status fail(cello_status st, const std::string& msg) {
   return st;
 }
 
+// State pools and adjoints must start on a 256-byte boundary (the ABI's
+// convention): the kernels move whole 32-byte sectors and 16-byte vectors,
+// which a misaligned address would turn into a device fault.
+bool misaligned(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0; }
+#define CELLO_REQUIRE_ALIGNED(p) \
+  do { if (misaligned(p)) return fail(CELLO_EINVAL, #p " is not 256-byte aligned"); } while (0)
+
 #define CELLO_CUDA(call)                                                                  \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
@@ -153,7 +160,7 @@ struct cello_mesh {
   int* d_group_start = nullptr;
   double* d_reg = nullptr;
   double* d_partials = nullptr;
-  long long* d_slow = nullptr;     // ghost runs that are not same-level copies (leaf * runs + run)
+  int* d_slow = nullptr;           // faces the refresh computes (leaf * 6 + face): neighbour not same-level
   std::vector<int> slow_start;     // per-leaf offsets into d_slow, B + 1 entries
   int exec_mode = CELLO_EXEC_BATCHED;
   int sweep_variant[3] = {0, 0, 0};   // per sweep axis; chosen by cello_autotune or set by the caller
@@ -411,45 +418,16 @@ cello_status finish_build(cello_mesh* M) {
   CELLO_TRY(upload(&M->d_group_start, M->group_start));
   if (ns > 0) CELLO_CUDA(cudaMalloc((void**)&M->d_reg, (size_t)ns * nfields(d) * d.n * d.n * sizeof(double)));
   CELLO_CUDA(cudaMalloc((void**)&M->d_partials, (size_t)std::max(B, 1) * 6 * sizeof(double)));
-  // ghost runs the vector-copy refresh leaves to the per-cell kernel: only
-  // leaves with a neighbour that is not a same-level leaf can have any
+  // faces whose phase region the refresh computes instead of copying: those
+  // whose neighbour is not a same-level leaf (coarser, finer, boundary)
   {
-    const int NS = ghost_run_count(d.n);
-    std::vector<int> cand;
-    for (int b = 0; b < B; ++b) {
-      bool all_same = true;
-      for (int e = 0; e < 27 && all_same; ++e) all_same = M->kind[(size_t)b * 27 + e] == kSame;
-      if (!all_same) cand.push_back(b);
-    }
-    std::vector<long long> slow;
-    std::vector<int> count((size_t)B, 0);
-    if (!cand.empty()) {
-      const int chunk = 8192;
-      int* d_cand = nullptr;
-      unsigned char* d_cls = nullptr;
-      std::vector<unsigned char> cls((size_t)std::min<size_t>(chunk, cand.size()) * NS);
-      cudaError_t e = cudaMalloc((void**)&d_cand, cand.size() * sizeof(int));
-      if (e == cudaSuccess) e = cudaMemcpy(d_cand, cand.data(), cand.size() * sizeof(int), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMalloc((void**)&d_cls, cls.size());
-      for (size_t c0 = 0; c0 < cand.size() && e == cudaSuccess; c0 += chunk) {
-        const int nl = (int)std::min<size_t>(chunk, cand.size() - c0);
-        launch_classify_runs(dm, d_cand + c0, nl, d_cls, 0);
-        e = cudaMemcpy(cls.data(), d_cls, (size_t)nl * NS, cudaMemcpyDeviceToHost);
-        for (int l = 0; l < nl && e == cudaSuccess; ++l) {
-          const int b = cand[c0 + l];
-          for (int r = 0; r < NS; ++r)
-            if (cls[(size_t)l * NS + r]) {
-              slow.push_back((long long)b * NS + r);
-              count[b]++;
-            }
-        }
-      }
-      if (d_cand) cudaFree(d_cand);
-      if (d_cls) cudaFree(d_cls);
-      if (e != cudaSuccess) return fail(CELLO_ECUDA, cudaGetErrorString(e));
-    }
+    std::vector<int> slow;
     M->slow_start.assign((size_t)B + 1, 0);
-    for (int b = 0; b < B; ++b) M->slow_start[b + 1] = M->slow_start[b] + count[b];
+    for (int b = 0; b < B; ++b) {
+      for (int f = 0; f < 6; ++f)
+        if (M->kind[(size_t)b * 27 + face_dir(f >> 1, (f & 1) ? 1 : -1)] != kSame) slow.push_back(b * 6 + f);
+      M->slow_start[b + 1] = (int)slow.size();
+    }
     CELLO_TRY(upload(&M->d_slow, slow));
   }
   CELLO_CUDA(cudaMalloc((void**)&M->d_work, sizeof(unsigned)));
@@ -461,11 +439,12 @@ cello_status finish_build(cello_mesh* M) {
   return CELLO_OK;
 }
 
-void launch_refresh(const cello_mesh* M, const DevMesh& dm, void* U, int leaf0, int nleaf, cudaStream_t s) {
+void launch_refresh(const cello_mesh* M, const DevMesh& dm, void* U, int leaf0, int nleaf, cudaStream_t s,
+                    int phases = kRefreshAll) {
   const int s0 = M->slow_start[leaf0], s1 = M->slow_start[leaf0 + nleaf];
-  const long long* slow = M->d_slow ? M->d_slow + s0 : nullptr;
-  if (M->desc.precision == 4) launch_refresh_f32(dm, static_cast<float*>(U), leaf0, nleaf, slow, s1 - s0, s);
-  else launch_refresh_f64(dm, static_cast<double*>(U), leaf0, nleaf, slow, s1 - s0, s);
+  const int* slow = M->d_slow ? M->d_slow + s0 : nullptr;
+  if (M->desc.precision == 4) launch_refresh_f32(dm, static_cast<float*>(U), leaf0, nleaf, slow, s1 - s0, phases, s);
+  else launch_refresh_f64(dm, static_cast<double*>(U), leaf0, nleaf, slow, s1 - s0, phases, s);
 }
 
 // Transverse pencil ranges of a sweep along `axis`: a transverse axis already
@@ -488,8 +467,9 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
   const int B = M->B;
   const bool plain = M->exec_mode == CELLO_EXEC_PLAIN && !ev;
   if (ev) cudaEventRecord(ev[0], s);
-  if (plain)
-    for (int b = 0; b < B; ++b) launch_refresh(M, dm, U, b, 1, s);
+  if (plain)   // one launch per leaf and phase; each phase over every leaf before the next
+    for (int ph : {kRefreshSlow, kRefreshX, kRefreshY, kRefreshZ})
+      for (int b = 0; b < B; ++b) launch_refresh(M, dm, U, b, 1, s, ph);
   else
     launch_refresh(M, dm, U, 0, B, s);
   if (ev) cudaEventRecord(ev[1], s);
@@ -744,6 +724,7 @@ cello_status cello_refine_flags(cello_mesh* M, const void* U, int field, double 
                                 void* stream) {
   if (!M || !U || !flags) return fail(CELLO_EINVAL, "NULL argument");
   if (field != 0 && field != 4) return fail(CELLO_EINVAL, "field must be 0 (density) or 4 (pressure)");
+  CELLO_REQUIRE_ALIGNED(U);
   launch_flags(M->dev(), U, M->desc.precision, field, tau, tau_c, flags, (cudaStream_t)stream);
   CELLO_CUDA(cudaGetLastError());
   return CELLO_OK;
@@ -751,6 +732,7 @@ cello_status cello_refine_flags(cello_mesh* M, const void* U, int field, double 
 
 cello_status cello_ghost_refresh(cello_mesh* M, void* U, void* stream) {
   if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U);
   launch_refresh(M, M->dev(), U, 0, M->B, (cudaStream_t)stream);
   CELLO_CUDA(cudaGetLastError());
   return CELLO_OK;
@@ -758,6 +740,7 @@ cello_status cello_ghost_refresh(cello_mesh* M, void* U, void* stream) {
 
 cello_status cello_reduce(cello_mesh* M, const void* U, double cfl, double* dt_next, double* totals, void* stream) {
   if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U);
   launch_reduce(M->dev(), U, M->desc.precision, cfl, M->d_partials, dt_next, totals, (cudaStream_t)stream);
   CELLO_CUDA(cudaGetLastError());
   return CELLO_OK;
@@ -774,6 +757,7 @@ cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycl
                               double* totals, void* stream) {
   if (!M || !U || !dt) return fail(CELLO_EINVAL, "NULL argument");
   if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
+  CELLO_REQUIRE_ALIGNED(U);
   cudaStream_t s = (cudaStream_t)stream;
   if (M->exec_mode != CELLO_EXEC_GRAPH) {
     enqueue_step(M, U, dt, cycle, cfl, dt_next, totals, s);
@@ -807,6 +791,8 @@ cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycl
 cello_status cello_remap(const cello_mesh* old, const void* U_old, const cello_mesh* neu, void* U_new,
                          void* stream) {
   if (!old || !neu || !U_old || !U_new) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U_old);
+  CELLO_REQUIRE_ALIGNED(U_new);
   if (std::memcmp(&old->desc, &neu->desc, sizeof(cello_mesh_desc)) != 0)
     return fail(CELLO_EINVAL, "meshes built from different descriptions");
   std::unordered_map<unsigned long long, int> where;
@@ -862,6 +848,8 @@ cello_status cello_remap(const cello_mesh* old, const void* U_old, const cello_m
 cello_status cello_hydro_adjoint_step(cello_mesh* M, const void* Un, void* lam, const double* dt, int cycle,
                                       void* stream) {
   if (!M || !Un || !lam || !dt) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(Un);
+  CELLO_REQUIRE_ALIGNED(lam);
   if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
   if (M->desc.riemann != CELLO_RIEMANN_TWO_SHOCK || M->desc.steepening || M->desc.dual_energy)
     return fail(CELLO_EINVAL,
@@ -887,6 +875,7 @@ cello_status cello_set_sweep_variant(cello_mesh* M, int variant) {
 
 cello_status cello_autotune(cello_mesh* M, void* U, int* variants_out, float* ms_out, int ms_len, void* stream) {
   if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U);
   cudaStream_t s = (cudaStream_t)stream;
   const cello_mesh_desc& d = M->desc;
   const DevMesh dm = M->dev();
@@ -954,6 +943,7 @@ cello_status cello_autotune(cello_mesh* M, void* U, int* variants_out, float* ms
 cello_status cello_hydro_step_host(cello_mesh* M, void* U_host, void* U_dev, double dt_host, double* dt_dev,
                                    int cycle, double cfl, double* scratch_dev, double* out_host, void* stream) {
   if (!M || !U_host || !U_dev || !dt_dev || !scratch_dev || !out_host) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U_dev);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)M->B * nfields(M->desc) * M->N * M->N * M->N * (size_t)M->desc.precision;
   CELLO_CUDA(cudaMemcpyAsync(U_dev, U_host, bytes, cudaMemcpyHostToDevice, s));
@@ -976,6 +966,7 @@ cello_status cello_particles_push(cello_mesh* M, const void* U, double* pos, int
                                   const double* dt, void* stream) {
   if (!M || !U || !dt || (count > 0 && (!pos || !leaf)) || count < 0)
     return fail(CELLO_EINVAL, "NULL argument or negative count");
+  CELLO_REQUIRE_ALIGNED(U);
   launch_particles_push(M->dev(), M->d_keys, M->desc.lo, M->desc.hi, U, M->desc.precision, pos, leaf, (long)count, dt,
                         (cudaStream_t)stream);
   CELLO_CUDA(cudaGetLastError());
@@ -994,7 +985,7 @@ cello_status cello_poisson_solve(cello_mesh* M, const double* f, double* phi, in
   for (const int4& lf : M->leaves)
     if (lf.x != L) return fail(CELLO_EINVAL, "the Poisson solver needs a uniform mesh (every leaf at one level)");
   const long Mg = (long)d.root[0] * (1L << L) * d.n;
-  if (Mg > 1024) return fail(CELLO_EINVAL, "grid too large for the Poisson solver (M > 1024)");
+  if (Mg / d.n > 512) return fail(CELLO_EINVAL, "grid too large for the Poisson solver (more than 512 blocks per axis)");
   const double h = std::ldexp((d.hi[0] - d.lo[0]) / (d.root[0] * d.n), -L);
   CELLO_CUDA(poisson_solve(&M->poisson, M->dev(), (int)Mg, h, f, phi, cycles, inner, resid_host,
                            (cudaStream_t)stream));
@@ -1034,6 +1025,7 @@ cello_status cello_sweep_opcount(const cello_mesh* M, float* U_host, const int32
 cello_status cello_profile_step(cello_mesh* M, void* U, const double* dt, int cycle, double cfl, float* phase_ms,
                                 void* stream) {
   if (!M || !U || !dt || !phase_ms) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U);
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t ev[7];
   for (int i = 0; i < 7; ++i) CELLO_CUDA(cudaEventCreate(&ev[i]));

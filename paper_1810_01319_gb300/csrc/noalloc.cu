@@ -29,6 +29,8 @@ extern "C" cello_status cello_reduce_noalloc(cello_mesh* mesh, const void* U, do
                                              double* totals_dev, void* stream) {
   using namespace cello;
   if (!mesh || !U) return set_error(CELLO_EINVAL, "cello_reduce_noalloc: NULL argument");
+  if ((reinterpret_cast<uintptr_t>(U) & 255u) != 0)
+    return set_error(CELLO_EINVAL, "cello_reduce_noalloc: U is not 256-byte aligned");
   const DevMesh dm = mesh_dev(mesh);
   if (dm.B > kNoAllocMaxLeaves)
     return set_error(CELLO_EINVAL, "cello_reduce_noalloc: the mesh has more leaves than the fixed scratch holds "

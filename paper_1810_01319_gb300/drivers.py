@@ -9,6 +9,21 @@ import torch
 from . import Mesh
 
 
+def may_change(leaves, flags) -> bool:
+    """False when the flags cannot change the mesh: no leaf asks for
+    refinement and no parent has all eight children flagged for coarsening
+    (a coarsening needs the whole octet).  Then the rebuild can be skipped."""
+    if (flags > 0).any():
+        return True
+    c = (flags < 0) & (leaves[:, 0] > 0)
+    if not c.any():
+        return False
+    lv = leaves[c].astype(np.int64)
+    parents = np.stack([lv[:, 0] - 1, lv[:, 1] >> 1, lv[:, 2] >> 1, lv[:, 3] >> 1], axis=1)
+    _, counts = np.unique(parents, axis=0, return_counts=True)
+    return bool((counts == 8).any())
+
+
 def adapt(mesh: Mesh, U, field: int = 0, tau: float = 0.3, tau_c: float | None = None, allow_coarsen=True):
     """One adaptation (Sec. II.B, Refine with Prolong/Restrict): returns the
     (possibly new) mesh and state.  U's ghosts are refreshed in place."""
@@ -17,7 +32,7 @@ def adapt(mesh: Mesh, U, field: int = 0, tau: float = 0.3, tau_c: float | None =
     flags = mesh.refine_flags(U, field, tau, tau_c).cpu().numpy()
     if not allow_coarsen:
         flags = np.where(flags > 0, 1, 0).astype(np.int8)
-    if not flags.any():
+    if not may_change(mesh.leaves, flags):
         return mesh, U
     new = Mesh(mesh.desc, mesh, flags)
     if new.n_leaves == mesh.n_leaves and np.array_equal(new.leaves, mesh.leaves):

@@ -115,6 +115,63 @@ def test_gradient_against_finite_differences(root, n, steps, ndir):
     assert worst < 1e-4, worst
 
 
+def test_float32_gradient_against_finite_differences():
+    """The adjoint workload (4^3 roots of 32^3 cells = 128^3, 50 steps) on the
+    float32 path: the float32 adjoint's directional derivatives against
+    central differences of the float32 forward (frozen dt from the float32
+    CFL reduction), on 16 directions.
+
+    A step suited to float32: each direction is a smooth field (the same
+    k^-2 random-field recipe as the initial density, seeds 100-115, zero in
+    the ghosts, unit norm) and eps = 1e-4 sqrt(cells), so the perturbation
+    is ~1e-4 per cell (~1700 float32 ulp of the unit density, small next to
+    the field's 0.1 amplitude) and the loss is summed in float64.  Budget:
+    the float32 rounding noise of the forward enters (L+ - L-) at ~1e-5 of
+    the signal, the O(eps^2) truncation at ~1e-6, and the float32 adjoint's
+    own rounding (50 reverse steps) at ~1e-4; tolerance 2e-3 relative."""
+    root, n, steps, ndir = (4, 4, 4), 32, 50, 16
+    od, om = _periodic(root=root, n=n)
+    gm = H.gpu_mesh_from_flags(od, [], 4)
+    base = H.state(od, om.leaves, "grf", seed=0).to(torch.float32).cuda()
+    tgt0 = H.state(od, om.leaves, "grf", seed=1).to(torch.float32).cuda()
+    dts = []
+    U = base.clone().contiguous()
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for s in range(steps):
+        gm.reduce(U, 0.4, dt_next=dt)
+        dts.append(float(dt))
+        gm.hydro_step(U, dt, s)
+    from paper_1810_01319_gb300.autograd import rollout
+    g4 = 4
+    target = rollout(gm, tgt0.contiguous(), dts, 0, 10)[:, 0, g4:g4 + n, g4:g4 + n, g4:g4 + n].double()
+
+    def loss(rho0):
+        U0 = base.clone()
+        U0[:, 0] = rho0
+        Uf = rollout(gm, U0, dts, 0, 10)
+        return ((Uf[:, 0, g4:g4 + n, g4:g4 + n, g4:g4 + n].double() - target) ** 2).sum()
+
+    rho0 = base[:, 0].clone().requires_grad_(True)
+    (grad,) = torch.autograd.grad(loss(rho0), rho0)
+    cells = om.n_leaves * n ** 3
+    eps = 1e-4 * np.sqrt(cells)
+    worst = 0.0
+    for k in range(ndir):
+        d = H.state(od, om.leaves, "grf", seed=100 + k)[:, 0] - 1.0
+        d[:, :g4] = 0; d[:, -g4:] = 0; d[:, :, :g4] = 0; d[:, :, -g4:] = 0; d[:, :, :, :g4] = 0; d[:, :, :, -g4:] = 0
+        d = (d / d.norm()).cuda()
+        with torch.no_grad():
+            rp = rho0.detach() + (eps * d).float()
+            rm = rho0.detach() - (eps * d).float()
+            lp, lm = float(loss(rp)), float(loss(rm))
+        fd = (lp - lm) / (2 * eps)
+        # along the perturbation float32 actually applied (rp - rm)
+        an = float((grad.double() * (rp.double() - rm.double())).sum()) / (2 * eps)
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-30))
+    print(f"float32 adjoint vs central differences, 128^3 x 50 steps: worst relative error {worst:.2e}")
+    assert worst < 2e-3, worst
+
+
 def test_float32_adjoint_close_to_float64():
     od, om = _periodic(n=16)
     U0 = _moving_state(od, om, 9)

@@ -133,3 +133,30 @@ def test_build_refine_coarsen_balance():
     flags = [-1 if t[0] == 2 else 0 for t in m2.leaves]
     m5 = M.build(desc, m2, flags)
     assert m5.n_leaves == 8
+
+
+def test_adapt_skips_only_rebuilds_that_change_nothing():
+    """The adapt driver skips the octree rebuild when no flag asks for
+    refinement and no parent has all eight children flagged -1: on random
+    meshes and flag sets, whenever it would skip, the oracle's build from
+    those flags returns the same leaves."""
+    from paper_1810_01319_gb300.drivers import may_change
+    rng = np.random.default_rng(11)
+    d = M.Desc(root=(2, 2, 2), n=8, ghosts=4, max_level=3)
+    skipped = changed = 0
+    for trial in range(40):
+        mesh = M.root_mesh(d)
+        for _ in range(3):
+            mesh = M.build(d, mesh, rng.choice([0, 1], size=mesh.n_leaves, p=[0.7, 0.3]).astype(np.int8))
+        p = rng.uniform(0.3, 1.0)
+        flags = np.where(rng.random(mesh.n_leaves) < p, -1, 0).astype(np.int8)
+        if trial % 5 == 0:
+            flags[rng.integers(mesh.n_leaves)] = 1
+        new = M.build(d, mesh, flags)
+        same = np.array_equal(new.leaves, mesh.leaves)
+        if not may_change(mesh.leaves, flags):
+            skipped += 1
+            assert same
+        elif not same:
+            changed += 1
+    assert skipped > 5 and changed > 5

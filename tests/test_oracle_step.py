@@ -327,3 +327,25 @@ def test_steepening_keeps_uniform_states_and_mirror_symmetry():
     Bb = Bm.flip(0).flip(-1).clone()
     Bb[:, 1] = -Bb[:, 1]
     assert torch.equal(_interior(mesh, A), _interior(mesh, Bb))
+
+
+def test_refresh_plan_on_a_subset_of_leaves():
+    """A plan restricted to some destination leaves, compacted onto a pool of
+    just the leaves it reads, fills those leaves' ghosts exactly as the
+    full plan does (the sampled full-size GPU parity test relies on it)."""
+    d = M.Desc(root=(2, 2, 2), n=8, ghosts=4, max_level=2, gamma=5.0 / 3.0, hi=(1.0, 1.0, 1.0),
+               bc=(M.PERIODIC, M.OUTFLOW, M.PERIODIC))
+    rng = np.random.default_rng(4)
+    mesh = M.root_mesh(d)
+    for _ in range(2):
+        mesh = M.build(d, mesh, rng.choice([0, 1], size=mesh.n_leaves, p=[0.6, 0.4]).astype(np.int8))
+    U = _state(mesh, "blobs", count=6, seed=1)
+    full = H.ghost_refresh(U, mesh)
+    dest = sorted(set(int(b) for b in rng.choice(mesh.n_leaves, 6, replace=False)))
+    plan = H.RefreshPlan(mesh, dest=dest)
+    read = plan.leaves_read()
+    assert set(dest) <= set(read.tolist()) and len(read) < mesh.n_leaves
+    out = plan.compact(read).apply(U[torch.as_tensor(read)].clone())
+    for k, b in enumerate(read):
+        if b in dest:
+            assert torch.equal(out[k], full[b])
