@@ -282,14 +282,19 @@ def sedov_run(cfg, precision, log=print, max_wall=300.0):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t, steps, step_ms, cell_updates, max_leaves = 0.0, 0, 0.0, 0, mesh.n_leaves
     adapt_s = 0.0
+    tuned = None
     wall = time.time()
     while t < cfg["t_end"] - 1e-15 and time.time() - wall < max_wall:
         if steps % cfg["adapt_every"] == 0:
             ta = time.time()
-            mesh, U = adapt(mesh, U, 4, cfg["tau"])
+            new_mesh, U = adapt(mesh, U, 4, cfg["tau"])
+            if new_mesh is not mesh and tuned is not None:
+                new_mesh.set_sweep_variants(tuned)    # a rebuilt mesh keeps the tuned sweep variants
+            mesh = new_mesh
             torch.cuda.synchronize()
             adapt_s += time.time() - ta
-            mesh.autotune(U) if steps == 0 else None
+            if steps == 0:
+                tuned = mesh.autotune(U)[0]
             max_leaves = max(max_leaves, mesh.n_leaves)
         mesh.reduce(U, cfg["cfl"], dt_next=dt)
         d = float(dt)
@@ -319,10 +324,37 @@ def sedov_run(cfg, precision, log=print, max_wall=300.0):
     r = torch.sqrt((x[sl] - 0.5) ** 2 + (y[sl] - 0.5) ** 2 + (z[sl] - 0.5) ** 2)
     m = rho > 0.9 * rho.max()
     R = float((r[m] * rho[m]).sum() / rho[m].sum())
+    peak = float(rho.max())
+    del rho, r, x, y, z, m
+    # FP32 batched (graph) against FP64 plain (one launch per leaf and phase)
+    # on the final mesh and state: the metric's comparison on many uneven leaves
+    from paper_1810_01319_gb300 import EXEC_GRAPH, EXEC_PLAIN
+    rates = {}
+    leaves = mesh.leaves
+    for prec, mode, nsteps in ((4, EXEC_GRAPH, 6), (8, EXEC_PLAIN, 2)):
+        d2 = make_desc(root, n, lmax, (0, 0, 0), (1, 1, 1), (PERIODIC,) * 3, prec, cfg["gamma"])
+        m2 = Mesh(d2, leaves=leaves)
+        if prec == 4 and tuned is not None:
+            m2.set_sweep_variants(tuned)
+        m2.set_exec(mode)
+        U2 = U.to(m2.dtype).contiguous()
+        d = torch.zeros(1, dtype=torch.float64, device="cuda")
+        m2.reduce(U2, cfg["cfl"], dt_next=d)
+        m2.hydro_step(U2, d, steps, cfg["cfl"])
+        ev0.record()
+        for k in range(nsteps):
+            m2.hydro_step(U2, d, steps + 1 + k, cfg["cfl"])
+        ev1.record()
+        ev1.synchronize()
+        rates[prec] = m2.n_leaves * n ** 3 * nsteps / (ev0.elapsed_time(ev1) / 1e3)
+        del U2, m2
+        torch.cuda.empty_cache()
     return {"steps": steps, "t": t, "reached_t_end": t >= cfg["t_end"] - 1e-15, "leaves_final": mesh.n_leaves,
+            "final_mesh_fp32_batched": rates[4], "final_mesh_fp64_plain": rates[8],
+            "final_mesh_ratio": rates[4] / rates[8],
             "leaves_max": max_leaves, "cell_updates": cell_updates, "step_ms_total": step_ms,
             "adapt_s_total": adapt_s, "wall_s": wall, "value": cell_updates / (step_ms / 1e3),
-            "shock_radius": R, "peak_density": float(rho.max())}
+            "shock_radius": R, "peak_density": peak}
 
 
 # ------------------------------------------------------- end to end, host

@@ -332,6 +332,60 @@ cello_status cello_reduce_noalloc(cello_mesh* mesh, const void* U, double cfl, d
  * launch's milliseconds to *ms_out (nullable).  Blocks until done. */
 cello_status cello_fp32_ffma_rate(double* ffma_per_s, double* ms_out, void* stream);
 
+/* ---- Sharded step: one rank's share of a step over a leaf partition ----
+ * Sec. II.B: a Block is independent of the others once its ghost layer is
+ * filled; Sec. III places the Blocks of the array of octrees on many ranks.
+ * A rank holds the whole pool with valid interiors for its own contiguous
+ * range of leaves (Morton order) and runs, with its own cello_mesh (its own
+ * flux registers):
+ *   1. cello_halo_unpack of the interiors of the other ranks' leaves its
+ *      refresh reads (packed there by cello_halo_pack);
+ *   2. cello_hydro_step_part(part 0): the ghost refresh and the three
+ *      sweeps of its range (face fluxes of coarse-fine faces into the
+ *      registers);
+ *   3. cello_flux_unpack of the fine face fluxes other ranks computed for
+ *      its coarse-fine faces (cello_flux_pack there);
+ *   4. cello_hydro_step_part(part 1): the flux correction of its range's
+ *      coarse faces;
+ *   5. cello_reduce_part: the CFL minimum and the totals of its range; the
+ *      step's dt_next is cfl x the min over ranks, its totals the sums.
+ * Each rank's leaves then equal those of cello_hydro_step on the whole
+ * pool, bit for bit (the same kernels, the same arithmetic); the totals
+ * differ only by the order of the final sums.  Lists are host arrays,
+ * checked (CELLO_EINVAL on an index out of range or a face without a flux
+ * register) and copied to a device list the mesh keeps (grown when
+ * needed); calls on one mesh must use one stream. */
+
+/* Interiors of the leaves leaf_ids[0..count) (host int32) from U into the
+ * device buffer buf[count][fields][n^3] (x fastest; 32-byte aligned), or
+ * from buf into U. */
+cello_status cello_halo_pack(cello_mesh* mesh, const void* U, const int32_t* leaf_ids, int64_t count, void* buf,
+                             void* stream);
+cello_status cello_halo_unpack(cello_mesh* mesh, void* U, const int32_t* leaf_ids, int64_t count, const void* buf,
+                               void* stream);
+
+/* Float64 face fluxes kept for the flux correction: faces[k] = leaf * 6 +
+ * face (order -x, +x, -y, +y, -z, +z), each a face on a coarse-fine face
+ * (coarse or fine side), into buf[count][fields][n^2] (device) or from
+ * it into the mesh's registers. */
+cello_status cello_flux_pack(cello_mesh* mesh, const int32_t* faces, int64_t count, double* buf, void* stream);
+cello_status cello_flux_unpack(cello_mesh* mesh, const int32_t* faces, int64_t count, const double* buf,
+                               void* stream);
+
+/* Part of cello_hydro_step for the leaves [leaf0, leaf0 + nleaf): part 0
+ * refreshes the ghosts (of every leaf: those of leaves outside the range may
+ * read stale interiors and are never used) and runs the three sweeps of the
+ * range; part 1 applies the flux correction of the coarse faces of the
+ * range.  dt and cycle as in cello_hydro_step. */
+cello_status cello_hydro_step_part(cello_mesh* mesh, void* U, const double* dt_dev, int cycle, int64_t leaf0,
+                                   int64_t nleaf, int part, void* stream);
+
+/* The reduction of cello_reduce over [leaf0, leaf0 + nleaf) (nleaf > 0):
+ * out_dev[0] = min over the range's cells of dx / (max |u_d| + c) (the CFL
+ * step before the factor cfl), out_dev[1..5] = the five totals. */
+cello_status cello_reduce_part(cello_mesh* mesh, const void* U, int64_t leaf0, int64_t nleaf, double* out_dev,
+                               void* stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* cello_last_error(void);
 

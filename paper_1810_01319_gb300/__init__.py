@@ -253,6 +253,59 @@ class Mesh:
         _lib.check(_lib.lib().cello_check(self.handle, ctypes.byref(w)), "cello_check")
         return w.value
 
+    # ------------------------------------------------- sharded step, one rank
+    def halo_pack(self, U, leaf_ids, buf=None, stream=None):
+        """Interiors of the listed leaves into a flat device buffer
+        [k, fields, n^3] (allocated if not given); returns it."""
+        self._check_state(U)
+        ids = np.ascontiguousarray(np.asarray(leaf_ids, dtype=np.int32))
+        if buf is None:
+            buf = torch.empty(len(ids), self.nf, self.desc.n ** 3, dtype=U.dtype, device=U.device)
+        _lib.check(_lib.lib().cello_halo_pack(self.handle, _ptr(U), ids.ctypes.data_as(ctypes.c_void_p), len(ids),
+                                              _ptr(buf), _stream(stream)), "cello_halo_pack")
+        return buf
+
+    def halo_unpack(self, U, leaf_ids, buf, stream=None):
+        self._check_state(U)
+        ids = np.ascontiguousarray(np.asarray(leaf_ids, dtype=np.int32))
+        if not (buf.is_cuda and buf.dtype == U.dtype and buf.is_contiguous()
+                and buf.numel() >= len(ids) * self.nf * self.desc.n ** 3):
+            raise CelloError("halo buffer must be a contiguous CUDA tensor of the state's dtype and size")
+        _lib.check(_lib.lib().cello_halo_unpack(self.handle, _ptr(U), ids.ctypes.data_as(ctypes.c_void_p), len(ids),
+                                                _ptr(buf), _stream(stream)), "cello_halo_unpack")
+
+    def flux_pack(self, faces, buf=None, device="cuda", stream=None):
+        """Float64 face fluxes of the listed faces (leaf * 6 + face) into a
+        flat device buffer [k, fields, n^2]; returns it."""
+        fc = np.ascontiguousarray(np.asarray(faces, dtype=np.int32))
+        if buf is None:
+            buf = torch.empty(len(fc), self.nf, self.desc.n ** 2, dtype=torch.float64, device=device)
+        _lib.check(_lib.lib().cello_flux_pack(self.handle, fc.ctypes.data_as(ctypes.c_void_p), len(fc), _ptr(buf),
+                                              _stream(stream)), "cello_flux_pack")
+        return buf
+
+    def flux_unpack(self, faces, buf, stream=None):
+        fc = np.ascontiguousarray(np.asarray(faces, dtype=np.int32))
+        if not (buf.is_cuda and buf.dtype == torch.float64 and buf.is_contiguous()
+                and buf.numel() >= len(fc) * self.nf * self.desc.n ** 2):
+            raise CelloError("flux buffer must be a contiguous float64 CUDA tensor of the listed size")
+        _lib.check(_lib.lib().cello_flux_unpack(self.handle, fc.ctypes.data_as(ctypes.c_void_p), len(fc), _ptr(buf),
+                                                _stream(stream)), "cello_flux_unpack")
+
+    def hydro_step_part(self, U, dt, cycle, leaf0, nleaf, part, stream=None):
+        self._check_state(U)
+        _lib.check(_lib.lib().cello_hydro_step_part(self.handle, _ptr(U), _ptr(dt), int(cycle), int(leaf0), int(nleaf),
+                                                    int(part), _stream(stream)), "cello_hydro_step_part")
+
+    def reduce_part(self, U, leaf0, nleaf, out=None, stream=None):
+        """[CFL minimum before the factor cfl, five totals] of the leaf range."""
+        self._check_state(U)
+        if out is None:
+            out = torch.empty(6, dtype=torch.float64, device=U.device)
+        _lib.check(_lib.lib().cello_reduce_part(self.handle, _ptr(U), int(leaf0), int(nleaf), _ptr(out),
+                                                _stream(stream)), "cello_reduce_part")
+        return out
+
     def set_sweep_variant(self, variant: int):
         _lib.check(_lib.lib().cello_set_sweep_variant(self.handle, int(variant)), "cello_set_sweep_variant")
 

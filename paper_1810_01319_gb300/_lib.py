@@ -54,6 +54,13 @@ SIGNATURES = {
     "cello_reduce": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_fp32_ffma_rate": (ctypes.c_int, [_vp, _vp, _vp]),
+    "cello_halo_pack": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "cello_halo_unpack": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "cello_flux_pack": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "cello_flux_unpack": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "cello_hydro_step_part": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int, _vp]),
+    "cello_reduce_part": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp]),
     "cello_set_exec": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cello_set_sweep_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "cello_set_sweep_variants": (ctypes.c_int, [_vp, _vp]),

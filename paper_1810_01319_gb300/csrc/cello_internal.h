@@ -162,6 +162,10 @@ void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace*
                      cudaStream_t s);
 void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
                    double* dt_next, double* totals, cudaStream_t s);
+// The same over leaves [leaf0, leaf0 + nleaf): partials of those leaves at
+// their own offsets, the min and the sums over the range only.
+void launch_reduce_range(const DevMesh& m, const void* U, int precision, double cfl, double* partials, int leaf0,
+                         int nleaf, double* dt_next, double* totals, cudaStream_t s);
 void launch_adjoint_sweep_f32(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStream_t s);
@@ -172,7 +176,8 @@ void launch_adjoint_refresh_scatter(const DevMesh& m, const void* U, void* lam, 
 void launch_fluxcorr_adjoint(const DevMesh& m, const void* lam, int precision, const CoarseFace* faces, int nfaces,
                              double* regb, const double* dt, cudaStream_t s);
 void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s);
-void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s);
+void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, int leaf0, int nleaf,
+                                cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);
 // Multigrid Poisson solver (poisson.cu) on the M^3 grid of a uniform periodic mesh.
@@ -186,6 +191,12 @@ void launch_particles_locate(const DevMesh& m, const unsigned long long* keys, c
 void launch_particles_push(const DevMesh& m, const unsigned long long* keys, const double lo[3], const double hi[3],
                            const void* U, int precision, double* pos, int* leaf, long count, const double* dt,
                            cudaStream_t s);
+// Sharded step (k_f64.cu): interiors of the listed leaves to (pack = 1) or
+// from (pack = 0) buf[count][nf][n^3]; float64 flux-register slots (per
+// doubles each) to or from buf[count][per].
+void launch_halo_copy(const DevMesh& m, void* U, int precision, const int* ids, long count, void* buf, int pack,
+                      cudaStream_t s);
+void launch_flux_copy(double* reg, const int* slots, long count, long per, double* buf, int pack, cudaStream_t s);
 // Host: counted operations of one leaf's sweep (opcount.cu), update applied.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
                   int riemann, int steepen, int dual, unsigned long long counts[6]);

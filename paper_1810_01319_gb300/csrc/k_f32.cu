@@ -148,19 +148,20 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
   }
 }
 
-void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, cudaStream_t s) {
+void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, int leaf0, int nleaf,
+                                cudaStream_t s) {
   if (m.nf == 6) {
     switch (m.n) {
-      case 8: reduce_partials_f32_kernel<8, 6><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
-      case 16: reduce_partials_f32_kernel<16, 6><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
-      case 32: reduce_partials_f32_kernel<32, 6><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+      case 8: reduce_partials_f32_kernel<8, 6><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
+      case 16: reduce_partials_f32_kernel<16, 6><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
+      case 32: reduce_partials_f32_kernel<32, 6><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
     }
     return;
   }
   switch (m.n) {
-    case 8: reduce_partials_f32_kernel<8><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
-    case 16: reduce_partials_f32_kernel<16><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
-    case 32: reduce_partials_f32_kernel<32><<<m.B, kReduceThreads, 0, s>>>(m, U, partials); break;
+    case 8: reduce_partials_f32_kernel<8><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
+    case 16: reduce_partials_f32_kernel<16><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
+    case 32: reduce_partials_f32_kernel<32><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
   }
 }
 

@@ -158,27 +158,34 @@ void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const
 }
 
 template <typename T, int NB>
-static void reduce_n(const DevMesh& m, const void* U, double* partials, cudaStream_t s) {
-  if (m.nf == 6) reduce_partials_kernel<T, NB, 6><<<m.B, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials);
-  else reduce_partials_kernel<T, NB><<<m.B, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials);
+static void reduce_n(const DevMesh& m, const void* U, double* partials, int leaf0, int nleaf, cudaStream_t s) {
+  if (m.nf == 6)
+    reduce_partials_kernel<T, NB, 6><<<nleaf, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials, leaf0);
+  else
+    reduce_partials_kernel<T, NB><<<nleaf, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials, leaf0);
 }
 
-void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
-                   double* dt_next, double* totals, cudaStream_t s) {
-  if (m.B <= 0) return;
-#define CELLO_RED(T)                                            \
-  switch (m.n) {                                                \
-    case 8: reduce_n<T, 8>(m, U, partials, s); break;           \
-    case 16: reduce_n<T, 16>(m, U, partials, s); break;         \
-    case 32: reduce_n<T, 32>(m, U, partials, s); break;         \
+void launch_reduce_range(const DevMesh& m, const void* U, int precision, double cfl, double* partials, int leaf0,
+                         int nleaf, double* dt_next, double* totals, cudaStream_t s) {
+  if (nleaf <= 0) return;
+#define CELLO_RED(T)                                                          \
+  switch (m.n) {                                                              \
+    case 8: reduce_n<T, 8>(m, U, partials, leaf0, nleaf, s); break;           \
+    case 16: reduce_n<T, 16>(m, U, partials, leaf0, nleaf, s); break;         \
+    case 32: reduce_n<T, 32>(m, U, partials, leaf0, nleaf, s); break;         \
   }
   if (precision == 4) {
-    launch_reduce_partials_f32(m, static_cast<const float*>(U), partials, s);
+    launch_reduce_partials_f32(m, static_cast<const float*>(U), partials, leaf0, nleaf, s);
   } else {
     CELLO_RED(double)
   }
 #undef CELLO_RED
-  reduce_finish_kernel<<<1, 1024, 0, s>>>(partials, m.B, cfl, dt_next, totals);
+  reduce_finish_kernel<<<1, 1024, 0, s>>>(partials + (long)leaf0 * 6, nleaf, cfl, dt_next, totals);
+}
+
+void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
+                   double* dt_next, double* totals, cudaStream_t s) {
+  launch_reduce_range(m, U, precision, cfl, partials, 0, m.B, dt_next, totals, s);
 }
 
 template <typename T, int NB>
@@ -317,6 +324,72 @@ void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace*
   if (precision == 4) { CELLO_FC_T(float) } else { CELLO_FC_T(double) }
 #undef CELLO_FC_T
 #undef CELLO_FC
+}
+
+}  // namespace cello
+
+// ---------------------------------------------------------------------------
+// Sharded step: leaf interiors and flux registers to and from flat buffers.
+namespace cello {
+namespace {
+
+// Leaf interiors <-> buf[count][nf][n^3] (x fastest), four cells per thread
+// (16-byte vectors: interior rows start at x = G, a multiple of four).
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) halo_copy_kernel(T* U, const int* ids, long count, int nf, T* buf, int pack) {
+  constexpr int G = kGhosts, N = NB + 2 * G, Q = NB / 4;
+  constexpr long SLAB = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= count * nf * NB * NB * Q) return;
+  const int q = (int)(gid % Q);
+  const int row = (int)((gid / Q) % (NB * NB));
+  const long kf = gid / ((long)Q * NB * NB);
+  const int f = (int)(kf % nf);
+  const long k = kf / nf;
+  T* u = U + ((long)ids[k] * nf + f) * SLAB + ((long)(row / NB + G) * N + (row % NB + G)) * N + G + 4 * q;
+  T* b = buf + (kf * NB * NB + row) * NB + 4 * q;
+  Vec4<T> v;
+  if (pack) {
+    v.load(u);
+    v.store(b);
+  } else {
+    v.load(b);
+    v.store(u);
+  }
+}
+
+__global__ void __launch_bounds__(256) flux_copy_kernel(double* reg, const int* slots, long count, long per,
+                                                        double* buf, int pack) {
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= count * per) return;
+  double* r = reg + (long)slots[gid / per] * per + gid % per;
+  if (pack) buf[gid] = *r;
+  else *r = buf[gid];
+}
+
+template <typename T>
+void halo_copy_t(const DevMesh& m, T* U, const int* ids, long count, T* buf, int pack, cudaStream_t s) {
+  const long threads = count * m.nf * (long)m.n * m.n * (m.n / 4);
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+  switch (m.n) {
+    case 8: halo_copy_kernel<T, 8><<<grid, 256, 0, s>>>(U, ids, count, m.nf, buf, pack); break;
+    case 16: halo_copy_kernel<T, 16><<<grid, 256, 0, s>>>(U, ids, count, m.nf, buf, pack); break;
+    case 32: halo_copy_kernel<T, 32><<<grid, 256, 0, s>>>(U, ids, count, m.nf, buf, pack); break;
+  }
+}
+
+}  // namespace
+
+void launch_halo_copy(const DevMesh& m, void* U, int precision, const int* ids, long count, void* buf, int pack,
+                      cudaStream_t s) {
+  if (count <= 0) return;
+  if (precision == 4) halo_copy_t<float>(m, static_cast<float*>(U), ids, count, static_cast<float*>(buf), pack, s);
+  else halo_copy_t<double>(m, static_cast<double*>(U), ids, count, static_cast<double*>(buf), pack, s);
+}
+
+void launch_flux_copy(double* reg, const int* slots, long count, long per, double* buf, int pack, cudaStream_t s) {
+  if (count <= 0) return;
+  flux_copy_kernel<<<(unsigned)((count * per + 255) / 256), 256, 0, s>>>(reg, slots, count, per, buf, pack);
 }
 
 }  // namespace cello

@@ -1245,11 +1245,12 @@ __device__ __forceinline__ void block_reduce6(double v[6], double* sh) {
 // NF = 6 (dual energy): the pressure for the sound speed and the health
 // check is selected as in the sweep's primitives, from E - ke or from rho e.
 template <typename T, int NB, int NF = 5>
-__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh m, const T* U, double* partials) {
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh m, const T* U, double* partials,
+                                                                         int leaf0) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   __shared__ double sh[6 * 32];
-  const int leaf = blockIdx.x;
+  const int leaf = leaf0 + blockIdx.x;
   const int4 lf = m.leaf[leaf];
   const T dx = T(ldexp(m.dx0, -lf.x));
   const T gamma = T(m.gamma), gm1 = T(m.gamma - 1.0);
@@ -1298,11 +1299,11 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 
 template <int NB, int NF = 5>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(DevMesh m, const float* U,
-                                                                             double* partials) {
+                                                                             double* partials, int leaf0) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   __shared__ double sh[6 * 32];
-  const int leaf = blockIdx.x;
+  const int leaf = leaf0 + blockIdx.x;
   const int4 lf = m.leaf[leaf];
   const float dx = float(ldexp(m.dx0, -lf.x));
   const float gamma = float(m.gamma), gm1 = float(m.gamma - 1.0);

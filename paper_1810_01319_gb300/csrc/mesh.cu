@@ -170,6 +170,8 @@ struct cello_mesh {
   double* d_zero = nullptr;        // dt = 0, for timing sweeps without changing the state
   void* adj_scratch = nullptr;   // three states for the adjoint's forward recomputation
   size_t adj_bytes = 0;
+  int* d_xlist = nullptr;        // index list of the last pack/unpack call (sharded step)
+  size_t xlist_cap = 0;
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
 
@@ -207,6 +209,9 @@ struct cello_mesh {
     capture_stream = nullptr;
     if (adj_scratch) cudaFree(adj_scratch);
     adj_scratch = nullptr;
+    if (d_xlist) cudaFree(d_xlist);
+    d_xlist = nullptr;
+    xlist_cap = 0;
     if (d_work) cudaFree(d_work);
     if (d_zero) cudaFree(d_zero);
     if (d_err) cudaFree(d_err);
@@ -460,19 +465,13 @@ void sweep_ranges(const cello_mesh* M, int axis, const bool swept[3], int& a0, i
 }
 
 // The launch sequence of one step on stream s.
-void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, double cfl, double* dt_next,
-                  double* totals, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+// The three split sweeps of leaves [leaf0, leaf0 + nleaf) (x, y, z on even
+// cycles, z, y, x on odd ones), face fluxes of coarse-fine faces into the
+// registers; plain: one launch per leaf and sweep; ev (nullable): events
+// after each sweep at ev[2 ..].
+void enqueue_sweeps(const cello_mesh* M, const DevMesh& dm, void* U, const double* dt, int cycle, int leaf0,
+                    int nleaf, bool plain, cudaStream_t s, cudaEvent_t* ev) {
   const cello_mesh_desc& d = M->desc;
-  const DevMesh dm = M->dev();
-  const int B = M->B;
-  const bool plain = M->exec_mode == CELLO_EXEC_PLAIN && !ev;
-  if (ev) cudaEventRecord(ev[0], s);
-  if (plain)   // one launch per leaf and phase; each phase over every leaf before the next
-    for (int ph : {kRefreshSlow, kRefreshX, kRefreshY, kRefreshZ})
-      for (int b = 0; b < B; ++b) launch_refresh(M, dm, U, b, 1, s, ph);
-  else
-    launch_refresh(M, dm, U, 0, B, s);
-  if (ev) cudaEventRecord(ev[1], s);
   const int order[3] = {cycle % 2 == 0 ? 0 : 2, 1, cycle % 2 == 0 ? 2 : 0};
   bool swept[3] = {false, false, false};
   for (int oi = 0; oi < 3; ++oi) {
@@ -487,21 +486,37 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
     p.work = M->d_work;
     p.variant = M->sweep_variant[axis];
     if (plain) {
-      for (int b = 0; b < B; ++b) {
+      for (int b = leaf0; b < leaf0 + nleaf; ++b) {
         p.leaf0 = b;
         p.nleaf = 1;
         if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
         else launch_sweep_f64(dm, p, pencils, s);
       }
-    } else {
-      p.leaf0 = 0;
-      p.nleaf = B;
+    } else if (nleaf > 0) {
+      p.leaf0 = leaf0;
+      p.nleaf = nleaf;
       if (d.precision == 4) launch_sweep_f32(dm, p, pencils, s);
       else launch_sweep_f64(dm, p, pencils, s);
     }
     swept[axis] = true;
     if (ev) cudaEventRecord(ev[2 + oi], s);
   }
+}
+
+void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, double cfl, double* dt_next,
+                  double* totals, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const cello_mesh_desc& d = M->desc;
+  const DevMesh dm = M->dev();
+  const int B = M->B;
+  const bool plain = M->exec_mode == CELLO_EXEC_PLAIN && !ev;
+  if (ev) cudaEventRecord(ev[0], s);
+  if (plain)   // one launch per leaf and phase; each phase over every leaf before the next
+    for (int ph : {kRefreshSlow, kRefreshX, kRefreshY, kRefreshZ})
+      for (int b = 0; b < B; ++b) launch_refresh(M, dm, U, b, 1, s, ph);
+  else
+    launch_refresh(M, dm, U, 0, B, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  enqueue_sweeps(M, dm, U, dt, cycle, 0, B, plain, s, ev);
   if (!M->cfaces.empty())
     launch_fluxcorr(dm, U, d.precision, M->d_cfaces, M->d_group_start, (int)M->group_start.size() - 1, M->d_reg,
                     dt, s);
@@ -742,6 +757,123 @@ cello_status cello_reduce(cello_mesh* M, const void* U, double cfl, double* dt_n
   if (!M || !U) return fail(CELLO_EINVAL, "NULL argument");
   CELLO_REQUIRE_ALIGNED(U);
   launch_reduce(M->dev(), U, M->desc.precision, cfl, M->d_partials, dt_next, totals, (cudaStream_t)stream);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+// ------------------------------------------------------------- sharded step
+namespace {
+
+// The host index list copied to the mesh's device list (grown when needed),
+// on the caller's stream.
+cello_status upload_list(cello_mesh* M, const std::vector<int>& h, cudaStream_t s) {
+  if (h.empty()) return CELLO_OK;
+  if (M->xlist_cap < h.size()) {
+    if (M->d_xlist) cudaFree(M->d_xlist);
+    M->d_xlist = nullptr;
+    M->xlist_cap = 0;
+    CELLO_CUDA(cudaMalloc((void**)&M->d_xlist, h.size() * sizeof(int)));
+    M->xlist_cap = h.size();
+  }
+  CELLO_CUDA(cudaMemcpyAsync(M->d_xlist, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  return CELLO_OK;
+}
+
+cello_status halo_copy(cello_mesh* M, void* U, const int32_t* leaf_ids, int64_t count, void* buf, int pack,
+                       void* stream) {
+  if (!M || count < 0 || (count > 0 && (!U || !leaf_ids || !buf))) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U);
+  if (reinterpret_cast<uintptr_t>(buf) & 31u) return fail(CELLO_EINVAL, "buffer is not 32-byte aligned");
+  std::vector<int> h((size_t)count);
+  for (int64_t k = 0; k < count; ++k) {
+    if (leaf_ids[k] < 0 || leaf_ids[k] >= M->B) return fail(CELLO_EINVAL, "leaf id out of range");
+    h[k] = leaf_ids[k];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CELLO_TRY(upload_list(M, h, s));
+  launch_halo_copy(M->dev(), U, M->desc.precision, M->d_xlist, (long)count, buf, pack, s);
+  CELLO_CUDA(cudaGetLastError());
+  // the list is read by the kernel: a later call must not overwrite it before
+  // the kernel has run, which the stream order guarantees for calls on one
+  // stream
+  return CELLO_OK;
+}
+
+cello_status flux_copy(cello_mesh* M, const int32_t* faces, int64_t count, double* buf, int pack, void* stream) {
+  if (!M || count < 0 || (count > 0 && (!faces || !buf))) return fail(CELLO_EINVAL, "NULL argument");
+  std::vector<int> h((size_t)count);
+  for (int64_t k = 0; k < count; ++k) {
+    if (faces[k] < 0 || faces[k] >= M->B * 6) return fail(CELLO_EINVAL, "face entry out of range");
+    const int slot = M->face_slot[(size_t)faces[k]];
+    if (slot < 0) return fail(CELLO_EINVAL, "a listed face is not on a coarse-fine face (no flux register)");
+    h[k] = slot;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CELLO_TRY(upload_list(M, h, s));
+  launch_flux_copy(M->d_reg, M->d_xlist, (long)count, (long)nfields(M->desc) * M->desc.n * M->desc.n, buf, pack, s);
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status check_range(const cello_mesh* M, int64_t leaf0, int64_t nleaf) {
+  if (leaf0 < 0 || nleaf < 0 || leaf0 + nleaf > M->B) return fail(CELLO_EINVAL, "leaf range outside the mesh");
+  return CELLO_OK;
+}
+
+}  // namespace
+
+cello_status cello_halo_pack(cello_mesh* M, const void* U, const int32_t* leaf_ids, int64_t count, void* buf,
+                             void* stream) {
+  return halo_copy(M, const_cast<void*>(U), leaf_ids, count, buf, 1, stream);
+}
+
+cello_status cello_halo_unpack(cello_mesh* M, void* U, const int32_t* leaf_ids, int64_t count, const void* buf,
+                               void* stream) {
+  return halo_copy(M, U, leaf_ids, count, const_cast<void*>(buf), 0, stream);
+}
+
+cello_status cello_flux_pack(cello_mesh* M, const int32_t* faces, int64_t count, double* buf, void* stream) {
+  return flux_copy(M, faces, count, buf, 1, stream);
+}
+
+cello_status cello_flux_unpack(cello_mesh* M, const int32_t* faces, int64_t count, const double* buf, void* stream) {
+  return flux_copy(M, faces, count, const_cast<double*>(buf), 0, stream);
+}
+
+cello_status cello_hydro_step_part(cello_mesh* M, void* U, const double* dt, int cycle, int64_t leaf0, int64_t nleaf,
+                                   int part, void* stream) {
+  if (!M || !U || !dt) return fail(CELLO_EINVAL, "NULL argument");
+  if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
+  if (part != 0 && part != 1) return fail(CELLO_EINVAL, "part must be 0 (refresh and sweeps) or 1 (flux correction)");
+  CELLO_REQUIRE_ALIGNED(U);
+  CELLO_TRY(check_range(M, leaf0, nleaf));
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevMesh dm = M->dev();
+  if (part == 0) {
+    launch_refresh(M, dm, U, 0, M->B, s);
+    enqueue_sweeps(M, dm, U, dt, cycle, (int)leaf0, (int)nleaf, false, s, nullptr);
+  } else if (!M->cfaces.empty()) {
+    // the groups (one per coarse leaf, in leaf order) whose leaf is in the range
+    const int ng = (int)M->group_start.size() - 1;
+    int g0 = 0, g1 = 0;
+    while (g0 < ng && M->cfaces[M->group_start[g0]].leaf < leaf0) ++g0;
+    g1 = g0;
+    while (g1 < ng && M->cfaces[M->group_start[g1]].leaf < leaf0 + nleaf) ++g1;
+    if (g1 > g0)
+      launch_fluxcorr(dm, U, M->desc.precision, M->d_cfaces, M->d_group_start + g0, g1 - g0, M->d_reg, dt, s);
+  }
+  CELLO_CUDA(cudaGetLastError());
+  return CELLO_OK;
+}
+
+cello_status cello_reduce_part(cello_mesh* M, const void* U, int64_t leaf0, int64_t nleaf, double* out_dev,
+                               void* stream) {
+  if (!M || !U || !out_dev) return fail(CELLO_EINVAL, "NULL argument");
+  CELLO_REQUIRE_ALIGNED(U);
+  CELLO_TRY(check_range(M, leaf0, nleaf));
+  if (nleaf == 0) return fail(CELLO_EINVAL, "empty leaf range");
+  launch_reduce_range(M->dev(), U, M->desc.precision, 1.0, M->d_partials, (int)leaf0, (int)nleaf, out_dev,
+                      out_dev + 1, (cudaStream_t)stream);
   CELLO_CUDA(cudaGetLastError());
   return CELLO_OK;
 }
