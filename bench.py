@@ -181,11 +181,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(cfg, seconds=15.0):
+def oracle_sample(cfg, seconds=15.0, single_core=False):
     """The FP64 oracle timed on a bounded sample of the same workload: a
     2^3-root-block periodic box of 32^3-cell blocks with the same blob
     density per volume, refined to level 2 on the same criterion, stepped
-    until about `seconds` of CPU time.  Returns (cell-updates/s, cores, text)."""
+    until about `seconds` of CPU time on all the host threads torch uses
+    (and, with single_core, one more step on one thread).  Returns
+    (cell-updates/s of the median step, threads, text, 1-thread rate or None)."""
     from oracle import hydro as OH
     from oracle import mesh as OM
     from workloads import ics
@@ -210,17 +212,32 @@ def oracle_sample(cfg, seconds=15.0):
     plan = OH.RefreshPlan(mesh)
     cf = OH.coarse_fine_faces(mesh)
     cells = mesh.n_leaves * od.n ** 3
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        dt = OH.reduce_dt_totals(U, mesh, cfg["cfl"])[0]
-        U = OH.step(U, mesh, dt, steps, plan, cf=cf)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or steps >= 50:
-            break
+
+    def timed_steps(U, budget, max_steps):
+        """Steps (each its own CFL reduction and step) until the time budget;
+        returns (U, per-step seconds)."""
+        per, t0 = [], time.perf_counter()
+        while True:
+            t1 = time.perf_counter()
+            dt = OH.reduce_dt_totals(U, mesh, cfg["cfl"])[0]
+            U = OH.step(U, mesh, dt, len(per), plan, cf=cf)
+            per.append(time.perf_counter() - t1)
+            if time.perf_counter() - t0 >= budget or len(per) >= max_steps:
+                return U, per
+    U, per = timed_steps(U, seconds, 50)
+    threads = torch.get_num_threads()
+    one_core = None
+    if single_core:
+        torch.set_num_threads(1)
+        try:
+            _, per1 = timed_steps(U, 0.0, 1)
+        finally:
+            torch.set_num_threads(threads)
+        one_core = cells / statistics.median(per1)
     text = (f"oracle (torch float64 CPU) on a {r}^3-root sub-box of 32^3 blocks, {count} blobs, "
-            f"{mesh.n_leaves} leaves to level {int(mesh.leaves[:, 0].max())}, {steps} steps")
-    return cells * steps / el, torch.get_num_threads(), text
+            f"{mesh.n_leaves} leaves to level {int(mesh.leaves[:, 0].max())}, {len(per)} steps on {threads} "
+            f"threads (rate from the median step)" + (", then 1 step on 1 thread" if single_core else ""))
+    return cells / statistics.median(per), threads, text, one_core
 
 
 # ------------------------------------------------------------ Sedov, deep
@@ -534,7 +551,7 @@ def main():
         for _ in range(args.warmup):
             oracle_sample(cfg, seconds=2.0)
         for _ in range(args.steps):
-            v, cores, text = oracle_sample(cfg, seconds=8.0)
+            v, cores, text, _ = oracle_sample(cfg, seconds=8.0)
             times.append(v)
         v = statistics.median(times)
         print(json.dumps({
@@ -584,10 +601,12 @@ def main():
     mesh.reduce(U, cfg["cfl"], dt_next=dt)
     stream = torch.cuda.current_stream()
 
+    # each step takes its dt from the CFL reduction of its own start state
+    # (cello_hydro_step_cfl: that reduction runs alongside the ghost refresh);
+    # the states are those of stepping with the previous step's dt_next
     cycle = 0
     for _ in range(args.warmup):
-        mesh.hydro_step(U, dt, cycle, cfg["cfl"], dt_next=dt_next, totals=totals)
-        dt.copy_(dt_next)
+        mesh.hydro_step_cfl(U, cycle, cfg["cfl"], dt, totals=totals)
         cycle += 1
     torch.cuda.synchronize()
     if world > 1:
@@ -597,8 +616,7 @@ def main():
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            mesh.hydro_step(U, dt, cycle, cfg["cfl"], dt_next=dt_next, totals=totals)
-            dt.copy_(dt_next)
+            mesh.hydro_step_cfl(U, cycle, cfg["cfl"], dt, totals=totals)
             cycle += 1
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -606,7 +624,9 @@ def main():
     value, ms = combine_ranks(ms, cells, args.steps)
     if world > 1:
         torch.distributed.barrier()
-    launches_per_step = 4 + 3 + (1 if mesh.n_coarse_fine else 0)
+    # kernels per step: reduction partials + finish, refresh phases X, Y, Z
+    # (+ the slow faces), three sweeps, flux correction (with coarse-fine faces)
+    launches_per_step = 2 + 3 + 3 + (2 if mesh.n_coarse_fine else 0)
 
     # algorithmic operations of the step's sweeps, counted by the library on a
     # sample of leaves (their slabs copied to the host, ghosts refreshed) and
@@ -792,15 +812,18 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, text = oracle_sample(cfg)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text}
+        v, cores, text, one = oracle_sample(cfg, single_core=True)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text,
+               "value_1_core": one, "host_cores_available": len(os.sched_getaffinity(0))}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(cfg, leaves=mesh.n_leaves, cells=cells, coarse_fine_faces=mesh.n_coarse_fine,
-                               sweep_variant=variant, sweep_variant_ms=variant_ms),
+                               sweep_variant=variant, sweep_variant_ms=variant_ms,
+                               step_call="cello_hydro_step_cfl (dt from the start state; its reduction alongside "
+                                         "the ghost refresh)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "tracers": tracers, "poisson": poisson,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
                 "hbm_frac_algorithmic": value * 40 / (hbm * 1e9)}

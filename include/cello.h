@@ -137,6 +137,19 @@ cello_status cello_neighbour_table(const cello_mesh* mesh, int8_t* kind_host, in
 cello_status cello_refine_flags(cello_mesh* mesh, const void* U, int field, double tau,
                                 double tau_coarsen, int8_t* flags_dev, void* stream);
 
+/* One hydro step whose dt is the CFL step of its own start state: dt_used
+ * (device, written) = cfl x min over leaf interior cells of dx / (max |u_d| +
+ * c) of U as given, totals (device, 5, nullable) the conserved totals of that
+ * start state; then the step of cello_hydro_step with that dt.  The
+ * reduction reads interiors only and the ghost refresh writes ghosts only, so
+ * the call runs them concurrently (a forked stream, captured into the graph
+ * in CELLO_EXEC_GRAPH mode); the sweeps wait for both.  A loop of these calls
+ * computes the same states as cello_hydro_step with dt taken from the
+ * previous call's dt_next (each step's dt is the CFL step of the state the
+ * previous step produced).  Errors as cello_hydro_step. */
+cello_status cello_hydro_step_cfl(cello_mesh* mesh, void* U, int cycle, double cfl, double* dt_used_dev,
+                                  double* totals_dev, void* stream);
+
 /* Remap field data onto a mesh rebuilt from `old` by one cello_octree_build
  * (Sec. II.B: Refine, with Prolong and Restrict moving data between levels).
  * U_old (old's pool, ghosts already refreshed) is read; the interior cells

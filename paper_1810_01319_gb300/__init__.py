@@ -145,6 +145,14 @@ class Mesh:
         _lib.check(_lib.lib().cello_hydro_step(self.handle, _ptr(U), _ptr(dt), int(cycle), float(cfl),
                                                _ptr(dt_next), _ptr(totals), _stream(stream)), "cello_hydro_step")
 
+    def hydro_step_cfl(self, U, cycle, cfl, dt_used, totals=None, stream=None):
+        """One step with dt = the CFL step of U as given (written to dt_used,
+        a float64 CUDA tensor of one element); totals (five) of that start
+        state.  The start-state reduction runs alongside the ghost refresh."""
+        self._check_state(U)
+        _lib.check(_lib.lib().cello_hydro_step_cfl(self.handle, _ptr(U), int(cycle), float(cfl), _ptr(dt_used),
+                                                   _ptr(totals), _stream(stream)), "cello_hydro_step_cfl")
+
     def hydro_adjoint_step(self, U_n, lam, dt, cycle, stream=None):
         """lam (adjoint of the state after the step) -> adjoint of U_n, in
         place; dt as in the forward step (held fixed)."""

@@ -51,6 +51,7 @@ SIGNATURES = {
     "cello_ghost_refresh": (ctypes.c_int, [_vp, _vp, _vp]),
     "cello_remap": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "cello_hydro_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
+    "cello_hydro_step_cfl": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_reduce_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "cello_fp32_ffma_rate": (ctypes.c_int, [_vp, _vp, _vp]),

@@ -101,6 +101,7 @@ void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStr
   }
 }
 
+
 void prepare_kernels_f64() {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -156,6 +157,7 @@ void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const
                         int phases, cudaStream_t s) {
   refresh_t<double>(m, U, leaf0, nleaf, slow, nslow, phases, s);
 }
+
 
 template <typename T, int NB>
 static void reduce_n(const DevMesh& m, const void* U, double* partials, int leaf0, int nleaf, cudaStream_t s) {

@@ -138,6 +138,7 @@ struct GraphEntry {
   double* dt_next;
   double* totals;
   cudaGraphExec_t exec;
+  bool cfl_step = false;   // a cello_hydro_step_cfl graph (dt from the start state)
 };
 
 struct cello_mesh {
@@ -174,6 +175,8 @@ struct cello_mesh {
   size_t xlist_cap = 0;
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
+  cudaStream_t side_stream = nullptr;          // the start-state reduction of cello_hydro_step_cfl
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
   DevMesh dev() const {
     DevMesh m;
@@ -207,6 +210,11 @@ struct cello_mesh {
     graphs.clear();
     if (capture_stream) cudaStreamDestroy(capture_stream);
     capture_stream = nullptr;
+    if (side_stream) cudaStreamDestroy(side_stream);
+    side_stream = nullptr;
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
+    fork_ev = join_ev = nullptr;
     if (adj_scratch) cudaFree(adj_scratch);
     adj_scratch = nullptr;
     if (d_xlist) cudaFree(d_xlist);
@@ -523,6 +531,25 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
   if (ev) cudaEventRecord(ev[5], s);
   if (dt_next || totals || ev) launch_reduce(dm, U, d.precision, cfl, M->d_partials, dt_next, totals, s);
   if (ev) cudaEventRecord(ev[6], s);
+}
+
+// One step whose dt is the CFL step of its start state: the reduction of the
+// start state (interiors only) on the side stream while the ghost refresh
+// (ghosts only) runs on s; the sweeps wait for both.
+void enqueue_step_cfl(const cello_mesh* M, void* U, int cycle, double cfl, double* dt_used, double* totals,
+                      cudaStream_t s) {
+  const cello_mesh_desc& d = M->desc;
+  const DevMesh dm = M->dev();
+  cudaEventRecord(M->fork_ev, s);
+  cudaStreamWaitEvent(M->side_stream, M->fork_ev, 0);
+  launch_reduce(dm, U, d.precision, cfl, M->d_partials, dt_used, totals, M->side_stream);
+  cudaEventRecord(M->join_ev, M->side_stream);
+  launch_refresh(M, dm, U, 0, M->B, s);
+  cudaStreamWaitEvent(s, M->join_ev, 0);
+  enqueue_sweeps(M, dm, U, dt_used, cycle, 0, M->B, false, s, nullptr);
+  if (!M->cfaces.empty())
+    launch_fluxcorr(dm, U, d.precision, M->d_cfaces, M->d_group_start, (int)M->group_start.size() - 1, M->d_reg,
+                    dt_used, s);
 }
 
 cello_status adjoint_step(cello_mesh* M, const void* Un, void* lam, const double* dt, int cycle, cudaStream_t s) {
@@ -898,7 +925,8 @@ cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycl
   }
   const int parity = cycle % 2;
   for (const GraphEntry& g : M->graphs)
-    if (g.U == U && g.dt == dt && g.parity == parity && g.cfl == cfl && g.dt_next == dt_next && g.totals == totals) {
+    if (!g.cfl_step && g.U == U && g.dt == dt && g.parity == parity && g.cfl == cfl && g.dt_next == dt_next &&
+        g.totals == totals) {
       CELLO_CUDA(cudaGraphLaunch(g.exec, s));
       return CELLO_OK;
     }
@@ -916,6 +944,46 @@ cello_status cello_hydro_step(cello_mesh* M, void* U, const double* dt, int cycl
     M->graphs.erase(M->graphs.begin());
   }
   M->graphs.push_back(GraphEntry{U, dt, parity, cfl, dt_next, totals, exec});
+  CELLO_CUDA(cudaGraphLaunch(exec, s));
+  return CELLO_OK;
+}
+
+cello_status cello_hydro_step_cfl(cello_mesh* M, void* U, int cycle, double cfl, double* dt_used, double* totals,
+                                  void* stream) {
+  if (!M || !U || !dt_used) return fail(CELLO_EINVAL, "NULL argument");
+  if (cycle < 0) return fail(CELLO_EINVAL, "cycle must be >= 0");
+  CELLO_REQUIRE_ALIGNED(U);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!M->side_stream) CELLO_CUDA(cudaStreamCreateWithFlags(&M->side_stream, cudaStreamNonBlocking));
+  if (!M->fork_ev) CELLO_CUDA(cudaEventCreateWithFlags(&M->fork_ev, cudaEventDisableTiming));
+  if (!M->join_ev) CELLO_CUDA(cudaEventCreateWithFlags(&M->join_ev, cudaEventDisableTiming));
+  if (M->exec_mode != CELLO_EXEC_GRAPH) {
+    enqueue_step_cfl(M, U, cycle, cfl, dt_used, totals, s);
+    CELLO_CUDA(cudaGetLastError());
+    return CELLO_OK;
+  }
+  const int parity = cycle % 2;
+  for (const GraphEntry& g : M->graphs)
+    if (g.cfl_step && g.U == U && g.dt == dt_used && g.parity == parity && g.cfl == cfl && g.totals == totals) {
+      CELLO_CUDA(cudaGraphLaunch(g.exec, s));
+      return CELLO_OK;
+    }
+  if (!M->capture_stream) CELLO_CUDA(cudaStreamCreateWithFlags(&M->capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  CELLO_CUDA(cudaStreamBeginCapture(M->capture_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_step_cfl(M, U, parity, cfl, dt_used, totals, M->capture_stream);
+  CELLO_CUDA(cudaStreamEndCapture(M->capture_stream, &graph));
+  cudaGraphExec_t exec;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CELLO_CUDA(e);
+  if (M->graphs.size() >= 8) {
+    cudaGraphExecDestroy(M->graphs.front().exec);
+    M->graphs.erase(M->graphs.begin());
+  }
+  GraphEntry ge{U, dt_used, parity, cfl, nullptr, totals, exec};
+  ge.cfl_step = true;
+  M->graphs.push_back(ge);
   CELLO_CUDA(cudaGraphLaunch(exec, s));
   return CELLO_OK;
 }

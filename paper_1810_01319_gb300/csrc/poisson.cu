@@ -195,11 +195,16 @@ __device__ __forceinline__ long bidx(int b, int x, int y, int z, int P) {
   return (((long)b * P + z) * P + y) * P + x;
 }
 
-// Interior cell number c of a block (x fastest) -> padded coordinates.
-__device__ __forceinline__ void interior_cell(long c, int n, int& x, int& y, int& z) {
-  x = (int)(c % n) + 1;
-  y = (int)((c / n) % n) + 1;
-  z = (int)(c / ((long)n * n)) + 1;
+// Block edges are powers of two (n, n/2, ..., 4): global cell gid of a
+// level -> block b and padded coordinates of its interior cell (x fastest),
+// by shifts and masks.
+__device__ __forceinline__ int blk_cell(long gid, int n, int& x, int& y, int& z) {
+  const int ln = __ffs(n) - 1;
+  const int c = (int)(gid & (((long)1 << (3 * ln)) - 1));
+  x = (c & (n - 1)) + 1;
+  y = ((c >> ln) & (n - 1)) + 1;
+  z = (c >> (2 * ln)) + 1;
+  return (int)(gid >> (3 * ln));
 }
 
 // Ghost layer of every block: each ghost cell takes the interior cell of the
@@ -254,9 +259,8 @@ __global__ void blk_jacobi_kernel(const T* __restrict__ in, T* __restrict__ out,
   const long n3 = (long)n * n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * n3) return;
-  const int b = (int)(gid / n3);
   int x, y, z;
-  interior_cell(gid - (long)b * n3, n, x, y, z);
+  const int b = blk_cell(gid, n, x, y, z);
   const int P = n + 2;
   const long i = bidx(b, x, y, z, P);
   out[i] = T(1.0 - kOmega) * in[i] + T(kOmega) * ((bnbsum(in, i, P) - h2 * f[i]) * T(1.0 / 6.0));
@@ -273,9 +277,8 @@ __global__ void blk_residual_restrict_kernel(DevMesh m, const T* __restrict__ ph
   const long nc3 = (long)nc * nc * nc;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * nc3) return;
-  const int b = (int)(gid / nc3);
   int X, Y, Z;
-  interior_cell(gid - (long)b * nc3, nc, X, Y, Z);   // padded: 1 .. nc
+  const int b = blk_cell(gid, nc, X, Y, Z);   // padded: 1 .. nc
   T s = T(0);
   bool first = true;
   for (int dz = 0; dz < 2; ++dz)
@@ -303,9 +306,8 @@ __global__ void blk_prolong_add_kernel(DevMesh m, const T* __restrict__ ec, cons
   const long n3 = (long)n * n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * n3) return;
-  const int b = (int)(gid / n3);
   int x, y, z;
-  interior_cell(gid - (long)b * n3, n, x, y, z);
+  const int b = blk_cell(gid, n, x, y, z);
   const int P = n + 2, nc = n / 2, Pc = nc + 2;
   // interior offsets 0 .. n-1; the parent and the nearer coarse neighbour
   const int ix = x - 1, iy = y - 1, iz = z - 1;
@@ -345,9 +347,8 @@ __global__ void blk_from_leaves_kernel(const double* __restrict__ src, double* _
   const long n3 = (long)n * n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * n3) return;
-  const int b = (int)(gid / n3);
   int x, y, z;
-  interior_cell(gid - (long)b * n3, n, x, y, z);
+  const int b = blk_cell(gid, n, x, y, z);
   dst[bidx(b, x, y, z, n + 2)] = src[gid] - *shift;
 }
 
@@ -355,9 +356,8 @@ __global__ void blk_to_leaves_kernel(const double* __restrict__ src, double* __r
   const long n3 = (long)n * n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * n3) return;
-  const int b = (int)(gid / n3);
   int x, y, z;
-  interior_cell(gid - (long)b * n3, n, x, y, z);
+  const int b = blk_cell(gid, n, x, y, z);
   dst[gid] = src[bidx(b, x, y, z, n + 2)];
 }
 
@@ -368,9 +368,8 @@ __global__ void blk_residual_f32_kernel(const double* __restrict__ phi, const do
   const long n3 = (long)n * n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * n3) return;
-  const int b = (int)(gid / n3);
   int x, y, z;
-  interior_cell(gid - (long)b * n3, n, x, y, z);
+  const int b = blk_cell(gid, n, x, y, z);
   const long i = bidx(b, x, y, z, n + 2);
   r[i] = (float)(f[i] - (bnbsum(phi, i, n + 2) - 6.0 * phi[i]) * ih2);
 }
@@ -379,9 +378,8 @@ __global__ void blk_correct_kernel(double* __restrict__ phi, const float* __rest
   const long n3 = (long)n * n * n;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long)B * n3) return;
-  const int b = (int)(gid / n3);
   int x, y, z;
-  interior_cell(gid - (long)b * n3, n, x, y, z);
+  const int b = blk_cell(gid, n, x, y, z);
   const long i = bidx(b, x, y, z, n + 2);
   phi[i] = phi[i] + (double)e[i];
 }
@@ -394,9 +392,8 @@ __global__ void blk_resmax_kernel(const double* __restrict__ phi, const double* 
   const long n3 = (long)n * n * n, count = (long)B * n3;
   double acc = 0.0;
   for (long gid = (long)blockIdx.x * blockDim.x + threadIdx.x; gid < count; gid += (long)gridDim.x * blockDim.x) {
-    const int b = (int)(gid / n3);
     int x, y, z;
-    interior_cell(gid - (long)b * n3, n, x, y, z);
+    const int b = blk_cell(gid, n, x, y, z);
     const long i = bidx(b, x, y, z, n + 2);
     const double r = fabs(f[i] - (bnbsum(phi, i, n + 2) - 6.0 * phi[i]) * ih2);
     acc = r > acc ? r : acc;

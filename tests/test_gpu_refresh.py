@@ -48,3 +48,21 @@ def test_refresh_fp32_close_to_oracle():
     gm.ghost_refresh(Ug)
     Uo = OH.ghost_refresh(U.double(), om)
     assert H.rel_err(Ug.cpu(), Uo) < 2e-6
+
+
+def test_misaligned_state_is_refused_before_any_launch():
+    """Every entry point that takes a state pool checks the header's 256-byte
+    alignment on the host (the kernels move 16- and 32-byte vectors): a pool
+    shifted by one element is refused with CELLO_EINVAL and left untouched."""
+    from paper_1810_01319_gb300 import CelloError
+    od = H.oracle_desc(root=(2, 2, 2), n=8, lmax=1)
+    gm = H.gpu_mesh_from_flags(od, [np.array([1, 0, 0, 0, 0, 0, 0, 0], dtype=np.int8)], 4)
+    raw = torch.zeros(gm.n_leaves * gm.leaf_elems + 1, dtype=torch.float32, device="cuda")
+    U = raw[1:].view(gm.n_leaves, gm.nf, gm.N, gm.N, gm.N)
+    dt = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    for call in (lambda: gm.ghost_refresh(U), lambda: gm.hydro_step(U, dt, 0), lambda: gm.reduce(U, 0.4, dt_next=dt),
+                 lambda: gm.refine_flags(U), lambda: gm.reduce_noalloc(U, 0.4, dt_next=dt)):
+        with pytest.raises(CelloError):
+            call()
+    torch.cuda.synchronize()
+    assert not raw.any()

@@ -222,3 +222,31 @@ def test_hydro_step_host_buffers_match_device_step(blob_amr):
         assert dn == float(dtn.item())
         assert th == [float(x) for x in tot.cpu()]
     assert torch.equal(host, Ud.cpu())
+
+
+@pytest.mark.parametrize("precision", [4, 8])
+def test_hydro_step_cfl_matches_the_dt_next_loop(blob_amr, precision):
+    """cello_hydro_step_cfl (dt from the start state, its reduction running
+    alongside the refresh) against the loop of cello_hydro_step fed with the
+    previous dt_next: the same states bit for bit in every exec mode, the
+    same dt sequence, and totals equal to cello_reduce of each start state."""
+    from paper_1810_01319_gb300 import EXEC_BATCHED, EXEC_GRAPH, EXEC_PLAIN
+    od, om, flags, U0, Uo, dts = blob_amr
+    gm = H.gpu_mesh_from_flags(od, flags, precision)
+    Ua, used_a, _ = _run_gpu(gm, U0, 4)
+    for mode in (EXEC_PLAIN, EXEC_BATCHED, EXEC_GRAPH):
+        gb = H.gpu_mesh_from_flags(od, flags, precision)
+        gb.set_exec(mode)
+        U = U0.to(gb.dtype).cuda().contiguous()
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tot = torch.zeros(5, dtype=torch.float64, device="cuda")
+        ref = torch.zeros(5, dtype=torch.float64, device="cuda")
+        used = []
+        for s in range(4):
+            gb.reduce(U, 0.4, totals=ref)
+            gb.hydro_step_cfl(U, s, 0.4, dt, totals=tot)
+            torch.cuda.synchronize()
+            used.append(float(dt))
+            assert torch.equal(tot, ref)
+        assert used == used_a
+        assert torch.equal(U.cpu(), Ua.cpu()), mode
