@@ -32,6 +32,7 @@ UNITS = {
     "mesh.cu": [],
     "noalloc.cu": [],
     "opcount.cu": [],
+    "peak.cu": [],
     "particles.cu": ["-fmad=false"],
     "poisson.cu": ["-fmad=false"],
 }
