@@ -707,6 +707,14 @@ def main():
                     "frac": achieved / hbm, "peak_source": src, "traffic": None,
                     "algorithmic_bytes_per_launch": alg_bytes[kname], "sweeps": sweeps,
                     "phase_ms": dict(zip(names, prof))}
+    # the memory-bound phases against the HBM roofline on their algorithmic
+    # bytes (the refresh: every ghost cell written once and its source read
+    # once; the reduction: the interior read once)
+    roofline["memory_phases"] = {
+        k: {"ms": prof[names.index(k)], "algorithmic_bytes": alg_bytes[k],
+            "achieved_gbs": alg_bytes[k] / (prof[names.index(k)] / 1e3) / 1e9,
+            "frac": alg_bytes[k] / (prof[names.index(k)] / 1e3) / 1e9 / hbm, "peak": hbm, "peak_source": src}
+        for k in ("ghost_refresh", "reduce")}
 
 
     # tracer particles (Sec. III's hydro workload carries tracers): one push of

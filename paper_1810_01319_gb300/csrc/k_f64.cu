@@ -121,8 +121,9 @@ static void refresh_nf(const DevMesh& m, T* U, int leaf0, int nleaf, const int* 
   auto blocks = [](long threads, int per) { return (unsigned)((threads + per - 1) / per); };
   if ((phases & kRefreshSlow) && nslow > 0) refresh_slow_kernel<T, NB, NF><<<nslow, 128, 0, s>>>(m, U, slow, nslow);
   if (nleaf <= 0) return;
-  if (phases & kRefreshX)
-    refresh_x_kernel<T, NB, NF><<<blocks((long)nleaf * NB * NB, 256), 256, 0, s>>>(m, U, leaf0, nleaf);
+  if (phases & kRefreshX)   // float32: one thread per row pair (see refresh_x_kernel)
+    refresh_x_kernel<T, NB, NF><<<blocks((long)nleaf * NB * (sizeof(T) == 4 ? NB / 2 : NB), 256), 256, 0, s>>>(
+        m, U, leaf0, nleaf);
   constexpr int S = Sector<T>::kCells;
   if (phases & kRefreshY)
     refresh_y_kernel<T, NB, NF><<<blocks((long)nleaf * 2 * NF * NB * (G * N / S), 256), 256, 0, s>>>(m, U, leaf0,

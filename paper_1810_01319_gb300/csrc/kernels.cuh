@@ -789,48 +789,76 @@ template <> struct Sector<double> {
 // boundary) has its phase region listed as slow work, computed from leaf
 // interiors.
 //
-// Phase X: one thread per (leaf A, interior row).  If A's -x face neighbour
-// B is a same-level leaf the thread fills both margins of that face: A's -x
-// margin from B's last four interior cells and B's +x margin from A's first
-// four.  Every access is one whole 32-byte sector: in float32 a 4-cell
-// margin is half of the sector it shares with the adjacent interior run, so
-// the thread loads A's first sector (ghost, interior) and B's last (interior,
-// ghost) and stores both back whole, each as (B's run, A's run); in float64 a
-// margin is a sector of its own.  A's +x margin is filled by the thread of
-// A's +x neighbour, or is slow work.
+// Phase X: the x margins of the interior rows, every access one whole
+// 32-byte sector.  A margin fills its sector only in float64; in float32 it is
+// half of the sector it shares with the adjacent interior run, and the two
+// halves of an exchange are written together: across the face between a
+// left leaf L and a right leaf R, the sectors L[row][NB, NB+8) and
+// R[row][0, 8) both become (L's last interior run, R's first interior run).
+//
+// float32: the last sector of row y and the first of row y+1 are one 64-byte
+// DRAM unit, so one thread per (leaf A, interior z, row pair y = G + 2k, y + 1)
+// owns that unit: it exchanges A's +x face at row y and A's -x face at row
+// y+1 (each with a same-level neighbour only), reading each partner's sector
+// once.  The +x face of the odd rows and the -x face of the even rows are the
+// threads of the neighbours.  float64: one thread per (leaf A, interior row)
+// exchanges A's -x face (A's +x face is its +x neighbour's thread).  Faces
+// whose neighbour is not a same-level leaf are slow work, done before.
 template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(256) refresh_x_kernel(DevMesh m, T* U, int leaf0, int nleaf) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long)nleaf * NB * NB) return;
-  const int A = leaf0 + (int)(gid / (NB * NB));
-  const int r = (int)(gid % (NB * NB));
-  const int e = A * 27 + face_dir(0, -1);
-  if (m.kind[e] != kSame) return;
-  const int Bn = m.idx[e];
-  const long row = ((long)(G + r / NB) * N + (G + r % NB)) * N;
-  T* a = U + (long)A * NF * SLAB + row;
-  T* b = U + (long)Bn * NF * SLAB + row;
   if constexpr (sizeof(T) == 4) {
-    Sector<T> sa[NF], sb[NF];
-#pragma unroll
+    constexpr int H = NB / 2;
+    if (gid >= (long)nleaf * NB * H) return;
+    const int A = leaf0 + (int)(gid / (NB * H));
+    const int r = (int)(gid % (NB * H));
+    const int y = G + 2 * (r % H), z = G + r / H;
+    const int ep = A * 27 + face_dir(0, 1), em = A * 27 + face_dir(0, -1);
+    const bool xp = m.kind[ep] == kSame, xm = m.kind[em] == kSame;
+    if (!xp && !xm) return;
+    const long row = ((long)z * N + y) * N;   // row y; row y + 1 starts at row + N
+    T* a = U + (long)A * NF * SLAB + row;
+    T* bp = xp ? U + (long)m.idx[ep] * NF * SLAB + row : nullptr;          // right neighbour, row y
+    T* bm = xm ? U + (long)m.idx[em] * NF * SLAB + row + N : nullptr;      // left neighbour, row y + 1
+#pragma unroll 1
     for (int f = 0; f < NF; ++f) {
-      sa[f].load(a + f * SLAB);        // A: cells 0..7 (ghost 0..3, interior 4..7)
-      sb[f].load(b + f * SLAB + NB);   // B: cells NB..NB+7 (interior NB..NB+3, ghost)
-    }
+      Sector<T> u0, u1, sp, sm;
+      u0.load(a + f * SLAB + NB);       // A[y][NB, NB+8): interior run, +x margin
+      u1.load(a + f * SLAB + N);        // A[y+1][0, 8): -x margin, interior run
+      if (xp) sp.load(bp + f * SLAB);   // R[y][0, 8)
+      if (xm) sm.load(bm + f * SLAB + NB);   // L[y+1][NB, NB+8)
+      if (xp) {
+        Sector<T> o;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      Sector<T> o;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        o.v[i] = sb[f].v[i];
-        o.v[4 + i] = sa[f].v[4 + i];
+        for (int i = 0; i < 4; ++i) {
+          o.v[i] = u0.v[i];
+          o.v[4 + i] = sp.v[4 + i];
+        }
+        o.store(a + f * SLAB + NB);
+        o.store(bp + f * SLAB);
       }
-      o.store(a + f * SLAB);
-      o.store(b + f * SLAB + NB);
+      if (xm) {
+        Sector<T> o;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          o.v[i] = sm.v[i];
+          o.v[4 + i] = u1.v[4 + i];
+        }
+        o.store(a + f * SLAB + N);
+        o.store(bm + f * SLAB + NB);
+      }
     }
   } else {
+    if (gid >= (long)nleaf * NB * NB) return;
+    const int A = leaf0 + (int)(gid / (NB * NB));
+    const int r = (int)(gid % (NB * NB));
+    const int e = A * 27 + face_dir(0, -1);
+    if (m.kind[e] != kSame) return;
+    const long row = ((long)(G + r / NB) * N + (G + r % NB)) * N;
+    T* a = U + (long)A * NF * SLAB + row;
+    T* b = U + (long)m.idx[e] * NF * SLAB + row;
     Sector<T> sa[NF], sb[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
