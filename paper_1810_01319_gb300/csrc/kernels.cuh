@@ -4,6 +4,7 @@
 
 #include "cello_internal.h"
 #include "ppm.cuh"
+#include "stream_x2.cuh"
 
 namespace cello {
 
@@ -60,6 +61,9 @@ sweep_kernel(DevMesh m, SweepParams prm) {
   constexpr long SLAB = (long)N * N * N;
   constexpr bool DE = (RS & 4) != 0;   // dual energy: a sixth field rho e
   constexpr int NQ = DE ? 6 : 5;
+  // float32 evaluates the per-field formulas as the streaming form does
+  // (stream_x2.cuh), so the two forms round alike
+  constexpr bool kPacked = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sW = reinterpret_cast<T*>(smem_raw);
   T* sA = sW + NQ * A;  // slopes, then left-edge states
@@ -119,8 +123,15 @@ sweep_kernel(DevMesh m, SweepParams prm) {
       T Us[NQ], W[NQ];
 #pragma unroll
       for (int k = 0; k < NQ; ++k) Us[k] = Uc[comp[k]];
-      if constexpr (DE) to_primitive_de(Us, gs, W);
-      else to_primitive(Us, gs, W);
+      if constexpr (kPacked) {
+        const px::Cell<NQ> Wc = px::primitives<NQ>(Us, gs);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) W[k] = Wc.get(k);
+      } else if constexpr (DE) {
+        to_primitive_de(Us, gs, W);
+      } else {
+        to_primitive(Us, gs, W);
+      }
 #pragma unroll
       for (int k = 0; k < NQ; ++k) sW[k * A + lc * S + lp] = W[k];
     }
@@ -132,7 +143,8 @@ sweep_kernel(DevMesh m, SweepParams prm) {
 #pragma unroll
       for (int k = 0; k < NQ; ++k) {
         const T* a = sW + k * A + p;
-        sA[k * A + j * S + p] = limited_slope(a[(j - 1) * S], a[j * S], a[(j + 1) * S]);
+        if constexpr (kPacked) sA[k * A + j * S + p] = px::slope(a[(j - 1) * S], a[j * S], a[(j + 1) * S]);
+        else sA[k * A + j * S + p] = limited_slope(a[(j - 1) * S], a[j * S], a[(j + 1) * S]);
       }
     }
     if (j >= 2 && j <= N - 3) {
@@ -145,15 +157,24 @@ sweep_kernel(DevMesh m, SweepParams prm) {
     // ---- phase 3 (interfaces j+1/2 read by cells 3..N-4)
     if (j >= 2 && j <= N - 4) {
 #pragma unroll
-      for (int k = 0; k < NQ; ++k)
-        sB[k * A + j * S + p] = interface_value(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
-                                                sA[k * A + j * S + p], sA[k * A + (j + 1) * S + p]);
+      for (int k = 0; k < NQ; ++k) {
+        if constexpr (kPacked)
+          sB[k * A + j * S + p] = px::interface_val(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
+                                                    sA[k * A + j * S + p], sA[k * A + (j + 1) * S + p]);
+        else
+          sB[k * A + j * S + p] = interface_value(sW[k * A + j * S + p], sW[k * A + (j + 1) * S + p],
+                                                  sA[k * A + j * S + p], sA[k * A + (j + 1) * S + p]);
+      }
     }
     if ((RS & 2) && j >= 3 && j <= N - 4) {   // contact steepening of cell j (density)
       const T* r = sW + p;
       const T* pr = sW + 4 * A + p;
-      sE[j * S + p] = steepening_eta(r[(j - 2) * S], r[(j - 1) * S], r[j * S], r[(j + 1) * S], r[(j + 2) * S],
-                                     pr[(j - 1) * S], pr[(j + 1) * S], gs.gamma);
+      if constexpr (kPacked)
+        sE[j * S + p] = px::steepening(r[(j - 2) * S], r[(j - 1) * S], r[j * S], r[(j + 1) * S], r[(j + 2) * S],
+                                       pr[(j - 1) * S], pr[(j + 1) * S], gs.gamma);
+      else
+        sE[j * S + p] = steepening_eta(r[(j - 2) * S], r[(j - 1) * S], r[j * S], r[(j + 1) * S], r[(j + 2) * S],
+                                       pr[(j - 1) * S], pr[(j + 1) * S], gs.gamma);
       sDL[j * S + p] = r[(j - 1) * S] + T(0.5) * sA[(j - 1) * S + p];
       sDR[j * S + p] = r[(j + 1) * S] - T(0.5) * sA[(j + 1) * S + p];
     }
@@ -172,12 +193,35 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         aR[k] = sB[k * A + j * S + p];
         if ((RS & 2) && k == 0) {
           const T e = sE[j * S + p];
-          aL[0] = aL[0] * (T(1) - e) + sDL[j * S + p] * e;
-          aR[0] = aR[0] * (T(1) - e) + sDR[j * S + p] * e;
+          if constexpr (kPacked) {
+            const float ome = px::sub(1.0f, e);
+            aL[0] = px::fma(aL[0], ome, px::mul(sDL[j * S + p], e));
+            aR[0] = px::fma(aR[0], ome, px::mul(sDR[j * S + p], e));
+          } else {
+            aL[0] = aL[0] * (T(1) - e) + sDL[j * S + p] * e;
+            aR[0] = aR[0] * (T(1) - e) + sDR[j * S + p] * e;
+          }
         }
-        flatten_monotone(W[k], f, aL[k], aR[k]);
+        if constexpr (kPacked) px::flatten_mono(W[k], f, px::sub(1.0f, f), aL[k], aR[k]);
+        else flatten_monotone(W[k], f, aL[k], aR[k]);
       }
-      trace<T, NQ>(W, aL, aR, dtdx, gs, Wm, Wp);
+      if constexpr (kPacked) {
+        px::Cell<NQ> Wc, aLc, aRc, Wmc, Wpc;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          Wc.set(k, W[k]);
+          aLc.set(k, aL[k]);
+          aRc.set(k, aR[k]);
+        }
+        px::trace_cell<NQ>(Wc, aLc, aRc, px::splat<float2>(dtdx), gs, Wmc, Wpc);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          Wm[k] = Wmc.get(k);
+          Wp[k] = Wpc.get(k);
+        }
+      } else {
+        trace<T, NQ>(W, aL, aR, dtdx, gs, Wm, Wp);
+      }
 #pragma unroll
       for (int k = 0; k < NQ; ++k) {
         sA[k * A + j * S + p] = Wm[k];
@@ -193,7 +237,19 @@ sweep_kernel(DevMesh m, SweepParams prm) {
         L[k] = sC[k * A + j * S + p];
         R[k] = sA[k * A + (j + 1) * S + p];
       }
-      if constexpr (DE) {
+      if constexpr (kPacked) {
+        px::Cell<NQ> Lc, Rc, Fc;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          Lc.set(k, L[k]);
+          Rc.set(k, R[k]);
+        }
+        float uf = 0.0f;
+        px::flux<NQ, RS>(Lc, Rc, gs, Fc, &uf);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) F[k] = Fc.get(k);
+        if constexpr (DE) sUF[j * S + p] = uf;
+      } else if constexpr (DE) {
         T uf;
         interface_flux6<RS>(L, R, gs, F, &uf);
         sUF[j * S + p] = uf;
@@ -227,12 +283,17 @@ sweep_kernel(DevMesh m, SweepParams prm) {
 #pragma unroll
       for (int k = 0; k < NQ; ++k) {
         const T Fp = sB[k * A + lc * S + lp], Fm = sB[k * A + (lc - 1) * S + lp];
-        Un[k] = Uc[comp[k]] - dtdx * sub_rn(Fp, Fm);
+        if constexpr (kPacked) Un[k] = px::fma(-dtdx, px::sub(Fp, Fm), Uc[comp[k]]);
+        else Un[k] = Uc[comp[k]] - dtdx * sub_rn(Fp, Fm);
       }
       if constexpr (DE) {
         const T pc = sW[4 * A + lc * S + lp];
-        Un[5] = Un[5] - (dtdx * pc) * sub_rn(sUF[lc * S + lp], sUF[(lc - 1) * S + lp]);
-        Un[5] = dual_sync(Un);
+        if constexpr (kPacked)
+          Un[5] = px::fma(-px::mul(dtdx, pc), px::sub(sUF[lc * S + lp], sUF[(lc - 1) * S + lp]), Un[5]);
+        else
+          Un[5] = Un[5] - (dtdx * pc) * sub_rn(sUF[lc * S + lp], sUF[(lc - 1) * S + lp]);
+        if constexpr (kPacked) Un[5] = px::dual_sync6(Un);
+        else Un[5] = dual_sync(Un);
       }
 #pragma unroll
       for (int k = 0; k < NQ; ++k) base[comp[k] * SLAB] = Un[k];
@@ -375,6 +436,107 @@ __device__ __forceinline__ void stream_step(PencilWindow<T, (RS & 4) ? 6 : 5>& S
   S.ft[0] = S.ft[1]; S.ft[1] = S.ft[2];
 }
 
+// Float32 form of stream_step: the same quantities at the same cells, the
+// fields of each in lane-pair groups (stream_x2.cuh).
+template <typename T, int NB, int RS, bool DEFER = false>
+__device__ __forceinline__ void stream_step(px::Window<(RS & 4) ? 6 : 5>& S, int k, const float* Us,
+                                            const float* old, float* base, long sAx, const int* comp, float dtdx,
+                                            const Gas<float>& gs, const DevMesh& m, const SweepParams& prm,
+                                            int leaf, int axis, bool face_row, int pa, int pb,
+                                            float* upd = nullptr) {
+  constexpr int G = kGhosts, N = NB + 2 * G;
+  constexpr long SLAB = (long)N * N * N;
+  constexpr int NQ = (RS & 4) ? 6 : 5;
+  using C = px::Cell<NQ>;
+  using CT = typename C::CT;
+  S.w[4] = px::primitives<NQ>(Us, gs);
+  if (k >= 3 && k <= N - 2)
+    S.dm[1] = px::each([](auto am, auto a0, auto ap) { return px::slope(am, a0, ap); }, S.w[2], S.w[3], S.w[4]);
+  if (k >= 4) {
+    S.ft[2] = flatten_tilde(S.w[0].a.y, S.w[1].a.y, S.w[3].a.y, S.w[4].a.y, S.w[1].a.x, S.w[3].a.x);
+    if (RS & 2)
+      S.eta[2] = px::steepening(px::lo(S.w[0].c), px::lo(S.w[1].c), px::lo(S.w[2].c), px::lo(S.w[3].c),
+                                px::lo(S.w[4].c), S.w[1].a.y, S.w[3].a.y, gs.gamma);
+    if (k <= N - 2)
+      S.ai[2] = px::each([](auto a0, auto a1, auto d0, auto d1) { return px::interface_val(a0, a1, d0, d1); },
+                         S.w[2], S.w[3], S.dm[0], S.dm[1]);
+  }
+  if (k >= 6) {
+    // cell j = k-3: W = w[1], aL = ai[0], aR = ai[1], shock detectors ft[0..2]
+    const float s = S.w[2].a.y - S.w[0].a.y;
+    const float f = (s > 0.0f) ? vmax(S.ft[1], S.ft[0]) : ((s < 0.0f) ? vmax(S.ft[1], S.ft[2]) : S.ft[1]);
+    C aL = S.ai[0], aR = S.ai[1];
+    if (RS & 2) {   // density of cell k-3: neighbours k-4 (slope dr[0]) and k-2 (slope dm[0])
+      const float e = S.eta[1], ome = px::sub(1.0f, e);
+      const float l0 = px::fma(px::lo(aL.c), ome, px::mul(px::fma(0.5f, S.dr[0], px::lo(S.w[0].c)), e));
+      const float r0 = px::fma(px::lo(aR.c), ome, px::mul(px::fma(-0.5f, px::lo(S.dm[0].c), px::lo(S.w[2].c)), e));
+      if constexpr (NQ == 6) { aL.c.x = l0; aR.c.x = r0; } else { aL.c = l0; aR.c = r0; }
+    }
+    const float2 f2 = px::splat<float2>(f), omf2 = px::splat<float2>(px::sub(1.0f, f));
+    px::flatten_mono(S.w[1].a, f2, omf2, aL.a, aR.a);
+    px::flatten_mono(S.w[1].b, f2, omf2, aL.b, aR.b);
+    px::flatten_mono(S.w[1].c, px::pick<CT>(f2), px::pick<CT>(omf2), aL.c, aR.c);
+    C Wm, Wp;
+    px::trace_cell<NQ>(S.w[1], aL, aR, px::splat<float2>(dtdx), gs, Wm, Wp);
+    if (k >= 7) {
+      // interface j = k-4 (+1/2): left state wp (cell k-4), right state Wm (cell k-3)
+      C Fc;
+      float uf = 0.0f;
+      px::flux<NQ, RS>(S.wp, Wm, gs, Fc, &uf);
+      const int j = k - 4;
+      if (face_row && (j == G - 1 || j == G + NB - 1)) {
+        const int face = 2 * axis + (j == G - 1 ? 0 : 1);
+        const int slot = m.face_slot[leaf * 6 + face];
+        if (slot >= 0) {
+          double* r = prm.reg + (long)slot * NQ * NB * NB + (pa - G) * NB + (pb - G);
+#pragma unroll
+          for (int c = 0; c < NQ; ++c) r[(long)comp[c] * NB * NB] = double(Fc.get(c));
+        }
+      }
+      if (k >= 8) {
+        // cell j = k-4 (window slot w[0]) between interfaces j-1/2 (fl) and j+1/2 (F)
+        C o;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) o.set(c, old[c]);
+        const float2 nd = px::splat<float2>(-dtdx);
+        C v;
+        v.a = px::fma(nd, px::sub(Fc.a, S.fl.a), o.a);
+        v.b = px::fma(nd, px::sub(Fc.b, S.fl.b), o.b);
+        v.c = px::fma(px::pick<CT>(nd), px::sub(Fc.c, S.fl.c), o.c);
+        if constexpr (NQ == 6) {
+          v.c.y = px::fma(-px::mul(dtdx, S.w[0].a.y), px::sub(uf, S.ufl), v.c.y);
+          float vv[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) vv[c] = v.get(c);
+          v.c.y = px::dual_sync6(vv);
+        }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+          if (DEFER) upd[c] = v.get(c);
+          else base[comp[c] * SLAB + (long)j * sAx] = v.get(c);
+        }
+      }
+      S.fl = Fc;
+      if constexpr (NQ == 6) S.ufl = uf;
+    }
+    S.wp = Wp;
+  }
+  // slide the windows
+  if (RS & 2) {
+    S.eta[0] = S.eta[1]; S.eta[1] = S.eta[2];
+    S.dr[0] = S.dr[1]; S.dr[1] = px::lo(S.dm[0].c);
+  }
+  S.w[0] = S.w[1]; S.w[1] = S.w[2]; S.w[2] = S.w[3]; S.w[3] = S.w[4];
+  S.dm[0] = S.dm[1];
+  S.ai[0] = S.ai[1]; S.ai[1] = S.ai[2];
+  S.ft[0] = S.ft[1]; S.ft[1] = S.ft[2];
+}
+
+// The window type of the streaming sweep: float32 keeps its fields in lane
+// pairs.
+template <typename T, int NQ> struct WindowOf { using type = PencilWindow<T, NQ>; };
+template <int NQ> struct WindowOf<float, NQ> { using type = px::Window<NQ>; };
+
 __device__ __forceinline__ float lane4(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
@@ -433,7 +595,7 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
       const int pa = prm.a0 + qa, pb = prm.b0 + q - qa * cB;
       T* base = U + (long)leaf * NQ * SLAB + pa * sTA + pb * sTB;
       const bool face_row = prm.reg && pa >= G && pa < G + NB && pb >= G && pb < G + NB;
-      PencilWindow<T, NQ> S;
+      typename WindowOf<T, NQ>::type S;
       T old[NQ];
       if (VEC == 3 && axis == 0) {
         // the groups of four cells are copied HBM -> shared memory by cp.async, one group
