@@ -626,7 +626,7 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           const float* cur = reinterpret_cast<const float*>(my + (g % 3) * NQ * CT);
           const float* prv = reinterpret_cast<const float*>(my + ((g + 2) % 3) * NQ * CT);
           float* out = reinterpret_cast<float*>(my + 3 * NQ * CT);
-#pragma unroll 1
+#pragma unroll 2
           for (int i = 0; i < 4; ++i) {
             T Us[NQ], up[NQ];
 #pragma unroll
@@ -687,24 +687,34 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           }
         }
       } else {
-        T nx[NQ];   // cell k+1, loaded one step ahead
+        // the one-cell walk, compiled once per axis so that the slab offsets of the fields
+        // and the stride along the pencil are constants of the address arithmetic
+        auto walk = [&](auto axis_tag) {
+          constexpr int AX = decltype(axis_tag)::value;
+          constexpr long sA = AX == 0 ? 1 : (AX == 1 ? N : (long)N * N);
+          constexpr int cmp[6] = {0, 1 + AX, AX == 0 ? 2 : 1, AX == 2 ? 2 : 3, 4, 5};
+          T nx[NQ];   // cell k+1, loaded one step ahead
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) nx[c] = base[comp[c] * SLAB];
+          for (int c = 0; c < NQ; ++c) nx[c] = base[cmp[c] * SLAB];
 #pragma unroll 1
-        for (int k = 0; k < N; ++k) {
-          T Us[NQ];
+          for (int k = 0; k < N; ++k) {
+            T Us[NQ];
 #pragma unroll
-          for (int c = 0; c < NQ; ++c) Us[c] = nx[c];
-          if (k + 1 < N) {
+            for (int c = 0; c < NQ; ++c) Us[c] = nx[c];
+            if (k + 1 < N) {
 #pragma unroll
-            for (int c = 0; c < NQ; ++c) nx[c] = base[comp[c] * SLAB + (k + 1) * sAx];
+              for (int c = 0; c < NQ; ++c) nx[c] = base[cmp[c] * SLAB + (k + 1) * sA];
+            }
+            if (k >= 8) {
+#pragma unroll
+              for (int c = 0; c < NQ; ++c) old[c] = base[cmp[c] * SLAB + (k - 4) * sA];
+            }
+            stream_step<T, NB, RS>(S, k, Us, old, base, sA, cmp, dtdx, gs, m, prm, leaf, AX, face_row, pa, pb);
           }
-          if (k >= 8) {
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) old[c] = base[comp[c] * SLAB + (k - 4) * sAx];
-          }
-          stream_step<T, NB, RS>(S, k, Us, old, base, sAx, comp, dtdx, gs, m, prm, leaf, axis, face_row, pa, pb);
-        }
+        };
+        if (axis == 0) walk(std::integral_constant<int, 0>());
+        else if (axis == 1) walk(std::integral_constant<int, 1>());
+        else walk(std::integral_constant<int, 2>());
       }
     }
     if (prm.work) {
