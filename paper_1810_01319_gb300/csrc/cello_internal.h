@@ -160,12 +160,14 @@ void prepare_kernels_de_f64();
 void launch_fluxcorr(const DevMesh& m, void* U, int precision, const CoarseFace* faces,
                      const int* group_start, int ngroups, const double* reg, const double* dt,
                      cudaStream_t s);
+// grid > 0: that many CTAs walk the leaves (a reduction that is to run
+// alongside other kernels); 0: one CTA per leaf.  The result is the same.
 void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
-                   double* dt_next, double* totals, cudaStream_t s);
+                   double* dt_next, double* totals, cudaStream_t s, int grid = 0);
 // The same over leaves [leaf0, leaf0 + nleaf): partials of those leaves at
 // their own offsets, the min and the sums over the range only.
 void launch_reduce_range(const DevMesh& m, const void* U, int precision, double cfl, double* partials, int leaf0,
-                         int nleaf, double* dt_next, double* totals, cudaStream_t s);
+                         int nleaf, double* dt_next, double* totals, cudaStream_t s, int grid = 0);
 void launch_adjoint_sweep_f32(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_sweep_f64(const DevMesh& m, const AdjSweepParams& p, cudaStream_t s);
 void launch_adjoint_refresh(const DevMesh& m, void* lam, int precision, cudaStream_t s);
@@ -176,7 +178,7 @@ void launch_adjoint_refresh_scatter(const DevMesh& m, const void* U, void* lam, 
 void launch_fluxcorr_adjoint(const DevMesh& m, const void* lam, int precision, const CoarseFace* faces, int nfaces,
                              double* regb, const double* dt, cudaStream_t s);
 void launch_zero_ghosts(const DevMesh& m, void* lam, int precision, cudaStream_t s);
-void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, int leaf0, int nleaf,
+void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, int leaf0, int nleaf, int grid,
                                 cudaStream_t s);
 void launch_flags(const DevMesh& m, const void* U, int precision, int field, double tau, double tau_c,
                   int8_t* flags, cudaStream_t s);

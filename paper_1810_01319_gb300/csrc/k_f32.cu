@@ -148,20 +148,21 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
   }
 }
 
-void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, int leaf0, int nleaf,
+void launch_reduce_partials_f32(const DevMesh& m, const float* U, double* partials, int leaf0, int nleaf, int grid,
                                 cudaStream_t s) {
+  const int g = (grid > 0 && grid < nleaf) ? grid : nleaf;
   if (m.nf == 6) {
     switch (m.n) {
-      case 8: reduce_partials_f32_kernel<8, 6><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
-      case 16: reduce_partials_f32_kernel<16, 6><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
-      case 32: reduce_partials_f32_kernel<32, 6><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
+      case 8: reduce_partials_f32_kernel<8, 6><<<g, kReduceThreads, 0, s>>>(m, U, partials, leaf0, nleaf); break;
+      case 16: reduce_partials_f32_kernel<16, 6><<<g, kReduceThreads, 0, s>>>(m, U, partials, leaf0, nleaf); break;
+      case 32: reduce_partials_f32_kernel<32, 6><<<g, kReduceThreads, 0, s>>>(m, U, partials, leaf0, nleaf); break;
     }
     return;
   }
   switch (m.n) {
-    case 8: reduce_partials_f32_kernel<8><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
-    case 16: reduce_partials_f32_kernel<16><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
-    case 32: reduce_partials_f32_kernel<32><<<nleaf, kReduceThreads, 0, s>>>(m, U, partials, leaf0); break;
+    case 8: reduce_partials_f32_kernel<8><<<g, kReduceThreads, 0, s>>>(m, U, partials, leaf0, nleaf); break;
+    case 16: reduce_partials_f32_kernel<16><<<g, kReduceThreads, 0, s>>>(m, U, partials, leaf0, nleaf); break;
+    case 32: reduce_partials_f32_kernel<32><<<g, kReduceThreads, 0, s>>>(m, U, partials, leaf0, nleaf); break;
   }
 }
 

@@ -161,24 +161,26 @@ void launch_refresh_f64(const DevMesh& m, double* U, int leaf0, int nleaf, const
 
 
 template <typename T, int NB>
-static void reduce_n(const DevMesh& m, const void* U, double* partials, int leaf0, int nleaf, cudaStream_t s) {
+static void reduce_n(const DevMesh& m, const void* U, double* partials, int leaf0, int nleaf, int g,
+                     cudaStream_t s) {
   if (m.nf == 6)
-    reduce_partials_kernel<T, NB, 6><<<nleaf, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials, leaf0);
+    reduce_partials_kernel<T, NB, 6><<<g, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials, leaf0, nleaf);
   else
-    reduce_partials_kernel<T, NB><<<nleaf, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials, leaf0);
+    reduce_partials_kernel<T, NB><<<g, kReduceThreads, 0, s>>>(m, static_cast<const T*>(U), partials, leaf0, nleaf);
 }
 
 void launch_reduce_range(const DevMesh& m, const void* U, int precision, double cfl, double* partials, int leaf0,
-                         int nleaf, double* dt_next, double* totals, cudaStream_t s) {
+                         int nleaf, double* dt_next, double* totals, cudaStream_t s, int grid) {
   if (nleaf <= 0) return;
+  const int g = (grid > 0 && grid < nleaf) ? grid : nleaf;
 #define CELLO_RED(T)                                                          \
   switch (m.n) {                                                              \
-    case 8: reduce_n<T, 8>(m, U, partials, leaf0, nleaf, s); break;           \
-    case 16: reduce_n<T, 16>(m, U, partials, leaf0, nleaf, s); break;         \
-    case 32: reduce_n<T, 32>(m, U, partials, leaf0, nleaf, s); break;         \
+    case 8: reduce_n<T, 8>(m, U, partials, leaf0, nleaf, g, s); break;        \
+    case 16: reduce_n<T, 16>(m, U, partials, leaf0, nleaf, g, s); break;      \
+    case 32: reduce_n<T, 32>(m, U, partials, leaf0, nleaf, g, s); break;      \
   }
   if (precision == 4) {
-    launch_reduce_partials_f32(m, static_cast<const float*>(U), partials, leaf0, nleaf, s);
+    launch_reduce_partials_f32(m, static_cast<const float*>(U), partials, leaf0, nleaf, g, s);
   } else {
     CELLO_RED(double)
   }
@@ -187,8 +189,8 @@ void launch_reduce_range(const DevMesh& m, const void* U, int precision, double 
 }
 
 void launch_reduce(const DevMesh& m, const void* U, int precision, double cfl, double* partials,
-                   double* dt_next, double* totals, cudaStream_t s) {
-  launch_reduce_range(m, U, precision, cfl, partials, 0, m.B, dt_next, totals, s);
+                   double* dt_next, double* totals, cudaStream_t s, int grid) {
+  launch_reduce_range(m, U, precision, cfl, partials, 0, m.B, dt_next, totals, s, grid);
 }
 
 template <typename T, int NB>

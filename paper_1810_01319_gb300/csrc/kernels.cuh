@@ -1412,8 +1412,9 @@ __global__ void __launch_bounds__(256) remap_kernel(DevMesh neu, DevMesh old, co
 }
 
 // =====================================================================
-// CFL dt candidates and conserved sums, one CTA per leaf (partials), then a
-// single-CTA fixed-order finish.  Deterministic for a fixed launch shape.
+// CFL dt candidates and conserved sums, one CTA per leaf at a time (grid-
+// stride over the leaves; a leaf's partials do not depend on the grid),
+// then a single-CTA fixed-order finish.  Deterministic.
 // =====================================================================
 constexpr int kReduceThreads = 256;
 
@@ -1446,11 +1447,12 @@ __device__ __forceinline__ void block_reduce6(double v[6], double* sh) {
 // check is selected as in the sweep's primitives, from E - ke or from rho e.
 template <typename T, int NB, int NF = 5>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh m, const T* U, double* partials,
-                                                                         int leaf0) {
+                                                                         int leaf0, int nleaf) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   __shared__ double sh[6 * 32];
-  const int leaf = leaf0 + blockIdx.x;
+  for (int lr = blockIdx.x; lr < nleaf; lr += gridDim.x) {
+  const int leaf = leaf0 + lr;
   const int4 lf = m.leaf[leaf];
   const T dx = T(ldexp(m.dx0, -lf.x));
   const T gamma = T(m.gamma), gm1 = T(m.gamma - 1.0);
@@ -1483,6 +1485,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(DevMesh
     for (int k = 1; k < 6; ++k) partials[leaf * 6 + k] = v[k] * vol;
     if (bad && m.err) atomicOr(m.err, 1u);
   }
+  __syncthreads();   // sh is rewritten by the next leaf
+  }
 }
 
 // Float32 state: per-thread sums carried as unevaluated float pairs (Knuth's
@@ -1499,11 +1503,12 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 
 template <int NB, int NF = 5>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(DevMesh m, const float* U,
-                                                                             double* partials, int leaf0) {
+                                                                             double* partials, int leaf0, int nleaf) {
   constexpr int G = kGhosts, N = NB + 2 * G;
   constexpr long SLAB = (long)N * N * N;
   __shared__ double sh[6 * 32];
-  const int leaf = leaf0 + blockIdx.x;
+  for (int lr = blockIdx.x; lr < nleaf; lr += gridDim.x) {
+  const int leaf = leaf0 + lr;
   const int4 lf = m.leaf[leaf];
   const float dx = float(ldexp(m.dx0, -lf.x));
   const float gamma = float(m.gamma), gm1 = float(m.gamma - 1.0);
@@ -1553,6 +1558,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partials_f32_kernel(Dev
     partials[leaf * 6 + 0] = v[0];
     for (int k = 1; k < 6; ++k) partials[leaf * 6 + k] = v[k] * vol;
     if (bad && m.err) atomicOr(m.err, 1u);
+  }
+  __syncthreads();   // sh is rewritten by the next leaf
   }
 }
 

@@ -536,13 +536,21 @@ void enqueue_step(const cello_mesh* M, void* U, const double* dt, int cycle, dou
 // One step whose dt is the CFL step of its start state: the reduction of the
 // start state (interiors only) on the side stream while the ghost refresh
 // (ghosts only) runs on s; the sweeps wait for both.
+constexpr int kSideReduceCtasPerSm = 2;
+
 void enqueue_step_cfl(const cello_mesh* M, void* U, int cycle, double cfl, double* dt_used, double* totals,
                       cudaStream_t s) {
   const cello_mesh_desc& d = M->desc;
   const DevMesh dm = M->dev();
   cudaEventRecord(M->fork_ev, s);
   cudaStreamWaitEvent(M->side_stream, M->fork_ev, 0);
-  launch_reduce(dm, U, d.precision, cfl, M->d_partials, dt_used, totals, M->side_stream);
+  // a few resident CTAs per SM walk the leaves, so that the reduction shares
+  // the SMs with the refresh's kernels (latency-bound, DRAM not saturated)
+  // instead of queueing behind them
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  launch_reduce(dm, U, d.precision, cfl, M->d_partials, dt_used, totals, M->side_stream, kSideReduceCtasPerSm * sms);
   cudaEventRecord(M->join_ev, M->side_stream);
   launch_refresh(M, dm, U, 0, M->B, s);
   cudaStreamWaitEvent(s, M->join_ev, 0);
