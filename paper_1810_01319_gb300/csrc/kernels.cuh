@@ -696,7 +696,7 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           T nx[NQ];   // cell k+1, loaded one step ahead
 #pragma unroll
           for (int c = 0; c < NQ; ++c) nx[c] = base[cmp[c] * SLAB];
-#pragma unroll 1
+#pragma unroll 2
           for (int k = 0; k < N; ++k) {
             T Us[NQ];
 #pragma unroll
