@@ -121,9 +121,11 @@ __device__ __forceinline__ V slope(V am, V a0, V ap) {
   const V dl = sub(a0, am), dr = sub(ap, a0);
   const V da = mul(splat<V>(0.5f), sub(ap, am));
   const V pr = mul(dl, dr);
-  const V mn = mul(splat<V>(2.0f), lanes([](float x, float y) { return vmin(fabsf(x), fabsf(y)); }, dl, dr));
-  return lanes([](float d, float m, float p) { return (p > 0.0f) ? copysignf(vmin(fabsf(d), m), d) : 0.0f; },
-               da, mn, pr);
+  (void)pr;
+  // with s = sign(da): s dl and s dr are both positive exactly where dl dr > 0
+  const V sg = lanes([](float d) { return copysignf(1.0f, d); }, da);
+  const V mn = mul(splat<V>(2.0f), lanes([](float x, float y) { return vmin(x, y); }, mul(sg, dl), mul(sg, dr)));
+  return mul(sg, lanes([](float d, float m) { return vmax(vmin(fabsf(d), m), 0.0f); }, da, mn));
 }
 
 // Interface value (a0 + a1)/2 - (dm1 - dm0)/6.
