@@ -89,7 +89,11 @@ enum { CELLO_RIEMANN_TWO_SHOCK = 0, CELLO_RIEMANN_HLLC = 1 };
  * periodic images) until none does.  Leaves are sorted by the Morton key of
  * their lower corner at max_level.  The 27-entry neighbour table is then
  * computed on the device.  *out receives a new mesh owned by the caller
- * (free with cello_mesh_free). */
+ * (free with cello_mesh_free).  The first mesh built on a device sets the
+ * calling process's L2 fetch-granularity hint for that device
+ * (cudaLimitMaxL2FetchGranularity) to 64 bytes: the ghost refresh reads
+ * 32-byte sectors of 160-byte rows.  The hint belongs to the process's
+ * context and ends with it. */
 cello_status cello_octree_build(const cello_mesh_desc* desc, const cello_mesh* prev,
                                 const int8_t* flags_host, cello_mesh** out);
 
