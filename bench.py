@@ -663,7 +663,7 @@ def main():
         v = variant[order[k]]
         sweeps[f"sweep_{k + 1}"] = {
             "axis": "xyz"[order[k]], "variant": v,
-            "form": {10: "streaming-staged", 11: "streaming-vec4"}.get(v % 12, "streaming") if v % 12 >= 6
+            "form": {10: "streaming-staged", 11: "streaming-staged"}.get(v % 12, "streaming") if v % 12 >= 6
             else "shared-memory",
             "ms": prof[1 + k], "hbm_gbs_algorithmic": alg_bytes[f"sweep_{k + 1}"] / t / 1e9}
         if ops is not None:

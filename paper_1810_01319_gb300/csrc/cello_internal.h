@@ -22,7 +22,7 @@ struct SweepVariant {
   int min_blocks;    // resident CTAs per SM the register bound is set for
   bool persistent;   // work-counter schedule over a resident grid
   bool stream;       // register-streaming form (sweep_stream_kernel)
-  int vec;           // streaming form moving x pencils four cells at a time: 1 registers, 3 staged by cp.async
+  int vec;           // streaming form moving x pencils four cells at a time, staged by cp.async (3), or not (0)
 };
 int sweep_variant_count_f32();
 int sweep_variant_count_f64();

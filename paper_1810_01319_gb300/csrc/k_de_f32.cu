@@ -37,7 +37,7 @@ void launch_stream_de_f32(const DevMesh& m, const SweepParams& p, int grid, cuda
 
 // The streaming variants of the float32 table: {CTA size, min CTAs per SM, vector I/O}.
 #define CELLO_DE_STREAM(X, NB) X(NB, 64, 8, 0) X(NB, 128, 4, 0) X(NB, 64, 6, 0) X(NB, 32, 16, 0) X(NB, 64, 8, 3) \
-  X(NB, 64, 6, 1)
+  X(NB, 64, 6, 3)
 #define CELLO_DE_SINST(NB, CT, MINB, VEC) \
   template void launch_stream_de_f32<NB, CT, MINB, VEC>(const DevMesh&, const SweepParams&, int, cudaStream_t);
 CELLO_DE_STREAM(CELLO_DE_SINST, 8)

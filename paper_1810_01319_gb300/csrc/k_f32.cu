@@ -11,10 +11,10 @@ namespace cello {
 static const SweepVariant kVariants[] = {
     {8, 3, false, false},  {8, 4, false, false},  {4, 6, false, false}, {16, 1, false, false},
     {4, 8, false, false},  {16, 2, false, false}, {64, 8, false, true}, {128, 4, false, true},
-    {64, 6, false, true},  {32, 16, false, true}, {64, 8, false, true, 3}, {64, 6, false, true, 1},
+    {64, 6, false, true},  {32, 16, false, true}, {64, 8, false, true, 3}, {64, 6, false, true, 3},
     {8, 3, true, false},   {8, 4, true, false},   {4, 6, true, false},  {16, 1, true, false},
     {4, 8, true, false},   {16, 2, true, false},  {64, 8, true, true},  {128, 4, true, true},
-    {64, 6, true, true},   {32, 16, true, true},  {64, 8, true, true, 3},  {64, 6, true, true, 1},
+    {64, 6, true, true},   {32, 16, true, true},  {64, 8, true, true, 3},  {64, 6, true, true, 3},
 };
 constexpr int kNT = 12;  // distinct kernel instantiations; variant v uses template v % kNT
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
@@ -125,7 +125,7 @@ static void prepare_nb(int sms) {
   prepare_stream_variant<NB, 64, 6, 0>(8, sms);
   prepare_stream_variant<NB, 32, 16, 0>(9, sms);
   prepare_stream_variant<NB, 64, 8, 3>(10, sms);
-  prepare_stream_variant<NB, 64, 6, 1>(11, sms);
+  prepare_stream_variant<NB, 64, 6, 3>(11, sms);
   for (int v = kNT; v < kNV; ++v) g_resident[nb_index(NB)][v] = g_resident[nb_index(NB)][v - kNT];
 }
 
@@ -144,7 +144,7 @@ static void launch_nb(const DevMesh& m, const SweepParams& p, int pencils, cudaS
     case 8: launch_stream_variant<NB, 64, 6, 0>(m, p, pencils, v, s); break;
     case 9: launch_stream_variant<NB, 32, 16, 0>(m, p, pencils, v, s); break;
     case 10: launch_stream_variant<NB, 64, 8, 3>(m, p, pencils, v, s); break;
-    case 11: launch_stream_variant<NB, 64, 6, 1>(m, p, pencils, v, s); break;
+    case 11: launch_stream_variant<NB, 64, 6, 3>(m, p, pencils, v, s); break;
   }
 }
 

@@ -541,18 +541,14 @@ __device__ __forceinline__ float lane4(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-__device__ __forceinline__ void set_lane4(float4& v, int i, float x) {
-  if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
-}
 
-// VEC > 0 (float32, used on the x sweep, whose pencils run along the
+// VEC = 3 (float32, used on the x sweep, whose pencils run along the
 // contiguous axis): cells are read and written four at a time as 16-byte
 // vectors (a group is read one group ahead; the group updated during group
 // g is g-1, written back at its end) instead of 4-byte accesses 160 bytes
-// apart across the warp; VEC = 1 unrolls the four cells of a group in
-// registers, VEC = 3 stages the groups in shared memory by asynchronous
-// copies and runs them through one copy of the step; other axes take the
-// one-cell path.
+// apart across the warp, the groups staged in shared memory by asynchronous
+// copies and run two cells per copy of the step; other axes, and VEC = 0,
+// take the one-cell walk.
 template <typename T, int NB, int CT, int MINB, int VEC, int RS>
 __global__ void __launch_bounds__(CT, MINB)
 sweep_stream_kernel(DevMesh m, SweepParams prm) {
@@ -649,43 +645,6 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
           }
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      } else if (VEC > 0 && axis == 0) {
-        // VEC == 1; rows start 16-byte aligned: N is a multiple of 4 and every slab and row offset is
-        float4* b4 = reinterpret_cast<float4*>(base);
-        float4 nx4[NQ];   // the next group of four cells
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) nx4[c] = b4[comp[c] * (SLAB / 4)];
-#pragma unroll 1
-        for (int g = 0; g < N / 4; ++g) {
-          float4 cur4[NQ], old4[NQ], out4[NQ];
-#pragma unroll
-          for (int c = 0; c < NQ; ++c) cur4[c] = nx4[c];
-          if (g + 1 < N / 4) {
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) nx4[c] = b4[comp[c] * (SLAB / 4) + g + 1];
-          }
-          if (g >= 2) {
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) old4[c] = b4[comp[c] * (SLAB / 4) + g - 1];
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            T Us[NQ], up[NQ];
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) {
-              Us[c] = lane4(cur4[c], i);
-              old[c] = lane4(old4[c], i);
-            }
-            stream_step<T, NB, RS, true>(S, 4 * g + i, Us, old, base, 1, comp, dtdx, gs, m, prm, leaf, axis,
-                                         face_row, pa, pb, up);
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) set_lane4(out4[c], i, up[c]);
-          }
-          if (g >= 2 && g - 1 <= N / 4 - 2) {   // group g-1 holds interior cells 4(g-1) .. 4(g-1)+3
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) b4[comp[c] * (SLAB / 4) + g - 1] = out4[c];
-          }
-        }
       } else {
         // the one-cell walk, compiled once per axis so that the slab offsets of the fields
         // and the stride along the pencil are constants of the address arithmetic

@@ -81,9 +81,9 @@ def test_amr32_fp64_20_steps(amr32, variant):
 
 
 # one variant of each float32 form per axis (x, y, z): shared-memory phases,
-# one-cell register walk, staged four-cell x walk with one-cell y and z
+# one-cell register walk, staged four-cell x walk with one-cell y and z (8 and 6 CTAs per SM)
 FP32_FORMS = {"shared-memory": [0, 0, 0], "streaming": [6, 6, 6], "streaming-staged": [22, 22, 22],
-              "streaming-vec4": [23, 20, 20]}
+              "streaming-staged-6": [23, 20, 20]}
 
 
 @pytest.mark.parametrize("form", sorted(FP32_FORMS))
