@@ -38,8 +38,9 @@ WORKLOAD = dict(workload="blob-amr-large", root=[16, 16, 16], n=32, max_level=2,
 # ncu on the 4^3-root blob box (3,970 leaves) for the same kernel form and
 # position in the sweep order, keyed "axis-form-position"; the roofline's
 # traffic is this times the leaves of the launch.
-SWEEP_DRAM_BYTES_PER_LEAF = {"x-streaming-staged-sweep_1": 2.578e6, "y-streaming-staged-sweep_2": 2.291e6,
-                             "z-streaming-staged-sweep_3": 1.831e6}
+SWEEP_DRAM_BYTES_PER_LEAF = {"x-streaming-staged-sweep_1": 2.573e6,
+                             "y-streaming-staged-sweep_2": 2.290e6, "y-streaming-sweep_2": 2.290e6,
+                             "z-streaming-staged-sweep_3": 1.830e6, "z-streaming-sweep_3": 1.830e6}
 
 
 def alu_peak(log=print):

@@ -375,91 +375,6 @@ CELLO_HD void riemann_flux(const T L[NQ], const T R[NQ], const Gas<T>& gs, T F[N
   }
 }
 
-// Float32 form of the same solver for the bulk path: the shock-curve
-// quantities are rewritten with shared reciprocals, algebraically identical
-// to riemann_flux (x = 1 + g1 (p*/p - 1) = (g1/p) p* + (1 - g1),
-// W = C sqrt(x), (p* - p)/W = (p* - p) rsqrt(x)/C, Z = 2W^3/(W^2 + C^2) =
-// 2 W x/(x + 1)); the float64 path keeps the literal formulas.
-template <int NQ = 5>
-CELLO_HD void riemann_flux_fast(const float L[NQ], const float R[NQ], const Gas<float>& gs, float F[NQ],
-                                float* uf = nullptr) {
-  const float rL = L[0], uL = L[1], pL = L[4];
-  const float rR = R[0], uR = R[1], pR = R[4];
-  const float qL = (gs.gamma * pL) * rL, qR = (gs.gamma * pR) * rR;
-#ifdef __CUDA_ARCH__
-  const float iCL = rsqrtf(qL), iCR = rsqrtf(qR);
-#else
-  const float iCL = 1.0f / sqrtf(qL), iCR = 1.0f / sqrtf(qR);
-#endif
-  const float CL = qL * iCL, CR = qR * iCR;
-  float ps = vdiv((CR * pL + CL * pR) + (CL * CR) * (uL - uR), CL + CR);
-  ps = vmax(ps, float(kPFloor));
-  const float aL = vdiv(gs.g1, pL), aR = vdiv(gs.g1, pR), b = 1.0f - gs.g1;
-  float WLs, WRs, uLs, uRs, ZL, ZR;
-#pragma unroll 1
-  for (int it = 0; it <= kRiemannIters; ++it) {
-    const float xL = aL * ps + b, xR = aR * ps + b;
-#ifdef __CUDA_ARCH__
-    const float rxL = rsqrtf(xL), rxR = rsqrtf(xR);
-#else
-    const float rxL = 1.0f / sqrtf(xL), rxR = 1.0f / sqrtf(xR);
-#endif
-    WLs = CL * (xL * rxL);
-    WRs = CR * (xR * rxR);
-    uLs = uL - (ps - pL) * (iCL * rxL);
-    uRs = uR + (ps - pR) * (iCR * rxR);
-    ZL = vdiv((2.0f * WLs) * xL, xL + 1.0f);
-    ZR = vdiv((2.0f * WRs) * xR, xR + 1.0f);
-    if (it == kRiemannIters) break;
-    const float pn = vmax(ps - vdiv((ZL * ZR) * (uRs - uLs), ZL + ZR), float(kPFloor));
-    if (pn == ps) break;   // fixed point (see riemann_flux)
-    ps = pn;
-  }
-  const float us = vdiv(ZL * uLs + ZR * uRs, ZL + ZR);
-  const bool left = us >= 0.0f;
-  const float rs = left ? rL : rR;
-  const float u_s = left ? uL : uR;
-  const float p_s = left ? pL : pR;
-  const float W_s = left ? WLs : WRs;
-  const float t1 = left ? L[2] : R[2];
-  const float t2 = left ? L[3] : R[3];
-  const float v_s = left ? -uL : uR;
-  const float v_star = left ? -us : us;
-  const float irs = vdiv(1.0f, rs);
-  const float tau = irs - vdiv(ps - p_s, W_s * W_s);
-  float rstar = (tau > 0.0f) ? vdiv(1.0f, tau) : float(kRhoFloor);
-  rstar = vmax(rstar, float(kRhoFloor));
-  const float c_s = vsqrt((gs.gamma * p_s) * irs);
-  const float c_star = vsqrt(vdiv(gs.gamma * ps, rstar));
-  const bool shock = ps > p_s;
-  const float head = shock ? v_s + W_s * irs : v_s + c_s;
-  const float tail = shock ? head : v_star + c_star;
-  const bool orig = head <= 0.0f;
-  const bool star = !orig && (tail > 0.0f);
-  float r, u, p;
-  if (orig) {
-    r = rs; u = u_s; p = p_s;
-  } else if (star) {
-    r = rstar; u = us; p = ps;
-  } else {
-    const float w = vdiv(head, head - tail);
-    r = rs + w * (rstar - rs);
-    u = u_s + w * (us - u_s);
-    p = p_s + w * (ps - p_s);
-  }
-  const float f0 = r * u;
-  F[0] = f0;
-  F[1] = f0 * u + p;
-  F[2] = f0 * t1;
-  F[3] = f0 * t2;
-  const float E = p * gs.inv_gm1 + (0.5f * r) * (u * u + (t1 * t1 + t2 * t2));
-  F[4] = u * (E + p);
-  if constexpr (NQ > 5) {
-    F[5] = f0 * (left ? L[5] : R[5]);
-    *uf = u;
-  }
-}
-
 // HLLC flux (Toro, Spruce & Speares 1994; Toro, Riemann Solvers and
 // Numerical Methods, Sec. 10.4): Davis wave-speed bounds, contact speed S*,
 // and the flux of the fan region at x/t = 0 (F_L if S_L >= 0, F*_L if
@@ -513,18 +428,11 @@ template <typename T>
 CELLO_HD void riemann_flux_bulk(const T L[5], const T R[5], const Gas<T>& gs, T F[5]) {
   riemann_flux(L, R, gs, F);
 }
-template <>
-CELLO_HD void riemann_flux_bulk<float>(const float L[5], const float R[5], const Gas<float>& gs, float F[5]) {
-  riemann_flux_fast(L, R, gs, F);
-}
 
-// Six-component (dual-energy) forms with the interface velocity.
+// Six-component (dual-energy) form with the interface velocity.
 template <typename T>
 CELLO_HD void riemann_flux_bulk6(const T L[6], const T R[6], const Gas<T>& gs, T F[6], T* uf) {
   riemann_flux<T, 6>(L, R, gs, F, uf);
-}
-CELLO_HD void riemann_flux_bulk6(const float L[6], const float R[6], const Gas<float>& gs, float F[6], float* uf) {
-  riemann_flux_fast<6>(L, R, gs, F, uf);
 }
 
 }  // namespace cello

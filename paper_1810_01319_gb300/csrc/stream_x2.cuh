@@ -335,8 +335,14 @@ __device__ __forceinline__ void sampled_flux(float r, float u, float p, float2 t
   if constexpr (NQ == 6) F.c.x = f0; else F.c = f0;
 }
 
-// Two-shock Riemann solver (ppm.cuh: riemann_flux_fast, the same algebra),
-// the left and right shock curves evaluated in one lane pair (L, R).
+// Two-shock Riemann solver (ppm.cuh: riemann_flux, the same iteration and
+// sampling), the left and right shock curves evaluated in one lane pair
+// (L, R).  The shock-curve quantities are rewritten with shared
+// reciprocals, algebraically identical to the literal formulas:
+// x = 1 + g1 (p*/p - 1) = (g1/p) p* + (1 - g1), W = C sqrt(x),
+// (p* - p)/W = (p* - p) rsqrt(x)/C, Z = 2W^3/(W^2 + C^2) = 2 W x/(x + 1),
+// with C = sqrt(gamma p rho) = (gamma p rho) rsqrt(gamma p rho); the float64
+// path keeps the literal formulas.
 template <int NQ>
 __device__ __forceinline__ void two_shock(const Cell<NQ>& Lc, const Cell<NQ>& Rc, const Gas<float>& gs, Cell<NQ>& F,
                                           float* uf) {
