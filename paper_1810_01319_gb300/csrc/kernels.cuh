@@ -596,10 +596,11 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
       if (VEC == 3 && axis == 0) {
         // the groups of four cells are copied HBM -> shared memory by cp.async, one group
         // ahead, into three per-thread slots (current group, the group being updated, the
-        // group in flight); the four cells of a group run through one copy of the step,
-        // each updated cell written to a fourth slot that cp.async never targets and
-        // stored from there as one vector per field, so the x sweep's code is no larger
-        // than the one-cell walk
+        // group in flight); the four cells of a group run through the step two at a time
+        // (two copies of the step: half the sliding window's register moves, while four
+        // copies would miss in the instruction cache), each updated cell written to a
+        // fourth slot that cp.async never targets and stored from there as one vector
+        // per field
         extern __shared__ __align__(16) unsigned char stream_raw[];
         float4* my = reinterpret_cast<float4*>(stream_raw) + t;   // slot s, field c at my[(s * NQ + c) * CT]
         const float4* b4 = reinterpret_cast<const float4*>(base);
