@@ -559,7 +559,6 @@ sweep_stream_kernel(DevMesh m, SweepParams prm) {
   T* U = static_cast<T*>(prm.U);
   const int axis = prm.axis;
   const int cA = prm.a1 - prm.a0, cB = prm.b1 - prm.b0;
-  const long sAx = axis == 0 ? 1 : (axis == 1 ? N : (long)N * N);
   const long sTA = axis == 2 ? N : (long)N * N;
   const long sTB = axis == 0 ? N : 1;
   int comp[6];
