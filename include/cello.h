@@ -307,11 +307,17 @@ cello_status cello_sweep_opcount(const cello_mesh* mesh, float* U_host, const in
 /* One step with the state in HOST memory: copies the state (host ->
  * device, into the caller's device buffer U_dev of the same size) and dt,
  * runs cello_hydro_step, copies the state back into U_host and dt_next and
- * the five totals into out_host[6], and waits for the stream.  U_host should
- * be page-locked (cudaHostAlloc or cudaHostRegister) for full copy speed;
- * pageable memory works, slower.  dt_host: the step's dt; dt_dev: a device
- * double the call writes it to; scratch_dev: 6 device doubles.  Errors as
- * cello_hydro_step. */
+ * the five totals into out_host[6], and waits for the stream.  If
+ * cudaHostGetDevicePointer gives U_host a device address (page-locked memory
+ * from cudaHostAlloc or cudaHostRegister; on systems whose GPU reads the
+ * host's page tables, any host memory) and U_host is 16-byte aligned, the
+ * GPU reads and writes its interior cells directly through that address and
+ * nothing else (the step rewrites every ghost cell from interiors before
+ * reading one): U_host's ghost cells are then neither read nor written, and
+ * the whole buffer must be addressable that way.  Otherwise the buffer is
+ * copied whole in both directions.  dt_host: the
+ * step's dt; dt_dev: a device double the call writes it to; scratch_dev: 6
+ * device doubles.  Errors as cello_hydro_step. */
 cello_status cello_hydro_step_host(cello_mesh* mesh, void* U_host, void* U_dev, double dt_host, double* dt_dev,
                                    int cycle, double cfl, double* scratch_dev, double* out_host, void* stream);
 

@@ -199,8 +199,10 @@ class Mesh:
         return o[:, :6].copy(), o[:, 6].copy(), o[:, 7].copy(), host
 
     def hydro_step_host(self, U_host, U_dev, dt: float, cycle: int, cfl: float = 0.4, stream=None):
-        """One step with the state in host memory (copied in and out by the
-        library; page-locked U_host copies at full speed).  Returns
+        """One step with the state in host memory.  Where U_host has a device
+        address (pin_memory, or any host memory on systems whose GPU reads the
+        host page tables) the GPU reads and writes its interior cells directly,
+        ghost cells untouched; otherwise it is copied whole.  Returns
         (dt_next, totals[5]) as Python floats."""
         self._check_state(U_dev)
         if U_host.device.type != "cpu" or U_host.dtype != U_dev.dtype or U_host.shape != U_dev.shape \

@@ -199,6 +199,9 @@ void launch_particles_push(const DevMesh& m, const unsigned long long* keys, con
 void launch_halo_copy(const DevMesh& m, void* U, int precision, const int* ids, long count, void* buf, int pack,
                       cudaStream_t s);
 void launch_flux_copy(double* reg, const int* slots, long count, long per, double* buf, int pack, cudaStream_t s);
+// Interior cells of every leaf and field from src to dst (same layout, both
+// device-addressable, 16-byte aligned).
+void launch_interior_copy(const DevMesh& m, const void* src, void* dst, int precision, cudaStream_t s);
 // Host: counted operations of one leaf's sweep (opcount.cu), update applied.
 void opcount_leaf(float* slab, int n, int g, int axis, int a0, int a1, int b0, int b1, double dtdx, double gamma,
                   int riemann, int steepen, int dual, unsigned long long counts[6]);

@@ -1170,10 +1170,23 @@ cello_status cello_hydro_step_host(cello_mesh* M, void* U_host, void* U_dev, dou
   CELLO_REQUIRE_ALIGNED(U_dev);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)M->B * nfields(M->desc) * M->N * M->N * M->N * (size_t)M->desc.precision;
-  CELLO_CUDA(cudaMemcpyAsync(U_dev, U_host, bytes, cudaMemcpyHostToDevice, s));
+  // Host memory with a device address (page-locked, or any host memory where
+  // the GPU reads the host's page tables), 16-byte aligned: the SMs read and
+  // write its interior cells only (the step rewrites every ghost cell from
+  // interiors before reading one).  Otherwise whole-buffer copies.
+  void* h_dev = nullptr;
+  bool mapped = false;
+  if ((reinterpret_cast<uintptr_t>(U_host) & 15u) == 0) {
+    if (cudaHostGetDevicePointer(&h_dev, U_host, 0) == cudaSuccess) mapped = h_dev != nullptr;
+    else cudaGetLastError();   // no device address for this memory
+  }
+  const DevMesh dm = M->dev();
+  if (mapped) launch_interior_copy(dm, h_dev, U_dev, M->desc.precision, s);
+  else CELLO_CUDA(cudaMemcpyAsync(U_dev, U_host, bytes, cudaMemcpyHostToDevice, s));
   CELLO_CUDA(cudaMemcpyAsync(dt_dev, &dt_host, sizeof(double), cudaMemcpyHostToDevice, s));
   CELLO_TRY(cello_hydro_step(M, U_dev, dt_dev, cycle, cfl, scratch_dev, scratch_dev + 1, stream));
-  CELLO_CUDA(cudaMemcpyAsync(U_host, U_dev, bytes, cudaMemcpyDeviceToHost, s));
+  if (mapped) launch_interior_copy(dm, U_dev, h_dev, M->desc.precision, s);
+  else CELLO_CUDA(cudaMemcpyAsync(U_host, U_dev, bytes, cudaMemcpyDeviceToHost, s));
   CELLO_CUDA(cudaMemcpyAsync(out_host, scratch_dev, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CELLO_CUDA(cudaStreamSynchronize(s));
   return CELLO_OK;

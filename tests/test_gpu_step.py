@@ -203,13 +203,21 @@ def test_sweep_opcount_mirrors_the_kernel():
         assert np.all(ops > 0)
 
 
-def test_hydro_step_host_buffers_match_device_step(blob_amr):
+@pytest.mark.parametrize("pinned", [False, True])
+def test_hydro_step_host_buffers_match_device_step(blob_amr, pinned):
     """The host-buffer entry point copies in, steps and copies out: the same
-    state, dt_next and totals as the device call."""
+    interior state, dt_next and totals as the device call.  Page-locked
+    memory is read and written by the GPU, interior cells only, its ghost
+    cells left as they were; pageable memory is either copied whole or (on
+    systems whose GPU reads the host page tables) handled the same way."""
     od, om, flags, U0, Uo, dts = blob_amr
     gm = H.gpu_mesh_from_flags(od, flags, 4)
     Ud = U0.to(torch.float32).cuda().contiguous()
     host = U0.to(torch.float32).contiguous().clone()
+    if pinned:
+        host = host.pin_memory()
+        host[:, :, :4] = -7.0   # ghost planes of the host copy: neither read nor written
+        marked = host[:, :, :4].clone()
     scratch = torch.empty_like(Ud)
     dtn = torch.zeros(1, dtype=torch.float64, device="cuda")
     tot = torch.zeros(5, dtype=torch.float64, device="cuda")
@@ -219,7 +227,9 @@ def test_hydro_step_host_buffers_match_device_step(blob_amr):
         dn, th = gm.hydro_step_host(host, scratch, dt, c)
         assert dn == float(dtn.item())
         assert th == [float(x) for x in tot.cpu()]
-    assert torch.equal(host, Ud.cpu())
+    assert torch.equal(H.interior(host, 16), H.interior(Ud.cpu(), 16))
+    if pinned:
+        assert torch.equal(host[:, :, :4], marked)
 
 
 @pytest.mark.parametrize("precision", [4, 8])
